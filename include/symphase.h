@@ -1,0 +1,251 @@
+/*
+ * symphase.h -- C ABI of the GB300 symbolic-phase stabilizer sampler.
+ *
+ * Method: arXiv 2311.03906 ("Phase symbolization for fast simulation of
+ * stabilizer circuits").  One forward pass of the stabilizer tableau with
+ * symbolic phases (Sec. 3.2, Eq. stabilizer3, rules Init-C / Init-P /
+ * Init-M) turns every measurement into an affine GF(2) form
+ *     m_j = c_j XOR <a_j, s>
+ * over the fault symbols and the random-measurement symbols (Sec. 3.2.1).
+ * Sampling (Sec. 3.2.3, Eq. sampling, Algorithm 1 "Sampling") draws every
+ * symbol from its noise channel and evaluates all forms as one GF(2)
+ * matrix product.  Detectors and observables are XORs of measurement
+ * records; their forms are XORs of the measurement forms.
+ *
+ * Conventions shared by every entry point
+ *   - All functions return an sp_status.  Arguments are validated before
+ *     any GPU work is enqueued; on error nothing is launched, the status is
+ *     returned and sp_last_error() (thread-local) describes the problem.
+ *     No function aborts the process.
+ *   - Pointers named d_* are caller-owned DEVICE memory; h_* are caller-
+ *     owned HOST memory.  The library never frees caller memory.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  sp_sample / sp_expect / sp_expect_grad / sp_sample_batch only
+ *     enqueue work on it and return without synchronising.
+ *   - Records are bit-packed, shot-major, little-endian: record r of shot t
+ *     is bit (r mod 64) of word t*ceil(n/64) + r/64 of a uint64_t array.
+ *     Pad bits of the last word of every shot are written as zero.
+ *   - Symbols are numbered in op order starting at 1 (symbol 0 is the
+ *     constant): a noise channel's symbols when the op is reached
+ *     (X/Y/Z_ERROR: 1; DEPOLARIZE1: 2 = x,z; DEPOLARIZE2: 4 = x_a,z_a,x_b,z_b),
+ *     a random measurement's symbol when it happens (Sec. 3.1: "symbols
+ *     induced by random measurements").  Channels are numbered the same way.
+ *   - Draws: Philox4x32-10, key (seed lo32, seed hi32), counter (shot lo32,
+ *     shot hi32, channel/4, 0), word channel%4 = u.  A channel fires when
+ *     u < T, T = floor(p*2^32) (p = 1 gives 2^32-1); a random-measurement
+ *     channel has T = 2^31.  DEPOLARIZE1/2 then take k = floor(u*m/T)
+ *     (m = 3 / 15) and symbol s0+i gets bit i of k+1.  Records depend only on
+ *     (seed, global shot index), so any chunking of a shot range gives the
+ *     same bits.
+ */
+#ifndef SYMPHASE_H
+#define SYMPHASE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SP_API __attribute__((visibility("default")))
+#else
+#define SP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SP_OK = 0,
+    SP_ERR_INVALID_ARG = 1,              /* bad pointer, size, target, probability, look-back */
+    SP_ERR_UNSUPPORTED_OP = 2,           /* unknown opcode */
+    SP_ERR_NONDETERMINISTIC_DETECTOR = 3,/* a detector/observable depends on a random outcome */
+    SP_ERR_OOM = 4,                      /* device or host allocation failed */
+    SP_ERR_CUDA = 5,                     /* a CUDA runtime call failed */
+    SP_ERR_TIMEOUT = 6,                  /* a device-side bounded wait gave up */
+    SP_ERR_TOO_LARGE = 7                 /* circuit beyond the supported size (qubits > 1024) */
+} sp_status;
+
+/* Op codes of sp_op.opcode (the circuit grammar). */
+enum {
+    SP_OP_H = 0, SP_OP_S = 1, SP_OP_CX = 2,           /* Clifford gates (Init-C) */
+    SP_OP_X = 3, SP_OP_Y = 4, SP_OP_Z = 5,            /* Pauli gates (Fact 1) */
+    SP_OP_M = 6, SP_OP_MR = 7, SP_OP_R = 8,           /* Z measurement, measure+reset, reset (Init-M) */
+    SP_OP_X_ERROR = 9, SP_OP_Y_ERROR = 10, SP_OP_Z_ERROR = 11,
+    SP_OP_DEPOLARIZE1 = 12, SP_OP_DEPOLARIZE2 = 13,   /* Pauli faults (Init-P, Sec. 3.1 channels) */
+    SP_OP_DETECTOR = 14, SP_OP_OBSERVABLE_INCLUDE = 15,
+    SP_OP_TICK = 16
+};
+
+/* One op.  Gate / noise / measurement ops apply to each target in turn
+ * (CX and DEPOLARIZE2 to consecutive pairs).  DETECTOR and
+ * OBSERVABLE_INCLUDE targets are look-backs k >= 1 meaning rec[-k].
+ * arg: probability for noise ops, observable index for
+ * OBSERVABLE_INCLUDE, ignored otherwise. */
+typedef struct {
+    uint32_t opcode;
+    uint32_t ntargets;
+    const uint32_t *targets;
+    double arg;
+} sp_op;
+
+typedef struct {
+    uint32_t num_qubits;   /* <= 1024 */
+    uint32_t num_ops;
+    const sp_op *ops;
+} sp_circuit_desc;
+
+/* Sampler variants for the GF(2) product. */
+enum {
+    SP_PATH_AUTO = 0,      /* chosen at build time from the measured density */
+    SP_PATH_SPARSE = 1,    /* symbol-index XOR gather over bit-sliced shots */
+    SP_PATH_DENSE = 2      /* 64-bit AND/popcount parity over shot-major words */
+};
+
+typedef struct {
+    uint64_t num_qubits;
+    uint64_t num_measurements;     /* recorded (M, MR) */
+    uint64_t num_detectors;
+    uint64_t num_observables;
+    uint64_t num_symbols;          /* n_s (excluding the constant) */
+    uint64_t num_channels;         /* fault channels + random-measurement channels */
+    uint64_t num_random;           /* random-measurement symbols */
+    uint64_t nnz_rows;             /* nonzero symbol coefficients over all record rows */
+    uint64_t nnz_delta;            /* after parent-delta encoding */
+    uint64_t log_words;            /* length of the traversal's row-operation log */
+    double density;                /* nnz_rows / (rows * n_s) */
+    int32_t path;                  /* SP_PATH_SPARSE or SP_PATH_DENSE */
+    int32_t reserved;
+    uint64_t chunk_shots;          /* shots per internal sampling chunk */
+    double build_ms;               /* wall time of sp_build */
+} sp_info_t;
+
+typedef struct sp_program sp_program;   /* opaque, library-owned */
+
+/*
+ * sp_build -- Algorithm 1 "Initialization": traverse the circuit once with
+ * symbolic phases (Init-C, Init-P, Init-M of Sec. 3.2.2) on the GPU and keep
+ * the coefficient rows of every measurement, detector and observable plus
+ * the sampler program on the current device.
+ *   circuit      host description; read only during the call.
+ *   cuda_stream  stream for the build kernels; sp_build synchronises it.
+ *   out          receives a program to release with sp_free.
+ * Errors: INVALID_ARG (target >= num_qubits, CX on one qubit, p outside
+ * [0,1], look-back beyond the records so far), UNSUPPORTED_OP,
+ * TOO_LARGE (num_qubits > 1024), NONDETERMINISTIC_DETECTOR, OOM, CUDA.
+ */
+SP_API sp_status sp_build(const sp_circuit_desc *circuit, void *cuda_stream, sp_program **out);
+
+/* sp_info -- sizes and statistics of a built program (host only). */
+SP_API sp_status sp_info(const sp_program *prog, sp_info_t *out);
+
+/*
+ * sp_sample -- Algorithm 1 "Sampling" (Eq. sampling) for shots
+ * shot0 .. shot0+nshots-1: draw every symbol (Sec. 3.1 distributions,
+ * Philox keyed by (seed, shot, channel)), then evaluate all forms.
+ *   d_meas  nshots * ceil(num_measurements/64) uint64 words, or NULL to skip
+ *   d_det   nshots * ceil(num_detectors/64) words, or NULL
+ *   d_obs   nshots * ceil(num_observables/64) words, or NULL
+ * Internal scratch (fault-bit and record tiles) is owned by the program and
+ * reused, so calls on one program must not overlap on different streams.
+ * Errors: INVALID_ARG (NULL prog, misaligned pointer), OOM, CUDA.
+ */
+SP_API sp_status sp_sample(sp_program *prog, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                    uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, void *cuda_stream);
+
+/*
+ * sp_sample_host -- the same records written to HOST buffers (layout as in
+ * sp_sample).  Shots are produced in chunks on the device and copied back
+ * while the next chunk is computed; pinned host memory gives full speed.
+ * Synchronises the stream before returning.
+ */
+SP_API sp_status sp_sample_host(sp_program *prog, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                         uint64_t *h_meas, uint64_t *h_det, uint64_t *h_obs, void *cuda_stream);
+
+/*
+ * sp_sample_batch -- many programs (uneven sizes, shot counts, seeds) in one
+ * enqueue.  Program i samples shots 0..nshots[i]-1 with seeds[i] into
+ * d_meas[i], d_det[i], d_obs[i] (entries may be NULL).  The work of all
+ * programs is laid out as one list of (program, shot tile) items and run by
+ * persistent kernels; the enqueue sequence is captured once in a CUDA graph
+ * per (program set, shot counts) and replayed.  Records are identical to nprog
+ * separate sp_sample calls.
+ */
+SP_API sp_status sp_sample_batch(sp_program *const *progs, uint32_t nprog, const uint64_t *seeds,
+                          const uint64_t *nshots, uint64_t *const *d_meas,
+                          uint64_t *const *d_det, uint64_t *const *d_obs, void *cuda_stream);
+
+/*
+ * sp_expect -- analytic detector (then observable) parity expectations
+ * E_j = E[(-1)^{D_j}] as log|E_j| in FP32:
+ *     log|E_j| = sum_c [channel c touches row j] * log(1 - 2 kappa_c p_c)
+ * with kappa = 1 (X/Y/Z_ERROR), 2/3 (DEPOLARIZE1), 8/15 (DEPOLARIZE2): the
+ * share of a channel's outcomes with odd overlap with any nonzero mask.
+ *   d_p     num_channels FP32 probabilities (random-measurement channels are
+ *           ignored), or NULL for the circuit's own probabilities.
+ *   d_logE  num_detectors + num_observables FP32 outputs.
+ * The sign of E_j is (-1)^{c_j} (constant bit of the row, see sp_export_rows).
+ */
+SP_API sp_status sp_expect(sp_program *prog, const float *d_p, float *d_logE, void *cuda_stream);
+
+/*
+ * sp_expect_grad -- adjoint of sp_expect:
+ *     d_grad_p[c] = sum_j d_grad_logE[j] * d log|E_j| / d p_c
+ *                 = -2 kappa_c / (1 - 2 kappa_c p_c) * sum_j A[c,j] g_j.
+ *   d_p, d_grad_logE  inputs (d_p may be NULL as in sp_expect)
+ *   d_grad_p          num_channels FP32 outputs (overwritten)
+ */
+SP_API sp_status sp_expect_grad(sp_program *prog, const float *d_p, const float *d_grad_logE,
+                         float *d_grad_p, void *cuda_stream);
+
+/*
+ * sp_export_rows -- copy coefficient rows to the host for inspection:
+ * which = 0 measurements, 1 detectors, 2 observables.  Row r occupies
+ * row_words uint64 words of h_out (bit 0 = constant c_j, bit s = symbol s);
+ * row_words must be >= ceil((num_symbols+1)/64).  Synchronous.
+ */
+SP_API sp_status sp_export_rows(const sp_program *prog, int32_t which, uint64_t *h_out, uint64_t row_words);
+
+/*
+ * sp_export_channels -- per-channel threshold T and kind (0 = one symbol
+ * Bernoulli, 1 = DEPOLARIZE1, 2 = DEPOLARIZE2, 3 = random measurement) and
+ * first symbol.  Arrays of num_channels entries; any may be NULL.
+ */
+SP_API sp_status sp_export_channels(const sp_program *prog, uint32_t *h_T, uint8_t *h_kind, uint64_t *h_sym0);
+
+/* sp_set_path -- force the sampler variant (SP_PATH_*); AUTO restores the
+ * build-time choice. */
+SP_API sp_status sp_set_path(sp_program *prog, int32_t path);
+
+/* sp_set_chunk -- shots per internal chunk (multiple of 1024, 0 = default). */
+SP_API sp_status sp_set_chunk(sp_program *prog, uint64_t chunk_shots);
+
+/* Kernel classes reported by sp_profile_read. */
+enum {
+    SP_KERNEL_DRAW = 0,      /* Philox fault draw */
+    SP_KERNEL_PRODUCT = 1,   /* GF(2) product (sparse or dense variant) */
+    SP_KERNEL_EMIT = 2,      /* bit-sliced -> shot-major record transpose */
+    SP_KERNEL_FUSED = 3,     /* fused draw + product */
+    SP_KERNEL_CLASSES = 8
+};
+
+/*
+ * sp_profile_enable -- when on != 0, every kernel the program launches in
+ * sp_sample / sp_sample_host is bracketed by a pair of CUDA events recorded
+ * on the launching stream.  sp_profile_read waits for those events, writes
+ * the accumulated milliseconds and launch counts per kernel class into
+ * ms[SP_KERNEL_CLASSES] and launches[SP_KERNEL_CLASSES] (either may be NULL)
+ * and clears the accumulators.
+ */
+SP_API sp_status sp_profile_enable(sp_program *prog, int32_t on);
+SP_API sp_status sp_profile_read(sp_program *prog, double *ms, uint64_t *launches);
+
+/* sp_free -- release a program (NULL is allowed). */
+SP_API void sp_free(sp_program *prog);
+
+/* sp_last_error -- message of the last failing call on this thread. */
+SP_API const char *sp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYMPHASE_H */

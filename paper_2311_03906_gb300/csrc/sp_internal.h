@@ -1,0 +1,158 @@
+// sp_internal.h -- internal declarations of the GB300 symbolic-phase library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/symphase.h"
+
+namespace sp {
+
+// ----------------------------------------------------------------------------
+// Elementary instructions produced by flattening the circuit (one per target
+// or target pair).  Detectors and observables do not appear here.
+// ----------------------------------------------------------------------------
+enum InstCode : uint32_t {
+    I_H = 0, I_S, I_CX, I_X, I_Y, I_Z,
+    I_M, I_MR, I_R,
+    I_XERR, I_YERR, I_ZERR, I_DEP1, I_DEP2
+};
+
+struct Inst {
+    uint32_t code;
+    uint32_t a;      // qubit
+    uint32_t b;      // second qubit (CX, DEP2)
+    uint32_t aux;    // threshold T for noise ops
+    uint32_t pbits;  // FP32 bits of the probability of noise ops
+};
+
+// Channel kinds used by the draw kernel.
+enum ChannelKind : uint8_t { CK_BERN = 0, CK_DEP1 = 1, CK_DEP2 = 2, CK_RANDOM = 3 };
+
+// Events of the row-operation log written by the traversal's first pass and
+// replayed column-parallel by the second (header = kind << 24 | count).
+enum LogEvent : uint32_t {
+    EV_INJECT = 1,   // [hdr|k, s0]            symbols s0..s0+k-1 get their injection columns
+    EV_MRAND = 2,    // [hdr|cnt, p, s, rec, rows..]  random measurement with pivot p
+    EV_MDET = 3,     // [hdr|cnt, rec, rows..]        deterministic measurement
+    EV_RESET = 4     // [hdr|cnt, rows..]             conditional X^e on the rows
+};
+constexpr uint32_t NO_REC = 0xFFFFFFFFu;
+
+// Counters written by the traversal kernel.
+struct TraverseCounts {
+    uint64_t log_len;
+    uint32_t nsym;
+    uint32_t nch;
+    uint32_t nrec;
+    uint32_t err;      // 0 ok, 1 log overflow, 2 nondeterministic product phase
+    uint32_t pad[2];
+};
+
+struct DeviceBuffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// ----------------------------------------------------------------------------
+// A built program.
+// ----------------------------------------------------------------------------
+}  // namespace sp
+
+struct sp_program {
+    int device = 0;
+    uint32_t n = 0;                 // qubits
+    int64_t n_meas = 0, n_det = 0, n_obs = 0, n_rows = 0;
+    int64_t n_sym = 0, n_ch = 0, n_rand = 0;
+    int64_t log_len = 0;
+    int64_t apitch = 0;             // u32 words per coefficient row
+    // coefficient rows: meas, det, obs (bit 0 = constant)
+    uint32_t *d_A = nullptr;
+    // channels
+    uint32_t *d_chT = nullptr;
+    uint8_t *d_chKind = nullptr;
+    float *d_chP = nullptr;         // circuit probabilities (FP32)
+    uint32_t *d_chSym0 = nullptr;   // first symbol of each channel
+    // sparse sampler program: row j = parent (or none) XOR const XOR sum of B rows
+    uint32_t *d_rowOff = nullptr;   // [n_rows+1]
+    uint32_t *d_idx = nullptr;      // symbol-1 indices
+    int32_t *d_parent = nullptr;    // [n_rows]
+    uint8_t *d_cflag = nullptr;     // [n_rows]
+    int64_t nnz_rows = 0, nnz_delta = 0;
+    // dense program: A rows in u64 words over symbols 1..n_s (bit s-1)
+    uint64_t *d_A64 = nullptr;
+    int64_t a64pitch = 0;
+    uint8_t *d_const = nullptr;     // [n_rows]
+    // expectation: row x channel incidence (bits) and its transpose
+    uint32_t *d_inc = nullptr;      // [n_tgt][incPitch]
+    uint32_t *d_incT = nullptr;     // [n_ch][incTPitch]
+    int64_t incPitch = 0, incTPitch = 0;
+    float *d_kappa = nullptr;       // [n_ch]
+    float *d_wbuf = nullptr;        // [2 * n_ch] channel weights and derivatives
+    // scratch (owned, reused across sample calls)
+    uint32_t *d_B = nullptr;        // fault bits, bit-sliced: [n_sym][chunk/32]
+    uint32_t *d_recT = nullptr;     // records, bit-sliced: [n_rows][chunk/32]
+    uint64_t *d_Bd = nullptr;       // dense path: fault bits shot-major [chunk][a64pitch]
+    size_t scratch_shots = 0;
+    int64_t chunk_shots = 0;
+    int path = SP_PATH_SPARSE;
+    int build_path = SP_PATH_SPARSE;
+    double build_ms = 0.0;
+    double density = 0.0;
+    // host-side copies used for host entry points and batching
+    std::vector<uint8_t> h_const;
+    // pinned host staging for sp_sample_host (allocated lazily)
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    uint64_t *d_out_stage = nullptr;
+    size_t d_out_stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // per-kernel event profiling (sp_profile_enable)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+};
+
+namespace sp {
+
+// error plumbing (sp_capi.cu)
+sp_status set_error(sp_status st, const std::string &msg);
+sp_status cuda_error(cudaError_t e, const char *what);
+
+#define SP_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return ::sp::cuda_error(_e, #call);     \
+    } while (0)
+
+// build (sp_build.cu)
+sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_program *P);
+
+// profiling: bracket one kernel launch with events when enabled
+struct ProfScope {
+    sp_program *P;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(sp_program *P_, int cls_, cudaStream_t s_);
+    ~ProfScope();
+};
+
+// sampling (sp_sample.cu)
+sp_status ensure_scratch(sp_program *P, size_t shots);
+sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                       uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
+int64_t default_chunk(const sp_program *P);
+
+// expectation (sp_expect.cu)
+sp_status expect_fwd(sp_program *P, const float *d_p, float *d_logE, cudaStream_t s);
+sp_status expect_bwd(sp_program *P, const float *d_p, const float *d_g, float *d_grad, cudaStream_t s);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace sp

@@ -1,0 +1,255 @@
+// sp_sample.cu -- Algorithm 1 "Sampling" on the GPU (arXiv 2311.03906,
+// Sec. 3.2.3, Eq. sampling): draw b for every shot from the noise model,
+// then M = [m_1; ...; m_nm] . [b_1 ... b_nsmp] over GF(2).
+//
+//   K4 k_draw     Philox4x32-10 per (seed, shot, channel/4); lane = shot; the
+//                 channel's symbol bits (Sec. 3.1 distributions) are packed
+//                 32 symbols at a time and transposed across the warp into
+//                 bit-sliced words B[s-1][shot/32] (bit = shot % 32).
+//   K5 k_gather   the GF(2) product in sparse form: record row j of a
+//                 32-shot word is c'_j ^ rec[parent(j)] ^ XOR_{s in delta_j}
+//                 B[s-1], lane = 32-shot word, so every index load is shared
+//                 by 1024 shots and every B load is a coalesced 128-byte row
+//                 segment.
+//   K6 k_emit     32x32 bit transposes from the bit-sliced records to the
+//                 shot-major packed output.
+#include <algorithm>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+constexpr uint32_t FULLM = 0xffffffffu;
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t &o0, uint32_t &o1,
+                                              uint32_t &o2, uint32_t &o3)
+{
+    // Salmon et al. (SC'11): per round (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2,
+    // c <- (hi1^c1^k0, lo1, hi0^c3^k1, lo0); key += Weyl constants.
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    o0 = c0; o1 = c1; o2 = c2; o3 = c3;
+}
+
+// 32x32 bit transpose across a warp: in lane l holds row l (bit j = M[l][j]);
+// out lane j holds column j (bit l = M[l][j]).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+    const uint32_t m16 = 0x0000FFFFu, m8 = 0x00FF00FFu, m4 = 0x0F0F0F0Fu, m2 = 0x33333333u, m1 = 0x55555555u;
+    uint32_t y;
+    y = __shfl_xor_sync(FULLM, x, 16); x = (lane & 16) ? ((x & ~m16) | ((y >> 16) & m16)) : ((x & m16) | ((y & m16) << 16));
+    y = __shfl_xor_sync(FULLM, x, 8);  x = (lane & 8) ? ((x & ~m8) | ((y >> 8) & m8)) : ((x & m8) | ((y & m8) << 8));
+    y = __shfl_xor_sync(FULLM, x, 4);  x = (lane & 4) ? ((x & ~m4) | ((y >> 4) & m4)) : ((x & m4) | ((y & m4) << 4));
+    y = __shfl_xor_sync(FULLM, x, 2);  x = (lane & 2) ? ((x & ~m2) | ((y >> 2) & m2)) : ((x & m2) | ((y & m2) << 2));
+    y = __shfl_xor_sync(FULLM, x, 1);  x = (lane & 1) ? ((x & ~m1) | ((y >> 1) & m1)) : ((x & m1) | ((y & m1) << 1));
+    return x;
+}
+
+// Outcome of one channel word u: 0 = nothing, else the symbol bits (bit i =
+// symbol s0+i) as k+1 with k = floor(u*m/T).
+__device__ __forceinline__ uint32_t channel_bits(uint32_t u, uint32_t T, uint32_t kind)
+{
+    if (u >= T) return 0u;
+    if (kind == CK_DEP1) return (uint32_t)(((uint64_t)u * 3u) / T) + 1u;
+    if (kind == CK_DEP2) return (uint32_t)(((uint64_t)u * 15u) / T) + 1u;
+    return 1u;
+}
+
+// K4.  Block = 8 warps; warp = one 32-shot word; all channels in order.
+__global__ void __launch_bounds__(256) k_draw(const uint32_t *__restrict__ chT,
+                                              const uint8_t *__restrict__ chKind, int64_t nch,
+                                              int64_t nsym, uint64_t seed, uint64_t shot0,
+                                              int64_t nwords, uint32_t *__restrict__ B, int64_t bpitch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (w >= nwords) return;
+    const uint64_t shot = shot0 + (uint64_t)w * 32u + (uint64_t)lane;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32);
+    uint64_t acc = 0;
+    int fill = 0;
+    int64_t base = 0;  // 0-based symbol index of bit 0 of acc
+    for (int64_t cb = 0; cb * 4 < nch; cb++) {
+        uint32_t r[4];
+        philox4x32_10(c0, c1, (uint32_t)cb, 0u, k0, k1, r[0], r[1], r[2], r[3]);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t c = cb * 4 + i;
+            if (c >= nch) break;
+            const uint32_t kind = chKind[c];
+            const int k = kind == CK_DEP2 ? 4 : (kind == CK_DEP1 ? 2 : 1);
+            acc |= (uint64_t)channel_bits(r[i], chT[c], kind) << fill;
+            fill += k;
+            if (fill >= 32) {
+                const uint32_t col = warp_transpose32((uint32_t)acc, lane);
+                if (base + lane < nsym) B[(size_t)(base + lane) * bpitch + w] = col;
+                acc >>= 32;
+                fill -= 32;
+                base += 32;
+            }
+        }
+    }
+    if (fill > 0) {
+        const uint32_t col = warp_transpose32((uint32_t)acc, lane);
+        if (base + lane < nsym) B[(size_t)(base + lane) * bpitch + w] = col;
+    }
+}
+
+// K5.  Warp = 1024 shots (lane = 32-shot word); rows in order so a parent
+// is always finished (by the same lane) before its children.
+__global__ void __launch_bounds__(128) k_gather(const uint32_t *__restrict__ B, int64_t bpitch,
+                                                int64_t nwords, const uint32_t *__restrict__ rowOff,
+                                                const uint32_t *__restrict__ idx,
+                                                const int32_t *__restrict__ parent,
+                                                const uint8_t *__restrict__ cflag, int64_t nrows,
+                                                uint32_t *recT, int64_t rpitch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 + lane;
+    if (((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 >= nwords) return;
+    const bool ok = w < nwords;
+    const uint32_t *Bw = B + w;
+    for (int64_t j = 0; j < nrows; j++) {
+        uint32_t acc = cflag[j] ? FULLM : 0u;
+        const int32_t p = parent[j];
+        if (p >= 0 && ok) acc ^= recT[(size_t)p * rpitch + w];
+        const uint32_t e = rowOff[j + 1];
+        uint32_t k = rowOff[j];
+        uint32_t a1 = 0, a2 = 0, a3 = 0;
+        if (ok) {
+            for (; k + 4 <= e; k += 4) {
+                const uint32_t s0 = idx[k], s1 = idx[k + 1], s2 = idx[k + 2], s3 = idx[k + 3];
+                acc ^= Bw[(size_t)s0 * bpitch];
+                a1 ^= Bw[(size_t)s1 * bpitch];
+                a2 ^= Bw[(size_t)s2 * bpitch];
+                a3 ^= Bw[(size_t)s3 * bpitch];
+            }
+            for (; k < e; k++) acc ^= Bw[(size_t)idx[k] * bpitch];
+            recT[(size_t)j * rpitch + w] = acc ^ a1 ^ a2 ^ a3;
+        }
+    }
+}
+
+// K6.  Block = 256 threads; tile = 256 record rows x 8 words (256 shots).
+// Reads 32-byte row segments, transposes 32x32 blocks with warp shuffles and
+// writes 32 contiguous bytes per shot.
+__global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ recT, int64_t rpitch,
+                                              int64_t row0, int64_t nrows, int64_t nshots,
+                                              uint32_t *__restrict__ out, int64_t out_words32)
+{
+    __shared__ uint32_t in_t[256][9];
+    __shared__ uint32_t out_t[256][9];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t rb = (int64_t)blockIdx.y * 256;   // first row (segment-relative)
+    const int64_t wb = (int64_t)blockIdx.x * 8;     // first 32-shot word
+    const int64_t nwords = (nshots + 31) / 32;
+    {
+        const int64_t r = rb + t;
+        for (int k = 0; k < 8; k++) {
+            uint32_t v = 0;
+            if (r < nrows && wb + k < nwords) v = recT[(size_t)(row0 + r) * rpitch + wb + k];
+            in_t[t][k] = v;
+        }
+    }
+    __syncthreads();
+    // 64 (row group, word) blocks, 8 per warp
+    for (int q = warp; q < 64; q += 8) {
+        const int g = q >> 3, k = q & 7;
+        const uint32_t x = in_t[g * 32 + lane][k];
+        out_t[k * 32 + lane][g] = warp_transpose32(x, lane);
+    }
+    __syncthreads();
+    const int64_t shot = wb * 32 + t;
+    if (shot < nshots) {
+        const int64_t word0 = rb / 32;   // first u32 word of this row chunk
+        uint32_t *dst = out + (size_t)shot * out_words32 + word0;
+        for (int g = 0; g < 8; g++)
+            if (word0 + g < out_words32) dst[g] = out_t[t][g];
+    }
+}
+
+int64_t default_chunk(const sp_program *P)
+{
+    const double per_shot = (double)(P->n_sym + P->n_rows) / 8.0 + 64.0;
+    const double budget = 4.0e9;
+    int64_t c = (int64_t)(budget / per_shot);
+    c = std::min<int64_t>(c, (int64_t)1 << 20);
+    c = std::max<int64_t>(1024, (c / 1024) * 1024);
+    return c;
+}
+
+sp_status ensure_scratch(sp_program *P, size_t shots)
+{
+    if (P->scratch_shots >= shots && P->d_B && P->d_recT) return SP_OK;
+    cudaFree(P->d_B);
+    cudaFree(P->d_recT);
+    P->d_B = nullptr;
+    P->d_recT = nullptr;
+    P->scratch_shots = 0;
+    const size_t words = (shots + 31) / 32;
+    const size_t bsz = (size_t)std::max<int64_t>(P->n_sym, 1) * words * 4;
+    const size_t rsz = (size_t)std::max<int64_t>(P->n_rows, 1) * words * 4;
+    if (cudaMalloc((void **)&P->d_B, bsz) != cudaSuccess) {
+        cudaGetLastError();
+        P->d_B = nullptr;
+        return set_error(SP_ERR_OOM, "cudaMalloc of the fault-bit scratch failed");
+    }
+    if (cudaMalloc((void **)&P->d_recT, rsz) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(P->d_B);
+        P->d_B = nullptr;
+        P->d_recT = nullptr;
+        return set_error(SP_ERR_OOM, "cudaMalloc of the record scratch failed");
+    }
+    P->scratch_shots = words * 32;
+    return SP_OK;
+}
+
+sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                       uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s)
+{
+    if (nshots == 0) return SP_OK;
+    const int64_t nwords = (int64_t)((nshots + 31) / 32);
+    const int64_t pitch = (int64_t)((P->scratch_shots + 31) / 32);
+    if (P->n_sym > 0) {
+        ProfScope ps(P, SP_KERNEL_DRAW, s);
+        k_draw<<<(unsigned)ceil_div(nwords, 8), 256, 0, s>>>(P->d_chT, P->d_chKind, P->n_ch, P->n_sym,
+                                                               seed, shot0, nwords, P->d_B, pitch);
+        SP_CUDA(cudaGetLastError());
+    }
+    if (P->n_rows > 0) {
+        const int64_t warps = ceil_div(nwords, 32);
+        ProfScope ps(P, SP_KERNEL_PRODUCT, s);
+        k_gather<<<(unsigned)ceil_div(warps, 4), 128, 0, s>>>(P->d_B, pitch, nwords, P->d_rowOff, P->d_idx,
+                                                                P->d_parent, P->d_cflag, P->n_rows,
+                                                                P->d_recT, pitch);
+        SP_CUDA(cudaGetLastError());
+    }
+    struct Seg { uint64_t *dst; int64_t row0, n; } segs[3] = {
+        {d_meas, 0, P->n_meas}, {d_det, P->n_meas, P->n_det}, {d_obs, P->n_meas + P->n_det, P->n_obs}};
+    for (const Seg &g : segs) {
+        if (!g.dst || g.n == 0) continue;
+        const int64_t words32 = 2 * ceil_div(g.n, 64);
+        dim3 grid((unsigned)ceil_div(nwords, 8), (unsigned)ceil_div(words32 * 32, 256));
+        ProfScope ps(P, SP_KERNEL_EMIT, s);
+        k_emit<<<grid, 256, 0, s>>>(P->d_recT, pitch, g.row0, g.n, (int64_t)nshots,
+                                    reinterpret_cast<uint32_t *>(g.dst), words32);
+        SP_CUDA(cudaGetLastError());
+    }
+    return SP_OK;
+}
+
+}  // namespace sp

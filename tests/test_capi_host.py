@@ -1,0 +1,83 @@
+"""The C-ABI library without a GPU: it builds for sm_103a, loads, exports
+every entry point include/symphase.h declares, and rejects bad arguments
+on the host before touching CUDA."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_03906_gb300 import _build
+    _build.build()
+    from paper_2311_03906_gb300 import binding
+    return binding.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "symphase.h")).read()
+    return sorted(set(re.findall(r"SP_API\s+[\w\s\*]*?\b(sp_\w+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("sp_build", "sp_sample", "sp_expect", "sp_expect_grad", "sp_free", "sp_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2311_03906_gb300 import binding
+    names = _declared()
+    assert names, "no SP_API declarations found"
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in symphase.h but not exported"
+    assert set(names) == set(binding.EXPORTS)
+
+
+def _desc(binding, nq, ops):
+    keep = []
+    arr = (binding.sp_op * len(ops))()
+    for i, (code, tg, arg) in enumerate(ops):
+        t = (C.c_uint32 * max(1, len(tg)))(*tg)
+        keep.append(t)
+        arr[i].opcode, arr[i].ntargets = code, len(tg)
+        arr[i].targets = C.cast(t, C.POINTER(C.c_uint32))
+        arr[i].arg = arg
+    return binding.sp_circuit_desc(nq, len(ops), C.cast(arr, C.POINTER(binding.sp_op))), (arr, keep)
+
+
+@pytest.mark.parametrize("nq,ops,status", [
+    (2, [(2, [0, 0], 0.0)], 1),              # CX on one qubit
+    (2, [(0, [5], 0.0)], 1),                 # target out of range
+    (2, [(9, [0], 1.5)], 1),                 # probability > 1
+    (2, [(9, [0], -0.1)], 1),                # probability < 0
+    (2, [(13, [0, 1, 1], 0.1)], 1),          # odd DEPOLARIZE2 targets
+    (2, [(6, [0], 0.0), (14, [2], 0.0)], 1), # look-back beyond the records
+    (2, [(42, [0], 0.0)], 2),                # unknown opcode
+    (2000, [(0, [0], 0.0)], 7),              # too many qubits
+])
+def test_build_rejects_on_host(lib, nq, ops, status):
+    from paper_2311_03906_gb300 import binding
+    desc, keep = _desc(binding, nq, ops)
+    h = C.c_void_p()
+    st = lib.sp_build(C.byref(desc), None, C.byref(h))
+    assert st == status
+    assert not h.value
+    assert lib.sp_last_error()
+
+
+def test_null_arguments(lib):
+    h = C.c_void_p()
+    assert lib.sp_build(None, None, C.byref(h)) == 1
+    assert lib.sp_info(None, None) == 1
+    assert lib.sp_sample(None, 0, 0, 10, None, None, None, None) == 1
+    assert lib.sp_expect(None, None, None, None) == 1
+    assert lib.sp_expect_grad(None, None, None, None, None) == 1
+    assert lib.sp_export_rows(None, 0, None, 1) == 1
+    assert lib.sp_set_chunk(None, 1024) == 1
+    lib.sp_free(None)
+    assert b"NULL" in lib.sp_last_error()

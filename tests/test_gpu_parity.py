@@ -1,0 +1,231 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Integer/bit work (coefficient rows, channel tables, records) must be
+bit-exact. FP32 expectations: relative error <= 1e-4 on log|E| against the
+FP64 oracle; gradients <= 1e-4 against the oracle's analytic adjoint and
+<= 1e-3 against FP64 central differences (h = 1e-6)."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import (Circuit, random_layered, random_small_circuit, repetition_code,
+                       surface_code)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2311_03906_gb300 as sp  # noqa: E402
+
+
+def _fig1():
+    c = Circuit(4)
+    c.append("H", [0]); c.append("CX", [0, 1, 1, 2, 2, 3])
+    c.append("Z_ERROR", [0], 0.1); c.append("X_ERROR", [1, 2, 3], 0.1)
+    c.append("CX", [2, 3, 1, 2, 0, 1]); c.append("H", [0]); c.append("M", [0, 1, 2, 3])
+    return c
+
+
+def _sec31():
+    c = Circuit(2)
+    c.append("H", [0]); c.append("CX", [0, 1]); c.append("X_ERROR", [0], 0.1)
+    c.append("X_ERROR", [1], 0.1); c.append("M", [0, 1])
+    return c
+
+
+CIRCUITS = {
+    "fig1": _fig1,
+    "sec31": _sec31,
+    "rep5": lambda: repetition_code(5, 5, 0.01),
+    "surf3": lambda: surface_code(3, 3, 1e-2),
+    "surf5": lambda: surface_code(5, 5, 2e-3),
+    "layered40": lambda: random_layered(40, 40, depolarize=0.01, seed=3),
+    "wide1000": lambda: random_layered(1000, 3, cnot_pairs=500, depolarize=0.001, seed=4),
+}
+for _s in range(8):
+    CIRCUITS[f"rand{_s}"] = (lambda s=_s: random_small_circuit(3 + 7 * s, 60 + 30 * s, seed=900 + s))
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+@pytest.fixture(scope="module")
+def d11():
+    c = surface_code(11, 11, 1e-3)
+    return c, sp.build(c), oracle.Program(c)
+
+
+@pytest.mark.parametrize("name", sorted(CIRCUITS))
+def test_rows_match_oracle(name):
+    c = CIRCUITS[name]()
+    prog, ref = sp.build(c), oracle.Program(c)
+    assert (prog.num_measurements, prog.num_detectors, prog.num_observables) == \
+        (ref.num_meas, ref.num_det, ref.num_obs)
+    assert prog.num_symbols == ref.num_symbols and prog.num_channels == ref.num_channels
+    w = (ref.num_symbols + 1 + 63) // 64
+    for which in ("meas", "det", "obs"):
+        np.testing.assert_array_equal(prog.rows(which)[:, :w], ref.rows(which)[:, :w], err_msg=which)
+    T, kind, s0 = prog.channels()
+    ch = ref.channels()
+    np.testing.assert_array_equal(T, ch.T)
+    np.testing.assert_array_equal(s0, ch.sym0)
+    want_kind = np.select([ch.type == 3, ch.type == 4, ch.type == 5], [1, 2, 3], 0)
+    np.testing.assert_array_equal(kind, want_kind)
+
+
+@pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "rand3", "rand7"])
+@pytest.mark.parametrize("shot0,shots", [(0, 1), (5, 31), (64, 33), (1 << 33, 1061), (7, 4101)])
+def test_records_match_oracle(name, shot0, shots):
+    c = CIRCUITS[name]()
+    prog, ref = sp.build(c), oracle.Program(c)
+    m, d, o = prog.sample(shots, seed=17, shot0=shot0)
+    torch.cuda.synchronize()
+    rm, rd, ro = ref.sample(17, shot0, shots)
+    np.testing.assert_array_equal(_u64(m), rm)
+    np.testing.assert_array_equal(_u64(d), rd)
+    np.testing.assert_array_equal(_u64(o), ro)
+
+
+def test_chunking_and_host_path_give_identical_records():
+    c = surface_code(5, 5, 5e-3)
+    prog = sp.build(c)
+    shots = 10_000
+    m0, d0, o0 = prog.sample(shots, seed=3, shot0=11)
+    prog.set_chunk(1024)
+    m1, d1, o1 = prog.sample(shots, seed=3, shot0=11)
+    hm, hd, ho = prog.sample_host(shots, seed=3, shot0=11)
+    torch.cuda.synchronize()
+    for a, b, h in ((m0, m1, hm), (d0, d1, hd), (o0, o1, ho)):
+        assert torch.equal(a, b)
+        assert torch.equal(a.cpu(), h)
+    # a sub-range equals the matching rows of the full range
+    m2, _, _ = prog.sample(100, seed=3, shot0=11 + 5000)
+    assert torch.equal(m2, m0[5000:5100])
+
+
+def test_full_size_d11_sampled_shots(d11):
+    """The d=11 r=11 p=1e-3 configuration at 1e6 shots in the launch
+    configuration the benchmark times; 300 shots spread over the range are
+    recomputed one by one by the oracle."""
+    c, prog, ref = d11
+    shots = 1_000_000
+    m, d, o = prog.sample(shots, seed=1, shot0=0)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    pick = np.unique(np.concatenate([rng.integers(0, shots, 296), [0, 31, 32, shots - 1]]))
+    rm, rd, ro = ref.sample_shots(1, pick)
+    idx = torch.as_tensor(pick, device="cuda")
+    np.testing.assert_array_equal(_u64(m[idx]), rm)
+    np.testing.assert_array_equal(_u64(d[idx]), rd)
+    np.testing.assert_array_equal(_u64(o[idx]), ro)
+    # pad bits beyond the last record are zero in every shot
+    nm = prog.num_measurements
+    pad_mask = np.uint64(~((1 << (nm % 64)) - 1) & 0xFFFFFFFFFFFFFFFF) if nm % 64 else np.uint64(0)
+    last = _u64(m[:, -1])
+    assert not np.any(last & pad_mask)
+
+
+def test_full_size_d11_detector_rates(d11):
+    """Monte-Carlo detector rates of 1e6 GPU shots against the analytic
+    expectation, within 5 sigma."""
+    c, prog, ref = d11
+    shots = 1_000_000
+    _, d, _ = prog.sample(shots, seed=2, shot0=0, meas=False, obs=False)
+    bits = torch.zeros(prog.num_detectors, dtype=torch.float64, device="cuda")
+    dd = d.view(torch.int64)
+    for j in range(prog.num_detectors):
+        bits[j] = ((dd[:, j // 64] >> (j % 64)) & 1).sum()
+    rates = (bits / shots).cpu().numpy()
+    la = prog.expect_raw().cpu().numpy()[: prog.num_detectors].astype(np.float64)
+    r = (1 - np.exp(la)) / 2
+    z = np.abs(rates - r) / np.sqrt(r * (1 - r) / shots)
+    assert z.max() < 5.0, z.max()
+
+
+@pytest.mark.parametrize("name", ["rep5", "surf3", "surf5", "rand5"])
+def test_expectation_matches_oracle(name):
+    c = CIRCUITS[name]()
+    prog, ref = sp.build(c), oracle.Program(c)
+    if prog.num_detectors + prog.num_observables == 0:
+        pytest.skip("no detectors")
+    rng = np.random.default_rng(1)
+    p = rng.uniform(5e-4, 2e-3, prog.num_channels).astype(np.float32)
+    got = prog.expect_raw(torch.as_tensor(p, device="cuda")).cpu().numpy().astype(np.float64)
+    la, _ = ref.expect(p.astype(np.float64))
+    np.testing.assert_allclose(got, la, rtol=1e-4, atol=1e-7)
+
+
+def test_expectation_d11_and_gradient(d11):
+    c, prog, ref = d11
+    rng = np.random.default_rng(5)
+    p = rng.uniform(5e-4, 2e-3, prog.num_channels).astype(np.float32)
+    pt = torch.as_tensor(p, device="cuda")
+    got = prog.expect_raw(pt).cpu().numpy().astype(np.float64)
+    la, _ = ref.expect(p.astype(np.float64))
+    np.testing.assert_allclose(got, la, rtol=1e-4)
+    g = rng.normal(size=prog.num_detectors + prog.num_observables).astype(np.float32)
+    grad = prog.expect_grad_raw(pt, torch.as_tensor(g, device="cuda")).cpu().numpy().astype(np.float64)
+    want = ref.expect_vjp(p.astype(np.float64), g.astype(np.float64))
+    scale = np.abs(want).max()
+    np.testing.assert_allclose(grad, want, rtol=1e-4, atol=1e-4 * scale)
+    # central differences of the FP64 oracle on 64 channels
+    h = 1e-6
+    p64 = p.astype(np.float64)
+    for ch in rng.choice(prog.num_channels, 64, replace=False):
+        if want[ch] == 0:
+            continue
+        pp, pm = p64.copy(), p64.copy()
+        pp[ch] += h
+        pm[ch] -= h
+        fd = (ref.expect(pp)[0] @ g - ref.expect(pm)[0] @ g) / (2 * h)
+        assert abs(grad[ch] - fd) <= 1e-3 * abs(fd) + 1e-6 * scale, (ch, grad[ch], fd)
+
+
+def test_autograd_function(d11):
+    c, prog, ref = d11
+    rng = np.random.default_rng(9)
+    p = torch.tensor(rng.uniform(5e-4, 2e-3, prog.num_channels), dtype=torch.float32,
+                     device="cuda", requires_grad=True)
+    target = torch.rand(prog.num_detectors + prog.num_observables, device="cuda") * 0.02
+    logE = sp.expect(prog, p)
+    r = (1 - torch.exp(logE)) / 2
+    loss = ((r - target) ** 2).sum()
+    loss.backward()
+    g = (2 * (r - target) * (-0.5) * torch.exp(logE)).detach().cpu().numpy().astype(np.float64)
+    want = ref.expect_vjp(p.detach().cpu().numpy().astype(np.float64), g)
+    got = p.grad.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, want, rtol=1e-3, atol=1e-4 * np.abs(want).max())
+
+
+def test_nondeterministic_detector_is_rejected():
+    c = Circuit(2)
+    c.append("H", [0]); c.append("M", [0]); c.append("DETECTOR", [1])
+    with pytest.raises(sp.SymPhaseError) as e:
+        sp.build(c)
+    assert e.value.status == 3
+
+
+def test_noiseless_and_symbol_free_circuits():
+    c = Circuit(3)
+    c.append("X", [1]); c.append("CX", [1, 2]); c.append("M", [0, 1, 2])
+    c.append("DETECTOR", [1, 2]); c.append("OBSERVABLE_INCLUDE", [1], 0)
+    prog = sp.build(c)
+    assert prog.num_symbols == 0
+    m, d, o = prog.sample(100, seed=1)
+    torch.cuda.synchronize()
+    assert np.all(_u64(m)[:, 0] == 0b110)
+    assert np.all(_u64(d)[:, 0] == 0)
+    assert np.all(_u64(o)[:, 0] == 1)
+
+
+def test_zero_shots_and_null_outputs():
+    prog = sp.build(repetition_code(3, 2, 0.1))
+    prog.sample(0, seed=1)
+    m, d, o = prog.alloc_outputs(50)
+    prog.sample(50, seed=1, out=(m, d, o), meas=False, obs=False)
+    torch.cuda.synchronize()
+    ref = oracle.Program(repetition_code(3, 2, 0.1))
+    np.testing.assert_array_equal(_u64(d), ref.sample(1, 0, 50)[1])
