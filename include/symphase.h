@@ -162,6 +162,33 @@ SP_API sp_status sp_sample_host(sp_program *prog, uint64_t seed, uint64_t shot0,
                          uint64_t *h_meas, uint64_t *h_det, uint64_t *h_obs, void *cuda_stream);
 
 /*
+ * sp_sample_static -- the records of sp_sample (same arguments, layout and
+ * bits) computed without allocating any memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a process whose GPU memory is already reserved in full by
+ * another allocator (a caching allocator or a pool that owns the device),
+ * a latency-critical path that cannot accept an allocation's implicit
+ * device synchronisation, or a host application that forbids its plugins to
+ * allocate device memory.
+ *   Scratch: one fixed 32 MiB device array, reserved on every GPU that
+ *   loads the library and held until the process exits.  Shots are
+ *   processed in chunks of as many 32-shot words as fit:
+ *   32 * floor(8 Mi / (num_symbols + num_rows)) shots per chunk.
+ *   Limit: a program with num_symbols + num_rows > 8,388,608 (more than
+ *   32 MiB per 32 shots) is rejected with SP_ERR_TOO_LARGE.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make
+ *   that first call before any stream capture on the device.
+ *   Sharing: every call on a device uses the same array and leaves its last
+ *   contents there.  Calls whose work overlaps on the GPU (different
+ *   streams, or different host threads) race on it and must be ordered by
+ *   the caller; calls on one stream are ordered by the stream.
+ * Errors: INVALID_ARG (NULL prog, misaligned pointer), TOO_LARGE, CUDA.
+ */
+SP_API sp_status sp_sample_static(sp_program *prog, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                                  uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, void *cuda_stream);
+
+/*
  * sp_sample_batch -- many programs (uneven sizes, shot counts, seeds) in one
  * enqueue.  Program i samples shots 0..nshots[i]-1 with seeds[i] into
  * d_meas[i], d_det[i], d_obs[i] (entries may be NULL).  The work of all

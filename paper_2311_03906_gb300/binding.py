@@ -25,7 +25,8 @@ OPCODES = {"H": 0, "S": 1, "CX": 2, "X": 3, "Y": 4, "Z": 5, "M": 6, "MR": 7, "R"
 PATH_AUTO, PATH_SPARSE, PATH_DENSE = 0, 1, 2
 
 # every entry point declared in include/symphase.h
-EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_batch", "sp_expect",
+EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",
+           "sp_sample_batch", "sp_expect",
            "sp_expect_grad", "sp_export_rows", "sp_export_channels", "sp_set_path", "sp_set_chunk",
            "sp_profile_enable", "sp_profile_read", "sp_free", "sp_last_error")
 KERNEL_CLASSES = ("draw", "product", "emit", "fused")
@@ -76,6 +77,7 @@ def load() -> C.CDLL:
     lib.sp_info.argtypes = [vp, C.POINTER(sp_info_t)]
     lib.sp_sample.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
     lib.sp_sample_host.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
+    lib.sp_sample_static.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
     lib.sp_sample_batch.argtypes = [vp, u32, vp, vp, vp, vp, vp, vp]
     lib.sp_expect.argtypes = [vp, vp, vp, vp]
     lib.sp_expect_grad.argtypes = [vp, vp, vp, vp, vp]
@@ -202,6 +204,14 @@ class Program:
         m, d, o = out if out is not None else self.alloc_outputs(shots, device="cpu", pin_memory=True)
         _check(self._lib.sp_sample_host(self._h, seed, shot0, shots, _ptr(m), _ptr(d), _ptr(o),
                                         C.c_void_p(_stream_handle(stream))))
+        return m, d, o
+
+    def sample_static(self, shots: int, seed: int = 0, shot0: int = 0, out=None, stream=None):
+        """Like sample(), but the library allocates nothing: it works in its
+        fixed per-device scratch array (for callers that cannot allocate)."""
+        m, d, o = out if out is not None else self.alloc_outputs(shots)
+        _check(self._lib.sp_sample_static(self._h, seed, shot0, shots, _ptr(m), _ptr(d), _ptr(o),
+                                          C.c_void_p(_stream_handle(stream))))
         return m, d, o
 
     def set_path(self, path: int):

@@ -148,6 +148,9 @@ sp_status ensure_scratch(sp_program *P, size_t shots);
 sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
                        uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
 int64_t default_chunk(const sp_program *P);
+sp_status sample_chunk_into(const sp_program *P, uint32_t *B, uint32_t *recT, int64_t pitch,
+                            uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
+                            uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
 
 // expectation (sp_expect.cu)
 sp_status expect_fwd(sp_program *P, const float *d_p, float *d_logE, cudaStream_t s);

@@ -181,6 +181,41 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ recT,
     }
 }
 
+// The same three launches as sample_chunk, on caller-provided scratch:
+// B (n_sym rows) and recT (n_rows rows), both with `pitch` 32-shot words per
+// row; nshots must not exceed 32 * pitch.  Used by the entry point that
+// allocates nothing.
+sp_status sample_chunk_into(const sp_program *P, uint32_t *B, uint32_t *recT, int64_t pitch,
+                            uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
+                            uint64_t *d_det, uint64_t *d_obs, cudaStream_t s)
+{
+    if (nshots == 0) return SP_OK;
+    const int64_t nwords = (int64_t)((nshots + 31) / 32);
+    if (nwords > pitch) return set_error(SP_ERR_INVALID_ARG, "chunk larger than the scratch pitch");
+    if (P->n_sym > 0) {
+        k_draw<<<(unsigned)ceil_div(nwords, 8), 256, 0, s>>>(P->d_chT, P->d_chKind, P->n_ch, P->n_sym,
+                                                               seed, shot0, nwords, B, pitch);
+        SP_CUDA(cudaGetLastError());
+    }
+    if (P->n_rows > 0) {
+        const int64_t warps = ceil_div(nwords, 32);
+        k_gather<<<(unsigned)ceil_div(warps, 4), 128, 0, s>>>(B, pitch, nwords, P->d_rowOff, P->d_idx,
+                                                                P->d_parent, P->d_cflag, P->n_rows, recT, pitch);
+        SP_CUDA(cudaGetLastError());
+    }
+    struct Seg { uint64_t *dst; int64_t row0, n; } segs[3] = {
+        {d_meas, 0, P->n_meas}, {d_det, P->n_meas, P->n_det}, {d_obs, P->n_meas + P->n_det, P->n_obs}};
+    for (const Seg &g : segs) {
+        if (!g.dst || g.n == 0) continue;
+        const int64_t words32 = 2 * ceil_div(g.n, 64);
+        dim3 grid((unsigned)ceil_div(nwords, 8), (unsigned)ceil_div(words32 * 32, 256));
+        k_emit<<<grid, 256, 0, s>>>(recT, pitch, g.row0, g.n, (int64_t)nshots,
+                                    reinterpret_cast<uint32_t *>(g.dst), words32);
+        SP_CUDA(cudaGetLastError());
+    }
+    return SP_OK;
+}
+
 int64_t default_chunk(const sp_program *P)
 {
     const double per_shot = (double)(P->n_sym + P->n_rows) / 8.0 + 64.0;
