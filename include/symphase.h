@@ -98,7 +98,8 @@ typedef struct {
 enum {
     SP_PATH_AUTO = 0,      /* chosen at build time from the measured density */
     SP_PATH_SPARSE = 1,    /* symbol-index XOR gather over bit-sliced shots */
-    SP_PATH_DENSE = 2      /* 64-bit AND/popcount parity over shot-major words */
+    SP_PATH_DENSE = 2,     /* 64-bit AND/popcount parity over shot-major words */
+    SP_PATH_FUSED = 3      /* draw + sparse product + epilogue in one kernel, tile in shared memory */
 };
 
 typedef struct {
@@ -113,7 +114,7 @@ typedef struct {
     uint64_t nnz_delta;            /* after parent-delta encoding */
     uint64_t log_words;            /* length of the traversal's row-operation log */
     double density;                /* nnz_rows / (rows * n_s) */
-    int32_t path;                  /* SP_PATH_SPARSE or SP_PATH_DENSE */
+    int32_t path;                  /* SP_PATH_SPARSE, SP_PATH_DENSE or SP_PATH_FUSED */
     int32_t reserved;
     uint64_t chunk_shots;          /* shots per internal sampling chunk */
     double build_ms;               /* wall time of sp_build */

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "SP_OK", 1: "SP_ERR_INVALID_ARG", 2: "SP_ERR_UNSUPPORTED_OP",
 OPCODES = {"H": 0, "S": 1, "CX": 2, "X": 3, "Y": 4, "Z": 5, "M": 6, "MR": 7, "R": 8,
            "X_ERROR": 9, "Y_ERROR": 10, "Z_ERROR": 11, "DEPOLARIZE1": 12, "DEPOLARIZE2": 13,
            "DETECTOR": 14, "OBSERVABLE_INCLUDE": 15, "TICK": 16}
-PATH_AUTO, PATH_SPARSE, PATH_DENSE = 0, 1, 2
+PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED = 0, 1, 2, 3
 
 # every entry point declared in include/symphase.h
 EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",

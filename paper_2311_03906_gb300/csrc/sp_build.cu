@@ -821,6 +821,8 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
         xrefs.insert(xrefs.end(), o.begin(), o.end());
         xoff.push_back((uint32_t)xrefs.size());
     }
+    P->h_xoff = xoff;
+    P->h_xrefs = xrefs;
     const int64_t ntgt = P->n_det + P->n_obs;
     if (ntgt > 0) {
         uint32_t *d_xoff, *d_xrefs;
@@ -924,7 +926,8 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     SP_CUDA(cudaStreamSynchronize(stream));
     const double cells = (double)std::max<int64_t>(R, 1) * (double)std::max<int64_t>(P->n_sym, 1);
     P->density = (double)P->nnz_rows / cells;
-    P->build_path = SP_PATH_SPARSE;
+    SP_TRY(build_fused_program(P, stream));
+    P->build_path = P->fused_tw ? SP_PATH_FUSED : SP_PATH_SPARSE;
     P->path = P->build_path;
     P->chunk_shots = default_chunk(P);
     P->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

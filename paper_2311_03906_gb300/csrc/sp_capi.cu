@@ -31,7 +31,9 @@ static void release(sp_program *P)
     if (cur != P->device) cudaSetDevice(P->device);
     void *bufs[] = {P->d_A, P->d_chT, P->d_chKind, P->d_chP, P->d_chSym0, P->d_rowOff, P->d_idx,
                     P->d_parent, P->d_cflag, P->d_A64, P->d_const, P->d_inc, P->d_incT, P->d_kappa,
-                    P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage};
+                    P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta,
+                    P->d_blkSym0, P->d_fRowMeta, P->d_fAOff, P->d_fChain, P->d_fBOff, P->d_fCOff,
+                    P->d_fCRefs, P->d_fIdx4};
     for (void *b : bufs) if (b) cudaFree(b);
     if (P->h_stage) cudaFreeHost(P->h_stage);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -136,6 +138,8 @@ sp_status sp_sample(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshot
     if (nshots == 0) return SP_OK;
     if (shot0 + nshots < shot0) return set_error(SP_ERR_INVALID_ARG, "shot range overflows 64 bits");
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (P->path == SP_PATH_FUSED && P->fused_tw)
+        return fused_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     const int64_t chunk = P->chunk_shots;
     st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)chunk));
     if (st != SP_OK) return st;
@@ -162,8 +166,11 @@ sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t 
     // pipeline granularity: at most the sampling chunk, at most 64 MiB of records
     int64_t piece = std::min<int64_t>(P->chunk_shots, std::max<int64_t>(1024, (64 << 20) / std::max<int64_t>(per_shot * 8, 8)));
     piece = std::max<int64_t>(1024, (piece / 1024) * 1024);
-    sp_status st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)piece));
-    if (st != SP_OK) return st;
+    sp_status st = SP_OK;
+    if (!(P->path == SP_PATH_FUSED && P->fused_tw)) {
+        st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)piece));
+        if (st != SP_OK) return st;
+    }
     const size_t stage_words = (size_t)piece * (size_t)per_shot;
     if (P->d_out_stage_bytes < 2 * stage_words * 8) {
         if (P->d_out_stage) cudaFree(P->d_out_stage);
@@ -272,7 +279,9 @@ sp_status sp_set_path(sp_program *P, int32_t path)
 {
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
     if (path == SP_PATH_AUTO) { P->path = P->build_path; return SP_OK; }
-    if (path != SP_PATH_SPARSE) return set_error(SP_ERR_INVALID_ARG, "unsupported path");
+    if (path == SP_PATH_FUSED && !P->fused_tw)
+        return set_error(SP_ERR_INVALID_ARG, "the fused tile of this program does not fit in shared memory");
+    if (path != SP_PATH_SPARSE && path != SP_PATH_FUSED) return set_error(SP_ERR_INVALID_ARG, "unsupported path");
     P->path = path;
     return SP_OK;
 }

@@ -8,7 +8,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/symphase.h"
+#include "symphase.h"
 
 namespace sp {
 
@@ -105,6 +105,9 @@ struct sp_program {
     double density = 0.0;
     // host-side copies used for host entry points and batching
     std::vector<uint8_t> h_const;
+    // detector/observable definitions: target t = XOR of measurement rows
+    // h_xrefs[h_xoff[t] .. h_xoff[t+1])
+    std::vector<uint32_t> h_xoff, h_xrefs;
     // pinned host staging for sp_sample_host (allocated lazily)
     void *h_stage = nullptr;
     size_t h_stage_bytes = 0;
@@ -112,6 +115,27 @@ struct sp_program {
     size_t d_out_stage_bytes = 0;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // draw descriptors: blocks of 4 channels (thresholds, kinds/offsets, first symbol)
+    int64_t n_blk = 0;
+    uint4 *d_blkT = nullptr;
+    uint32_t *d_blkMeta = nullptr;
+    uint32_t *d_blkSym0 = nullptr;
+    // fused product program (three steps, see sp_fused.cu)
+    uint4 *d_fRowMeta = nullptr;      // step A items {group offset, groups, row, const flag}, per thread
+    uint32_t *d_fAOff = nullptr;      // [threads+1]
+    uint2 *d_fChain = nullptr;        // step B items (row, parent), per thread, parents first
+    uint32_t *d_fBOff = nullptr;      // [threads+1]
+    uint32_t *d_fCOff = nullptr;      // step C: target t = XOR of measurement rows d_fCRefs[off[t]..off[t+1])
+    uint32_t *d_fCRefs = nullptr;
+    uint4 *d_fIdx4 = nullptr;
+    int64_t fused_idx4 = 0;
+    bool fused_idx16 = false;        // 16-bit symbol indices (n_sym < 65535)
+    double fused_max_load = 0.0;     // largest per-thread product load (index groups + rows)
+    int fused_tw = 0;                 // shots per tile / 32 (0 = tile does not fit)
+    size_t fused_smem = 0;
+    uint32_t fused_rec_off = 0;
+    int fused_ctas_per_sm = 1;
+    int num_sms = 0;
     // per-kernel event profiling (sp_profile_enable)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -148,6 +172,12 @@ sp_status ensure_scratch(sp_program *P, size_t shots);
 sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
                        uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
 int64_t default_chunk(const sp_program *P);
+// fused path (sp_fused.cu)
+sp_status build_fused_program(sp_program *P, cudaStream_t s);
+sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
+                      uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
+sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *B,
+                             int64_t pitch, cudaStream_t s);
 sp_status sample_chunk_into(const sp_program *P, uint32_t *B, uint32_t *recT, int64_t pitch,
                             uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
                             uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);

@@ -2,10 +2,11 @@
 // Sec. 3.2.3, Eq. sampling): draw b for every shot from the noise model,
 // then M = [m_1; ...; m_nm] . [b_1 ... b_nsmp] over GF(2).
 //
-//   K4 k_draw     Philox4x32-10 per (seed, shot, channel/4); lane = shot; the
-//                 channel's symbol bits (Sec. 3.1 distributions) are packed
-//                 32 symbols at a time and transposed across the warp into
-//                 bit-sliced words B[s-1][shot/32] (bit = shot % 32).
+//   K4 k_draw_staged (sp_fused.cu)  Philox4x32-10 per (seed, shot,
+//                 channel/4); lane = shot; the channel's symbol bits (Sec. 3.1
+//                 distributions) are packed 32 symbols at a time and
+//                 transposed across the warp into bit-sliced words
+//                 B[s-1][shot/32] (bit = shot % 32).
 //   K5 k_gather   the GF(2) product in sparse form: record row j of a
 //                 32-shot word is c'_j ^ rec[parent(j)] ^ XOR_{s in delta_j}
 //                 B[s-1], lane = 32-shot word, so every index load is shared
@@ -21,28 +22,6 @@ namespace sp {
 
 constexpr uint32_t FULLM = 0xffffffffu;
 
-__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                              uint32_t k0, uint32_t k1, uint32_t &o0, uint32_t &o1,
-                                              uint32_t &o2, uint32_t &o3)
-{
-    // Salmon et al. (SC'11): per round (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2,
-    // c <- (hi1^c1^k0, lo1, hi0^c3^k1, lo0); key += Weyl constants.
-#pragma unroll
-    for (int r = 0; r < 10; r++) {
-        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
-        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
-        c0 = n0;
-        c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o0 = c0; o1 = c1; o2 = c2; o3 = c3;
-}
-
 // 32x32 bit transpose across a warp: in lane l holds row l (bit j = M[l][j]);
 // out lane j holds column j (bit l = M[l][j]).
 __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
@@ -55,57 +34,6 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
     y = __shfl_xor_sync(FULLM, x, 2);  x = (lane & 2) ? ((x & ~m2) | ((y >> 2) & m2)) : ((x & m2) | ((y & m2) << 2));
     y = __shfl_xor_sync(FULLM, x, 1);  x = (lane & 1) ? ((x & ~m1) | ((y >> 1) & m1)) : ((x & m1) | ((y & m1) << 1));
     return x;
-}
-
-// Outcome of one channel word u: 0 = nothing, else the symbol bits (bit i =
-// symbol s0+i) as k+1 with k = floor(u*m/T).
-__device__ __forceinline__ uint32_t channel_bits(uint32_t u, uint32_t T, uint32_t kind)
-{
-    if (u >= T) return 0u;
-    if (kind == CK_DEP1) return (uint32_t)(((uint64_t)u * 3u) / T) + 1u;
-    if (kind == CK_DEP2) return (uint32_t)(((uint64_t)u * 15u) / T) + 1u;
-    return 1u;
-}
-
-// K4.  Block = 8 warps; warp = one 32-shot word; all channels in order.
-__global__ void __launch_bounds__(256) k_draw(const uint32_t *__restrict__ chT,
-                                              const uint8_t *__restrict__ chKind, int64_t nch,
-                                              int64_t nsym, uint64_t seed, uint64_t shot0,
-                                              int64_t nwords, uint32_t *__restrict__ B, int64_t bpitch)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (w >= nwords) return;
-    const uint64_t shot = shot0 + (uint64_t)w * 32u + (uint64_t)lane;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32);
-    uint64_t acc = 0;
-    int fill = 0;
-    int64_t base = 0;  // 0-based symbol index of bit 0 of acc
-    for (int64_t cb = 0; cb * 4 < nch; cb++) {
-        uint32_t r[4];
-        philox4x32_10(c0, c1, (uint32_t)cb, 0u, k0, k1, r[0], r[1], r[2], r[3]);
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int64_t c = cb * 4 + i;
-            if (c >= nch) break;
-            const uint32_t kind = chKind[c];
-            const int k = kind == CK_DEP2 ? 4 : (kind == CK_DEP1 ? 2 : 1);
-            acc |= (uint64_t)channel_bits(r[i], chT[c], kind) << fill;
-            fill += k;
-            if (fill >= 32) {
-                const uint32_t col = warp_transpose32((uint32_t)acc, lane);
-                if (base + lane < nsym) B[(size_t)(base + lane) * bpitch + w] = col;
-                acc >>= 32;
-                fill -= 32;
-                base += 32;
-            }
-        }
-    }
-    if (fill > 0) {
-        const uint32_t col = warp_transpose32((uint32_t)acc, lane);
-        if (base + lane < nsym) B[(size_t)(base + lane) * bpitch + w] = col;
-    }
 }
 
 // K5.  Warp = 1024 shots (lane = 32-shot word); rows in order so a parent
@@ -193,9 +121,8 @@ sp_status sample_chunk_into(const sp_program *P, uint32_t *B, uint32_t *recT, in
     const int64_t nwords = (int64_t)((nshots + 31) / 32);
     if (nwords > pitch) return set_error(SP_ERR_INVALID_ARG, "chunk larger than the scratch pitch");
     if (P->n_sym > 0) {
-        k_draw<<<(unsigned)ceil_div(nwords, 8), 256, 0, s>>>(P->d_chT, P->d_chKind, P->n_ch, P->n_sym,
-                                                               seed, shot0, nwords, B, pitch);
-        SP_CUDA(cudaGetLastError());
+        sp_status st = launch_draw_staged(P, seed, shot0, nwords, B, pitch, s);
+        if (st != SP_OK) return st;
     }
     if (P->n_rows > 0) {
         const int64_t warps = ceil_div(nwords, 32);
@@ -259,11 +186,12 @@ sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t ns
     if (nshots == 0) return SP_OK;
     const int64_t nwords = (int64_t)((nshots + 31) / 32);
     const int64_t pitch = (int64_t)((P->scratch_shots + 31) / 32);
+    if (P->path == SP_PATH_FUSED && P->fused_tw)
+        return fused_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     if (P->n_sym > 0) {
         ProfScope ps(P, SP_KERNEL_DRAW, s);
-        k_draw<<<(unsigned)ceil_div(nwords, 8), 256, 0, s>>>(P->d_chT, P->d_chKind, P->n_ch, P->n_sym,
-                                                               seed, shot0, nwords, P->d_B, pitch);
-        SP_CUDA(cudaGetLastError());
+        sp_status st = launch_draw_staged(P, seed, shot0, nwords, P->d_B, pitch, s);
+        if (st != SP_OK) return st;
     }
     if (P->n_rows > 0) {
         const int64_t warps = ceil_div(nwords, 32);

@@ -76,11 +76,16 @@ def test_rows_match_oracle(name):
     np.testing.assert_array_equal(kind, want_kind)
 
 
-@pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "rand3", "rand7"])
+@pytest.mark.parametrize("path", ["fused", "staged"])
+@pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "wide1000", "rand3", "rand7"])
 @pytest.mark.parametrize("shot0,shots", [(0, 1), (5, 31), (64, 33), (1 << 33, 1061), (7, 4101)])
-def test_records_match_oracle(name, shot0, shots):
+def test_records_match_oracle(name, shot0, shots, path):
     c = CIRCUITS[name]()
     prog, ref = sp.build(c), oracle.Program(c)
+    if path == "staged":
+        prog.set_path(sp.PATH_SPARSE)
+    else:
+        assert prog.info["path"] == sp.PATH_FUSED, "small circuits take the fused path"
     m, d, o = prog.sample(shots, seed=17, shot0=shot0)
     torch.cuda.synchronize()
     rm, rd, ro = ref.sample(17, shot0, shots)
@@ -126,6 +131,43 @@ def test_full_size_d11_sampled_shots(d11):
     pad_mask = np.uint64(~((1 << (nm % 64)) - 1) & 0xFFFFFFFFFFFFFFFF) if nm % 64 else np.uint64(0)
     last = _u64(m[:, -1])
     assert not np.any(last & pad_mask)
+
+
+@pytest.mark.parametrize("path", ["fused", "staged"])
+def test_full_size_d11_both_paths_agree(d11, path):
+    c, prog, ref = d11
+    prog.set_path(sp.PATH_FUSED if path == "fused" else sp.PATH_SPARSE)
+    try:
+        m, d, o = prog.sample(200_000, seed=4, shot0=999)
+        torch.cuda.synchronize()
+        pick = np.array([0, 1, 31, 32, 63, 64, 65, 1023, 1024, 99_999, 150_001, 199_999])
+        rm, rd, ro = ref.sample_shots(4, pick + 999)
+        idx = torch.as_tensor(pick, device="cuda")
+        np.testing.assert_array_equal(_u64(m[idx]), rm)
+        np.testing.assert_array_equal(_u64(d[idx]), rd)
+        np.testing.assert_array_equal(_u64(o[idx]), ro)
+    finally:
+        prog.set_path(sp.PATH_AUTO)
+
+
+def test_full_size_d17_in_64k_chunks():
+    """d=17 r=17 p=2e-3 (the staged path: its fault tile does not fit in
+    shared memory), 1e6 shots sampled in 65536-shot chunks; 48 shots spread
+    over the range are recomputed by the oracle."""
+    c = surface_code(17, 17, 2e-3)
+    prog, ref = sp.build(c), oracle.Program(c)
+    assert prog.info["path"] == sp.PATH_SPARSE
+    prog.set_chunk(65536)
+    shots = 1_000_000
+    m, d, o = prog.sample(shots, seed=3, shot0=0)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    pick = np.unique(np.concatenate([rng.integers(0, shots, 44), [0, 65535, 65536, shots - 1]]))
+    rm, rd, ro = ref.sample_shots(3, pick)
+    idx = torch.as_tensor(pick, device="cuda")
+    np.testing.assert_array_equal(_u64(m[idx]), rm)
+    np.testing.assert_array_equal(_u64(d[idx]), rd)
+    np.testing.assert_array_equal(_u64(o[idx]), ro)
 
 
 def test_full_size_d11_detector_rates(d11):
