@@ -146,6 +146,53 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _batched_vs_plain(args):
+    """64 uneven circuits (rotated surface codes d = 3..15, p in {5e-4, 1e-3,
+    2e-3}, seeds 0..63), 1e5 shots each: one graph-captured batched enqueue
+    vs 64 separate sp_sample calls, identical records."""
+    import torch
+    import paper_2311_03906_gb300 as sp
+    from workloads import batch_suite
+    suite = batch_suite(64)
+    t0 = time.perf_counter()
+    progs = [sp.build(c) for c, _ in suite]
+    build_s = time.perf_counter() - t0
+    seeds = [s for _, s in suite]
+    shots = [args.batch_shots] * len(progs)
+    outs = [p.alloc_outputs(n) for p, n in zip(progs, shots)]
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        sp.sample_batch(progs, seeds, shots, outs=outs)
+
+    def plain():
+        for p, s, n, o in zip(progs, seeds, shots, outs):
+            p.sample(n, seed=s, out=o)
+
+    res = {}
+    for name, fn in (("batched", batched), ("plain", plain)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 3
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "shots_per_s": sum(shots) / (ms / 1e3)}
+    res["speedup"] = res["plain"]["ms"] / res["batched"]["ms"]
+    res["config"] = {"workload": "64 rotated surface codes d=3+2*(i mod 7), p=(5e-4,1e-3,2e-3)[(i//7) mod 3], seed i",
+                     "shots_per_circuit": args.batch_shots, "build_s": build_s,
+                     "paths": {"fused": sum(p.info["path"] == 3 for p in progs),
+                               "staged": sum(p.info["path"] == 1 for p in progs)}}
+    for p in progs:
+        p.close()
+    return res
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -262,6 +309,8 @@ def run_ours(args):
                    "measurements": info["num_measurements"], "detectors": info["num_detectors"],
                    "observables": info["num_observables"], "nnz_delta": info["nnz_delta"],
                    "path": {1: "staged-sparse", 2: "dense", 3: "fused"}.get(info["path"], "?"),
+                   "fused_tile_shots": info["fused_tile_shots"],
+                   "fused_blocks_per_iter": info["fused_blocks_per_iter"],
                    "chunk_shots": info["chunk_shots"],
                    "parallelism": f"shot-sharded x{world}" if world > 1 else "single GPU",
                    "l2": "outputs larger than L2: records %.2f GB per step (fault bits %.2f GB, in shared "
@@ -275,6 +324,8 @@ def run_ours(args):
         "e2e": {"value": shots * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h},
     }
+    if world == 1 and not args.no_batch:
+        line["batched"] = _batched_vs_plain(args)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(circuit, budget_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -291,6 +342,8 @@ def main():
     ap.add_argument("--shots", type=int, default=SHOTS)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-shots", type=int, default=100_000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

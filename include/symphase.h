@@ -115,7 +115,9 @@ typedef struct {
     uint64_t log_words;            /* length of the traversal's row-operation log */
     double density;                /* nnz_rows / (rows * n_s) */
     int32_t path;                  /* SP_PATH_SPARSE, SP_PATH_DENSE or SP_PATH_FUSED */
-    int32_t reserved;
+    int32_t fused_tile_shots;      /* shots per fused tile (32 or 64; 0 = fused path unavailable) */
+    int32_t fused_blocks_per_iter; /* channel blocks drawn per iteration of the fused kernel */
+    int32_t fused_windows;         /* symbol windows per tile of the fused kernel */
     uint64_t chunk_shots;          /* shots per internal sampling chunk */
     double build_ms;               /* wall time of sp_build */
 } sp_info_t;
@@ -243,6 +245,16 @@ SP_API sp_status sp_export_channels(const sp_program *prog, uint32_t *h_T, uint8
 /* sp_set_path -- force the sampler variant (SP_PATH_*); AUTO restores the
  * build-time choice. */
 SP_API sp_status sp_set_path(sp_program *prog, int32_t path);
+
+/*
+ * sp_set_fused_config -- choose the fused kernel variant by hand instead of
+ * the build-time autotuner's choice: tile_shots 32 or 64, blocks_per_iter 1
+ * or 2, windows = number of symbol windows a tile is drawn and consumed in
+ * (0 = the fewest that fit in shared memory, allowing two CTAs per SM for
+ * 32-shot tiles when possible).  INVALID_ARG if that tile does not fit.
+ * Records are identical for every variant.
+ */
+SP_API sp_status sp_set_fused_config(sp_program *prog, int32_t tile_shots, int32_t blocks_per_iter, int32_t windows);
 
 /* sp_set_chunk -- shots per internal chunk (multiple of 1024, 0 = default). */
 SP_API sp_status sp_set_chunk(sp_program *prog, uint64_t chunk_shots);

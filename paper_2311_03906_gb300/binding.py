@@ -27,7 +27,8 @@ PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED = 0, 1, 2, 3
 # every entry point declared in include/symphase.h
 EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",
            "sp_sample_batch", "sp_expect",
-           "sp_expect_grad", "sp_export_rows", "sp_export_channels", "sp_set_path", "sp_set_chunk",
+           "sp_expect_grad", "sp_export_rows", "sp_export_channels", "sp_set_path", "sp_set_fused_config",
+           "sp_set_chunk",
            "sp_profile_enable", "sp_profile_read", "sp_free", "sp_last_error")
 KERNEL_CLASSES = ("draw", "product", "emit", "fused")
 
@@ -53,7 +54,8 @@ class sp_info_t(C.Structure):
                 ("num_symbols", C.c_uint64), ("num_channels", C.c_uint64),
                 ("num_random", C.c_uint64), ("nnz_rows", C.c_uint64), ("nnz_delta", C.c_uint64),
                 ("log_words", C.c_uint64), ("density", C.c_double), ("path", C.c_int32),
-                ("reserved", C.c_int32), ("chunk_shots", C.c_uint64), ("build_ms", C.c_double)]
+                ("fused_tile_shots", C.c_int32), ("fused_blocks_per_iter", C.c_int32),
+                ("fused_windows", C.c_int32), ("chunk_shots", C.c_uint64), ("build_ms", C.c_double)]
 
 
 _lib = None
@@ -85,6 +87,7 @@ def load() -> C.CDLL:
     lib.sp_export_channels.argtypes = [vp, vp, vp, vp]
     lib.sp_set_path.argtypes = [vp, i32]
     lib.sp_set_chunk.argtypes = [vp, u64]
+    lib.sp_set_fused_config.argtypes = [vp, i32, i32, i32]
     lib.sp_profile_enable.argtypes = [vp, i32]
     lib.sp_profile_read.argtypes = [vp, vp, vp]
     lib.sp_free.argtypes = [vp]
@@ -216,6 +219,10 @@ class Program:
 
     def set_path(self, path: int):
         _check(self._lib.sp_set_path(self._h, path))
+        self.refresh_info()
+
+    def set_fused_config(self, tile_shots: int, blocks_per_iter: int, windows: int = 0):
+        _check(self._lib.sp_set_fused_config(self._h, tile_shots, blocks_per_iter, windows))
         self.refresh_info()
 
     def set_chunk(self, chunk_shots: int):

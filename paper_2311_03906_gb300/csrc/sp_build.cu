@@ -778,7 +778,7 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     const bool in_smem = head_bytes + tab_bytes <= 200 * 1024;
     if (!in_smem) SP_TRY(tmp.alloc(&d_gtab, 2 * (size_t)Wq * R2));
     const size_t smem = head_bytes + (in_smem ? tab_bytes : 0);
-    SP_CUDA(cudaFuncSetAttribute(k_traverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SP_CUDA(max_dynamic_smem(k_traverse));
     TravParams tp;
     tp.insts = d_insts; tp.ninst = (int64_t)F.insts.size(); tp.n = n; tp.Wq = Wq; tp.R2 = R2;
     tp.gtab = d_gtab; tp.tab_in_smem = in_smem ? 1 : 0; tp.log = d_log; tp.log_cap = log_cap;
@@ -806,7 +806,7 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     if (P->n_sym > 0 && n > 0) {
         const int64_t nblk = ceil_div(P->n_sym + 1, 1024);
         const size_t vsm = (size_t)n * 32 * 4;
-        SP_CUDA(cudaFuncSetAttribute(k_replay, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+        SP_CUDA(max_dynamic_smem(k_replay));
         k_replay<<<(unsigned)nblk, 32, vsm, stream>>>(d_log, hc.log_len, d_inj, Wq, d_logpos,
                                                        hc.nsym, n, P->d_A, P->apitch);
         SP_CUDA(cudaGetLastError());
@@ -927,6 +927,7 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     const double cells = (double)std::max<int64_t>(R, 1) * (double)std::max<int64_t>(P->n_sym, 1);
     P->density = (double)P->nnz_rows / cells;
     SP_TRY(build_fused_program(P, stream));
+    SP_TRY(autotune(P, stream));
     P->build_path = P->fused_tw ? SP_PATH_FUSED : SP_PATH_SPARSE;
     P->path = P->build_path;
     P->chunk_shots = default_chunk(P);

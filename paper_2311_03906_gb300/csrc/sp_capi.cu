@@ -26,15 +26,16 @@ sp_status cuda_error(cudaError_t e, const char *what)
 static void release(sp_program *P)
 {
     if (!P) return;
+    batch_forget(P);
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != P->device) cudaSetDevice(P->device);
     void *bufs[] = {P->d_A, P->d_chT, P->d_chKind, P->d_chP, P->d_chSym0, P->d_rowOff, P->d_idx,
                     P->d_parent, P->d_cflag, P->d_A64, P->d_const, P->d_inc, P->d_incT, P->d_kappa,
                     P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta,
-                    P->d_blkSym0, P->d_fRowMeta, P->d_fAOff, P->d_fChain, P->d_fBOff, P->d_fCOff,
-                    P->d_fCRefs, P->d_fIdx4};
+                    P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs};
     for (void *b : bufs) if (b) cudaFree(b);
+    for (auto &L : P->layouts) L.release();
     if (P->h_stage) cudaFreeHost(P->h_stage);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     for (auto &pe : P->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -123,6 +124,9 @@ sp_status sp_info(const sp_program *P, sp_info_t *o)
     o->log_words = (uint64_t)P->log_len;
     o->density = P->density;
     o->path = P->path;
+    o->fused_tile_shots = 32 * P->fused_tw;
+    o->fused_blocks_per_iter = P->fused_unroll;
+    o->fused_windows = P->fused_tw ? P->layouts[P->fused_layout].nw : 0;
     o->chunk_shots = (uint64_t)P->chunk_shots;
     o->build_ms = P->build_ms;
     return SP_OK;
@@ -222,11 +226,13 @@ sp_status sp_sample_batch(sp_program *const *progs, uint32_t nprog, const uint64
         if (!progs[i]) return set_error(SP_ERR_INVALID_ARG, "progs[" + std::to_string(i) + "] is NULL");
     }
     for (uint32_t i = 0; i < nprog; i++) {
-        sp_status st = sp_sample(progs[i], seeds[i], 0, nshots[i], d_meas ? d_meas[i] : nullptr,
-                                 d_det ? d_det[i] : nullptr, d_obs ? d_obs[i] : nullptr, cuda_stream);
-        if (st != SP_OK) return st;
+        for (uint64_t *const *arr : {d_meas, d_det, d_obs}) {
+            if (!arr) continue;
+            sp_status st = check_ptr(arr[i], "output");
+            if (st != SP_OK) return st;
+        }
     }
-    return SP_OK;
+    return sample_batch(progs, nprog, seeds, nshots, d_meas, d_det, d_obs, (cudaStream_t)cuda_stream);
 }
 
 sp_status sp_expect(sp_program *P, const float *d_p, float *d_logE, void *cuda_stream)
@@ -280,10 +286,21 @@ sp_status sp_set_path(sp_program *P, int32_t path)
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
     if (path == SP_PATH_AUTO) { P->path = P->build_path; return SP_OK; }
     if (path == SP_PATH_FUSED && !P->fused_tw)
-        return set_error(SP_ERR_INVALID_ARG, "the fused tile of this program does not fit in shared memory");
+        return set_error(SP_ERR_INVALID_ARG, "the fused path is unavailable for this program");
     if (path != SP_PATH_SPARSE && path != SP_PATH_FUSED) return set_error(SP_ERR_INVALID_ARG, "unsupported path");
     P->path = path;
     return SP_OK;
+}
+
+sp_status sp_set_fused_config(sp_program *P, int32_t tile_shots, int32_t blocks_per_iter, int32_t windows)
+{
+    if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
+    if (tile_shots != 32 && tile_shots != 64) return set_error(SP_ERR_INVALID_ARG, "tile_shots must be 32 or 64");
+    const int tw = tile_shots / 32;
+    int nw = windows;
+    if (nw == 0) nw = tw == 1 ? (P->nw_half ? P->nw_half : P->nw_full1) : P->nw_full2;
+    if (nw <= 0) return set_error(SP_ERR_INVALID_ARG, "no window count makes that tile fit in shared memory");
+    return fused_select(P, tw, nw, blocks_per_iter);
 }
 
 sp_status sp_set_chunk(sp_program *P, uint64_t chunk_shots)

@@ -22,7 +22,11 @@
 // on b, so they are computed once per shot: 17 of the 20 wide multiplies of a
 // block remain per (shot, block).
 #include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "sp_internal.h"
@@ -69,24 +73,40 @@ __device__ __forceinline__ ShotConst shot_const(uint64_t shot, uint32_t k1)
     return s;
 }
 
+// Round keys k + r*W for r = 0..9 (the same for every lane).
+struct Keys {
+    uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ Keys make_keys(uint32_t k0, uint32_t k1)
+{
+    Keys K;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        K.k0[r] = k0 + (uint32_t)r * PH_W0;
+        K.k1[r] = k1 + (uint32_t)r * PH_W1;
+    }
+    return K;
+}
+
 // Rounds 1..10 of Philox4x32-10 for counter (shot, b): uhi/ulo = M1*b.
-__device__ __forceinline__ void philox_block(const ShotConst &s, uint32_t uhi, uint32_t ulo, uint32_t k0,
-                                             uint32_t k1, uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
+__device__ __forceinline__ void philox_block(const ShotConst &s, uint32_t uhi, uint32_t ulo, const Keys &K,
+                                             uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
 {
     // round 1 (counter word 3 is 0)
-    uint32_t x0 = uhi ^ s.c1 ^ k0;
+    const uint32_t x0 = uhi ^ s.c1 ^ K.k0[0];
     // round 2
     const uint64_t p = (uint64_t)PH_M0 * x0;
-    uint32_t c0 = s.r2hi ^ ulo ^ (k0 + PH_W0);
+    uint32_t c0 = s.r2hi ^ ulo ^ K.k0[1];
     uint32_t c1 = s.r2lo;
-    uint32_t c2 = (uint32_t)(p >> 32) ^ s.x3 ^ (k1 + PH_W1);
+    uint32_t c2 = (uint32_t)(p >> 32) ^ s.x3 ^ K.k1[1];
     uint32_t c3 = (uint32_t)p;
 #pragma unroll
     for (int r = 2; r < 10; r++) {
         const uint64_t p0 = (uint64_t)PH_M0 * c0;
         const uint64_t p1 = (uint64_t)PH_M1 * c2;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ (k0 + (uint32_t)r * PH_W0);
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ (k1 + (uint32_t)r * PH_W1);
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[r];
         c1 = (uint32_t)p1;
         c3 = (uint32_t)p0;
         c0 = n0;
@@ -121,50 +141,90 @@ __device__ __forceinline__ uint32_t chan_bits(uint32_t u, uint32_t T, uint32_t k
 template <int TW> struct Cols { uint32_t v[TW]; };
 template <int TW> struct Shots { ShotConst s[TW]; };
 
-template <int TW, typename Sink>
+template <int TW, int U, typename Sink>
 __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
-                                            int64_t b0, int64_t b1, uint32_t sym_begin, const Shots<TW> sc,
+                                            uint32_t b0, uint32_t b1, uint32_t sym_begin, const Shots<TW> sc,
                                             uint32_t k0, uint32_t k1, int lane, Sink sink)
 {
+    const Keys K = make_keys(k0, k1);
     uint64_t acc[TW];
 #pragma unroll
     for (int t = 0; t < TW; t++) acc[t] = 0;
     uint32_t fill = 0, base = sym_begin;
-    for (int64_t b = b0; b < b1; b++) {
-        const uint4 T = blkT[b];
-        const uint32_t meta = blkMeta[b];
-        const uint64_t u = (uint64_t)PH_M1 * (uint32_t)b;
-        const uint32_t uhi = (uint32_t)(u >> 32), ulo = (uint32_t)u;
-        uint32_t r[TW][4];
-        bool fire = false;
+    auto flush = [&]() {
+        Cols<TW> col;
 #pragma unroll
         for (int t = 0; t < TW; t++) {
-            philox_block(sc.s[t], uhi, ulo, k0, k1, r[t][0], r[t][1], r[t][2], r[t][3]);
-            fire |= (r[t][0] < T.x) | (r[t][1] < T.y) | (r[t][2] < T.z) | (r[t][3] < T.w);
+            const uint32_t lo = (uint32_t)acc[t];
+            col.v[t] = __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
+            acc[t] >>= 32;
         }
-        if (__any_sync(FM, fire)) {
-            const uint32_t Ts[4] = {T.x, T.y, T.z, T.w};
+        sink(base, col);
+        fill -= 32;
+        base += 32;
+    };
+    // U blocks per iteration: U*TW independent Philox evaluations per lane.
+    // fill stays below 32 between iterations and a block adds at most 16
+    // symbols, so U <= 2 keeps every inserted bit inside the 64-bit word.
+    static_assert(U == 1 || U == 2, "at most two blocks per iteration");
+    uint32_t b = b0;
+    for (; b + U <= b1; b += U) {
+        uint4 T[U];
+        uint32_t meta[U];
+        uint32_t r[U][TW][4];
+        uint32_t fm[U];
+#pragma unroll
+        for (int v = 0; v < U; v++) {
+            T[v] = blkT[b + v];
+            meta[v] = blkMeta[b + v];
+            const uint64_t ub = (uint64_t)PH_M1 * (b + (uint32_t)v);
+            fm[v] = 0;
+#pragma unroll
+            for (int t = 0; t < TW; t++) {
+                philox_block(sc.s[t], (uint32_t)(ub >> 32), (uint32_t)ub, K, r[v][t][0], r[v][t][1], r[v][t][2], r[v][t][3]);
+                fm[v] |= ((uint32_t)(r[v][t][0] < T[v].x) | ((uint32_t)(r[v][t][1] < T[v].y) << 1) |
+                          ((uint32_t)(r[v][t][2] < T[v].z) << 2) | ((uint32_t)(r[v][t][3] < T[v].w) << 3)) << (4 * t);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < U; v++) {
+            if (__any_sync(FM, fm[v] != 0u)) {
+                const uint32_t Ts[4] = {T[v].x, T[v].y, T[v].z, T[v].w};
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+#pragma unroll
+                    for (int t = 0; t < TW; t++) {
+                        const bool hit = (fm[v] >> (4 * t + i)) & 1u;
+                        if (__any_sync(FM, hit)) {
+                            const uint32_t kind = (meta[v] >> (2 * i)) & 3u;
+                            const uint32_t off = fill + ((meta[v] >> (8 + 4 * i)) & 15u);
+                            if (hit) acc[t] |= (uint64_t)chan_bits(r[v][t][i], Ts[i], kind) << off;
+                        }
+                    }
+                }
+            }
+            fill += meta[v] >> 24;
+        }
+        if (fill >= 32) flush();
+    }
+    for (; b < b1; b++) {
+        const uint4 T = blkT[b];
+        const uint32_t meta = blkMeta[b];
+        const uint64_t ub = (uint64_t)PH_M1 * b;
+        const uint32_t Ts[4] = {T.x, T.y, T.z, T.w};
+#pragma unroll
+        for (int t = 0; t < TW; t++) {
+            uint32_t r[4];
+            philox_block(sc.s[t], (uint32_t)(ub >> 32), (uint32_t)ub, K, r[0], r[1], r[2], r[3]);
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const uint32_t kind = (meta >> (2 * i)) & 3u;
                 const uint32_t off = fill + ((meta >> (8 + 4 * i)) & 15u);
-#pragma unroll
-                for (int t = 0; t < TW; t++) acc[t] |= (uint64_t)chan_bits(r[t][i], Ts[i], kind) << off;
+                acc[t] |= (uint64_t)chan_bits(r[i], Ts[i], kind) << off;
             }
         }
         fill += meta >> 24;
-        if (fill >= 32) {
-            Cols<TW> col;
-#pragma unroll
-            for (int t = 0; t < TW; t++) {
-                const uint32_t lo = (uint32_t)acc[t];
-                col.v[t] = __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
-                acc[t] >>= 32;
-            }
-            sink(base, col);
-            fill -= 32;
-            base += 32;
-        }
+        if (fill >= 32) flush();
     }
     if (fill > 0) {
         Cols<TW> col;
@@ -181,19 +241,21 @@ struct FusedParams {
     const uint4 *blkT;
     const uint32_t *blkMeta;
     const uint32_t *blkSym0;
-    int64_t n_blk;
     int64_t n_sym, n_rows, n_meas, n_det, n_obs;
-    const uint4 *aItem;        // step A: {index-group offset, group count, row, const flag}
-    const uint32_t *aOff;      // [threads + 1]
+    int nw;                    // symbol windows drawn and consumed one after another
+    const uint32_t *winBlk;    // [nw + 1] first channel block of each window
+    const uint4 *aItem;        // step A: {index-group offset, group count, row, 0}
+    const uint32_t *aOff;      // [nw][threads + 1] items of (window, thread)
+    const uint8_t *cflag;      // [n_meas] constant bit of each measurement row's own part
     const uint2 *bItem;        // step B: (row, parent), parents first within a thread
     const uint32_t *bOff;      // [threads + 1]
     const uint32_t *cOff;      // step C: detector/observable t = XOR of measurement rows
     const uint32_t *cRefs;
-    const uint4 *idx4;         // groups of 4 (u32) or 8 (u16) symbol indices
+    const uint4 *idx4;         // groups of 8 x 16-bit window-relative symbol indices
     uint64_t seed, shot0, nshots;
     uint64_t *out[3];
     int64_t rows0[3], nrow[3];
-    uint32_t rec_off_words;   // offset of R_s in shared memory (u32 words)
+    uint32_t rec_off_words;    // offset of R_s in shared memory (u32 words)
 };
 
 template <int TW> struct TileWord;
@@ -215,12 +277,6 @@ __device__ __forceinline__ uint32_t xorw(uint32_t a, uint32_t b) { return a ^ b;
 __device__ __forceinline__ uint2 xorw(uint2 a, uint2 b) { return make_uint2(a.x ^ b.x, a.y ^ b.y); }
 
 template <typename W>
-__device__ __forceinline__ W gather4(const W *Bs, uint4 s)
-{
-    return xorw(xorw(Bs[s.x], Bs[s.y]), xorw(Bs[s.z], Bs[s.w]));
-}
-
-template <typename W>
 __device__ __forceinline__ W gather8(const W *Bs, uint4 s)
 {
     const W a = xorw(xorw(Bs[s.x & 0xffffu], Bs[s.x >> 16]), xorw(Bs[s.y & 0xffffu], Bs[s.y >> 16]));
@@ -228,106 +284,138 @@ __device__ __forceinline__ W gather8(const W *Bs, uint4 s)
     return xorw(a, b);
 }
 
-template <int TW, bool IDX16>
-__global__ void __launch_bounds__(FUSED_THREADS, (TW == 1 ? 2 : 1)) k_fused(FusedParams p)
+// One tile of 32*TW shots of one program, by the whole CTA.  Ends with a
+// barrier, so the caller may start another tile right away.
+template <int TW, int U>
+__device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, uint32_t *sm)
 {
     typedef TileWord<TW> TWd;
     typedef typename TWd::T W;
-    extern __shared__ __align__(16) uint32_t sm[];
-    W *Bs = reinterpret_cast<W *>(sm);                       // n_sym + 1 (last = zero)
+    W *Bs = reinterpret_cast<W *>(sm);                       // one window of symbols + a zero slot
     W *Rs = reinterpret_cast<W *>(sm + p.rec_off_words);     // n_rows
     uint32_t *stage = sm;                                    // aliases Bs in phase 3
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const uint64_t trel = tile * (32u * TW);
+    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    Shots<TW> sc;
+#pragma unroll
+    for (int t = 0; t < TW; t++) sc.s[t] = shot_const(p.shot0 + trel + 32u * t + lane, k1);
+    // own parts start from their constants
+    for (int64_t j = tid; j < p.n_meas; j += blockDim.x) Rs[j] = p.cflag[j] ? TWd::ones() : TWd::zero();
+    for (int w = 0; w < p.nw; w++) {
+        // ---- phase 1: draw the symbols of window w ------------------------
+        const uint32_t wb0 = p.winBlk[w], wb1 = p.winBlk[w + 1];
+        const uint32_t wsym0 = p.blkSym0[wb0], wsize = p.blkSym0[wb1] - wsym0;
+        const uint32_t nbw = wb1 - wb0;
+        const uint32_t b0 = wb0 + (uint32_t)((uint64_t)warp * nbw / nwarps);
+        const uint32_t b1 = wb0 + (uint32_t)((uint64_t)(warp + 1) * nbw / nwarps);
+        const uint32_t send = p.blkSym0[b1];
+        if (tid == 0) Bs[wsize] = TWd::zero();
+        draw_blocks<TW, U>(p.blkT, p.blkMeta, b0, b1, p.blkSym0[b0], sc, k0, k1, lane,
+                           [=](uint32_t base, const Cols<TW> col) {
+                               if (base + lane < send) Bs[base + lane - wsym0] = TWd::make(col);
+                           });
+        __syncthreads();
+        // ---- phase 2A: own parts over this window's symbols -------------------
+        {
+            const uint32_t *ao = p.aOff + (size_t)w * (blockDim.x + 1);
+            const uint32_t e = ao[tid + 1];
+            for (uint32_t i = ao[tid]; i < e; i++) {
+                const uint4 m = p.aItem[i];
+                const uint4 *q = p.idx4 + m.x;
+                W acc = TWd::zero();
+                uint32_t k = 0;
+                for (; k + 2 <= m.y; k += 2) {
+                    const uint4 s0 = q[k], s1 = q[k + 1];
+                    acc = xorw(acc, xorw(gather8(Bs, s0), gather8(Bs, s1)));
+                }
+                if (k < m.y) acc = xorw(acc, gather8(Bs, q[k]));
+                Rs[m.z] = xorw(Rs[m.z], acc);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- phase 2B: parent chains, m_j = own part ^ m_parent ---------------
+    {
+        const uint32_t e = p.bOff[tid + 1];
+        for (uint32_t i = p.bOff[tid]; i < e; i++) {
+            const uint2 rp = p.bItem[i];
+            Rs[rp.x] = xorw(Rs[rp.x], Rs[rp.y]);
+        }
+    }
+    __syncthreads();
+    // ---- phase 2C: detectors and observables from measurement records ------
+    for (int64_t t = tid; t < p.n_det + p.n_obs; t += blockDim.x) {
+        W acc = TWd::zero();
+        for (uint32_t k = p.cOff[t]; k < p.cOff[t + 1]; k++) acc = xorw(acc, Rs[p.cRefs[k]]);
+        Rs[p.n_meas + t] = acc;
+    }
+    __syncthreads();
+    // ---- phase 3: emit shot-major records -----------------------------------
+#pragma unroll
+    for (int sg = 0; sg < 3; sg++) {
+        uint64_t *dst = p.out[sg];
+        const int64_t n = p.nrow[sg];
+        if (!dst || n == 0) continue;
+        const int64_t row0 = p.rows0[sg];
+        const int words32 = (int)(2 * ((n + 63) / 64));
+        const int stride = words32 + 1;
+        for (int g = warp; g < words32; g += nwarps) {
+            const int64_t r = 32 * (int64_t)g + lane;
+#pragma unroll
+            for (int t = 0; t < TW; t++) {
+                const uint32_t x = r < n ? TWd::get(Rs[row0 + r], t) : 0u;
+                stage[(32 * t + lane) * stride + g] = __any_sync(FM, x != 0u) ? transpose32(x, lane) : 0u;
+            }
+        }
+        __syncthreads();
+        uint32_t *o32 = reinterpret_cast<uint32_t *>(dst);
+        for (int sh = warp; sh < 32 * TW; sh += nwarps) {
+            const uint64_t shot = trel + (uint64_t)sh;
+            if (shot >= p.nshots) continue;
+            uint32_t *o = o32 + shot * (uint64_t)words32;
+            for (int g = lane; g < words32; g += 32) o[g] = stage[sh * stride + g];
+        }
+        __syncthreads();
+    }
+    // phase 3 may have been skipped (no outputs): keep the tile boundary
+    __syncthreads();
+}
+
+template <int TW, int U>
+__global__ void __launch_bounds__(FUSED_THREADS, (TW == 1 ? 2 : 1)) k_fused(FusedParams p)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
     const uint64_t per_tile = 32u * TW;
     const uint64_t ntiles = (p.nshots + per_tile - 1) / per_tile;
-    const int64_t b0 = (int64_t)warp * p.n_blk / nwarps, b1 = (int64_t)(warp + 1) * p.n_blk / nwarps;
-    const uint32_t sbeg = p.blkSym0[b0], send = p.blkSym0[b1];
-    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) fused_tile<TW, U>(p, tile, sm);
+}
 
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t trel = tile * per_tile;
-        // ---- phase 1: draw ------------------------------------------------
-        Shots<TW> sc;
-#pragma unroll
-        for (int t = 0; t < TW; t++) sc.s[t] = shot_const(p.shot0 + trel + 32u * t + lane, k1);
-        if (tid == 0) Bs[p.n_sym] = TWd::zero();
-        draw_blocks<TW>(p.blkT, p.blkMeta, b0, b1, sbeg, sc, k0, k1, lane,
-                        [=](uint32_t base, const Cols<TW> col) {
-                            if (base + lane < send) Bs[base + lane] = TWd::make(col);
-                        });
+// Batched form: many programs in one persistent launch.  Work items are
+// (program, 32-shot tile) pairs handed out in order by an atomic counter;
+// items of program i are [tileEnd[i-1], tileEnd[i]).  The launcher orders
+// the programs by decreasing cost per tile so the tail is made of the
+// cheapest items.
+template <int MINB>
+__global__ void __launch_bounds__(FUSED_THREADS, MINB) k_fused_batch(const FusedParams *__restrict__ progs, int nprog,
+                                                                  const uint64_t *__restrict__ tileEnd,
+                                                                  unsigned long long *counter)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ unsigned long long s_item;
+    const uint64_t total = tileEnd[nprog - 1];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
         __syncthreads();
-        // ---- phase 2: GF(2) product ------------------------------------------
-        // A: every measurement row's own part c'_j ^ XOR of B_s over its delta
-        //    symbols; rows are independent, balanced over threads.
-        {
-            const uint32_t e = p.aOff[tid + 1];
-            for (uint32_t i = p.aOff[tid]; i < e; i++) {
-                const uint4 m = p.aItem[i];
-                W acc = m.w ? TWd::ones() : TWd::zero();
-                const uint4 *q = p.idx4 + m.x;
-                uint32_t k = 0;
-                if (IDX16) {
-                    for (; k + 2 <= m.y; k += 2) {
-                        const uint4 s0 = q[k], s1 = q[k + 1];
-                        acc = xorw(acc, xorw(gather8(Bs, s0), gather8(Bs, s1)));
-                    }
-                    if (k < m.y) acc = xorw(acc, gather8(Bs, q[k]));
-                } else {
-                    for (; k + 4 <= m.y; k += 4) {
-                        const uint4 s0 = q[k], s1 = q[k + 1], s2 = q[k + 2], s3 = q[k + 3];
-                        acc = xorw(acc, xorw(gather4(Bs, s0), gather4(Bs, s1)));
-                        acc = xorw(acc, xorw(gather4(Bs, s2), gather4(Bs, s3)));
-                    }
-                    for (; k < m.y; k++) acc = xorw(acc, gather4(Bs, q[k]));
-                }
-                Rs[m.z] = acc;
-            }
-        }
+        const uint64_t item = s_item;
         __syncthreads();
-        // B: parent chains, m_j = own part ^ m_parent (each thread owns whole
-        //    trees and walks them parents first).
-        {
-            const uint32_t e = p.bOff[tid + 1];
-            for (uint32_t i = p.bOff[tid]; i < e; i++) {
-                const uint2 rp = p.bItem[i];
-                Rs[rp.x] = xorw(Rs[rp.x], Rs[rp.y]);
-            }
+        if (item >= total) break;
+        int lo = 0, hi = nprog - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (tileEnd[mid] > item) hi = mid; else lo = mid + 1;
         }
-        __syncthreads();
-        // C: detectors and observables are XORs of measurement records.
-        for (int64_t t = tid; t < p.n_det + p.n_obs; t += blockDim.x) {
-            W acc = TWd::zero();
-            for (uint32_t k = p.cOff[t]; k < p.cOff[t + 1]; k++) acc = xorw(acc, Rs[p.cRefs[k]]);
-            Rs[p.n_meas + t] = acc;
-        }
-        __syncthreads();
-        // ---- phase 3: emit shot-major records ------------------------------
-#pragma unroll
-        for (int sg = 0; sg < 3; sg++) {
-            uint64_t *dst = p.out[sg];
-            const int64_t n = p.nrow[sg];
-            if (!dst || n == 0) continue;
-            const int64_t row0 = p.rows0[sg];
-            const int words32 = (int)(2 * ((n + 63) / 64));
-            const int stride = words32 + 1;
-            for (int g = warp; g < words32; g += nwarps) {
-                const int64_t r = 32 * (int64_t)g + lane;
-#pragma unroll
-                for (int t = 0; t < TW; t++) {
-                    const uint32_t x = r < n ? TWd::get(Rs[row0 + r], t) : 0u;
-                    stage[(32 * t + lane) * stride + g] = __any_sync(FM, x != 0u) ? transpose32(x, lane) : 0u;
-                }
-            }
-            __syncthreads();
-            uint32_t *o32 = reinterpret_cast<uint32_t *>(dst);
-            for (int sh = warp; sh < 32 * TW; sh += nwarps) {
-                const uint64_t shot = trel + (uint64_t)sh;
-                if (shot >= p.nshots) continue;
-                uint32_t *o = o32 + shot * (uint64_t)words32;
-                for (int g = lane; g < words32; g += 32) o[g] = stage[sh * stride + g];
-            }
-            __syncthreads();
-        }
+        fused_tile<1, 2>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
     }
 }
 
@@ -344,7 +432,7 @@ __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ b
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     Shots<1> sc;
     sc.s[0] = shot_const(shot0 + (uint64_t)w * 32u + (uint64_t)lane, k1);
-    draw_blocks<1>(blkT, blkMeta, 0, n_blk, 0u, sc, k0, k1, lane,
+    draw_blocks<1, 2>(blkT, blkMeta, 0u, (uint32_t)n_blk, 0u, sc, k0, k1, lane,
                    [=](uint32_t base, const Cols<1> col) {
                        if ((int64_t)base + lane < n_sym) B[(size_t)(base + lane) * bpitch + w] = col.v[0];
                    });
@@ -365,6 +453,30 @@ sp_status upload(T **dst, const std::vector<T> &src, cudaStream_t s)
     }
     if (!src.empty()) SP_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     return SP_OK;
+}
+
+// Longest-processing-time assignment: items (already sorted by decreasing
+// cost) go one by one to the least loaded of nt threads.
+double lpt_assign(const std::vector<int64_t> &items, const std::vector<double> &cost, int nt, std::vector<int32_t> &owner)
+{
+    std::vector<std::pair<double, int>> heap;
+    for (int t = 0; t < nt; t++) heap.push_back({0.0, t});
+    auto cmp = [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first > b.first || (a.first == b.first && a.second > b.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    double mx = 0.0;
+    for (int64_t it : items) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto h = heap.back();
+        heap.pop_back();
+        owner[it] = h.second;
+        h.first += cost[it];
+        mx = std::max(mx, h.first);
+        heap.push_back(h);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    return mx;
 }
 }  // namespace
 
@@ -408,89 +520,29 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     if ((st = upload(&P->d_blkT, bT, s)) || (st = upload(&P->d_blkMeta, bMeta, s)) || (st = upload(&P->d_blkSym0, bSym0, s)))
         return st;
 
-    // ---- level-ordered, padded product program ----------------------------
+    // ---- product program: host copies of the measurement rows' own parts --
     const int64_t R = P->n_rows;
+    const int64_t M = P->n_meas;
     std::vector<int32_t> parent((size_t)R);
     std::vector<uint8_t> cflag((size_t)R);
     std::vector<uint32_t> off((size_t)R + 1);
-    std::vector<uint32_t> idx((size_t)P->nnz_delta);
     if (R) {
         SP_CUDA(cudaMemcpyAsync(parent.data(), P->d_parent, (size_t)R * 4, cudaMemcpyDeviceToHost, s));
         SP_CUDA(cudaMemcpyAsync(cflag.data(), P->d_cflag, (size_t)R, cudaMemcpyDeviceToHost, s));
         SP_CUDA(cudaMemcpyAsync(off.data(), P->d_rowOff, ((size_t)R + 1) * 4, cudaMemcpyDeviceToHost, s));
-        if (!idx.empty())
-            SP_CUDA(cudaMemcpyAsync(idx.data(), P->d_idx, idx.size() * 4, cudaMemcpyDeviceToHost, s));
         SP_CUDA(cudaStreamSynchronize(s));
     }
-    // Step A: the own part of every measurement row (its delta symbols and
-    // constant) -- independent rows, longest first to the least loaded thread.
-    // Step B: parent chains -- whole trees per thread, parents first.
-    // Step C: detectors and observables from their measurement records.
-    const int64_t M = P->n_meas;
-    const bool idx16 = P->n_sym < 65535;
-    const uint32_t per_group = idx16 ? 8u : 4u;
+    P->h_own_off.assign(off.begin(), off.begin() + (M + 1));
+    P->h_own_idx.assign((size_t)P->h_own_off[M], 0u);
+    if (!P->h_own_idx.empty())
+        SP_CUDA(cudaMemcpy(P->h_own_idx.data(), P->d_idx, P->h_own_idx.size() * 4, cudaMemcpyDeviceToHost));
+    P->h_blkSym0 = bSym0;
+    for (int64_t j = 0; j < M; j++)
+        if (parent[j] >= M) return set_error(SP_ERR_CUDA, "measurement row with a non-measurement parent");
+    // step 0: constants of the own parts
+    std::vector<uint8_t> cf(cflag.begin(), cflag.begin() + M);
+    // step B: parent chains, whole trees per thread, parents first
     const int NT = FUSED_THREADS;
-    auto lpt = [&](const std::vector<int64_t> &items, const std::vector<double> &cost, std::vector<int32_t> &owner_of) {
-        std::vector<std::pair<double, int>> heap;
-        for (int t = 0; t < NT; t++) heap.push_back({0.0, t});
-        auto cmp = [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
-            return a.first > b.first || (a.first == b.first && a.second > b.second);
-        };
-        std::make_heap(heap.begin(), heap.end(), cmp);
-        double mx = 0.0;
-        for (int64_t it : items) {
-            std::pop_heap(heap.begin(), heap.end(), cmp);
-            auto hh = heap.back();
-            heap.pop_back();
-            owner_of[it] = hh.second;
-            hh.first += cost[it];
-            mx = std::max(mx, hh.first);
-            heap.push_back(hh);
-            std::push_heap(heap.begin(), heap.end(), cmp);
-        }
-        return mx;
-    };
-    std::vector<uint32_t> groups((size_t)M);
-    std::vector<double> costA((size_t)M);
-    std::vector<int64_t> itemsA((size_t)M);
-    for (int64_t j = 0; j < M; j++) {
-        groups[j] = (off[j + 1] - off[j] + per_group - 1) / per_group;
-        costA[j] = 1.0 + groups[j];
-        itemsA[j] = j;
-    }
-    std::stable_sort(itemsA.begin(), itemsA.end(), [&](int64_t a, int64_t b) { return costA[a] > costA[b]; });
-    std::vector<int32_t> ownerA((size_t)M, 0);
-    P->fused_max_load = lpt(itemsA, costA, ownerA);
-    // index groups laid out per measurement row
-    std::vector<uint4> idx4;
-    std::vector<uint32_t> goff((size_t)M);
-    const uint32_t zero = (uint32_t)P->n_sym;   // index of the zero slot
-    for (int64_t j = 0; j < M; j++) {
-        const uint32_t a = off[j], e = off[j + 1];
-        goff[j] = (uint32_t)idx4.size();
-        for (uint32_t k = 0; k < groups[j]; k++) {
-            uint32_t v[8];
-            for (uint32_t i = 0; i < per_group; i++) {
-                const uint32_t at = a + per_group * k + i;
-                v[i] = at < e ? idx[at] : zero;
-            }
-            if (idx16)
-                idx4.push_back(make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16)));
-            else
-                idx4.push_back(make_uint4(v[0], v[1], v[2], v[3]));
-        }
-    }
-    std::vector<uint32_t> aOff((size_t)NT + 1, 0);
-    for (int64_t j = 0; j < M; j++) aOff[ownerA[j] + 1]++;
-    for (int t = 0; t < NT; t++) aOff[t + 1] += aOff[t];
-    std::vector<uint4> aItem((size_t)M);
-    {
-        std::vector<uint32_t> pos(aOff.begin(), aOff.end() - 1);
-        for (int64_t j : itemsA)
-            aItem[pos[ownerA[j]]++] = make_uint4(goff[j], groups[j], (uint32_t)j, (uint32_t)cflag[j]);
-    }
-    // step B: trees of measurement rows (parents of measurement rows are
-    // earlier measurement rows)
     std::vector<int64_t> root((size_t)M);
     std::vector<double> tsize((size_t)M, 0.0);
     for (int64_t j = 0; j < M; j++) {
@@ -501,7 +553,7 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     for (int64_t j = 0; j < M; j++) if (root[j] == j && tsize[j] > 0) trees.push_back(j);
     std::stable_sort(trees.begin(), trees.end(), [&](int64_t a, int64_t b) { return tsize[a] > tsize[b]; });
     std::vector<int32_t> ownerT((size_t)M, 0);
-    lpt(trees, tsize, ownerT);
+    lpt_assign(trees, tsize, NT, ownerT);
     std::vector<uint32_t> bOff((size_t)NT + 1, 0);
     for (int64_t j = 0; j < M; j++) if (parent[j] >= 0) bOff[ownerT[root[j]] + 1]++;
     for (int t = 0; t < NT; t++) bOff[t + 1] += bOff[t];
@@ -511,48 +563,238 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
         for (int64_t j = 0; j < M; j++)   // increasing j: parents before children
             if (parent[j] >= 0) bItem[pos[ownerT[root[j]]]++] = make_uint2((uint32_t)j, (uint32_t)parent[j]);
     }
-    P->fused_idx16 = idx16;
-    if ((st = upload(&P->d_fRowMeta, aItem, s)) || (st = upload(&P->d_fAOff, aOff, s)) ||
-        (st = upload(&P->d_fChain, bItem, s)) || (st = upload(&P->d_fBOff, bOff, s)) ||
-        (st = upload(&P->d_fCOff, P->h_xoff, s)) || (st = upload(&P->d_fCRefs, P->h_xrefs, s)) ||
-        (st = upload(&P->d_fIdx4, idx4, s)))
+    if ((st = upload(&P->d_fCflag, cf, s)) || (st = upload(&P->d_fChain, bItem, s)) || (st = upload(&P->d_fBOff, bOff, s)) ||
+        (st = upload(&P->d_fCOff, P->h_xoff, s)) || (st = upload(&P->d_fCRefs, P->h_xrefs, s)))
         return st;
-    P->fused_idx4 = (int64_t)idx4.size();
-    // the fused program needs measurement rows to have measurement parents
-    for (int64_t j = 0; j < M; j++)
-        if (parent[j] >= M) return set_error(SP_ERR_CUDA, "measurement row with a non-measurement parent");
 
-    // ---- shared-memory footprint and occupancy of the fused kernel --------
+    // ---- window counts that fit each tile width / occupancy ---------------
     int dev = 0, smem_max = 0, nsm = 0;
     SP_CUDA(cudaGetDevice(&dev));
     SP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     SP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     P->num_sms = nsm;
+    P->smem_max = smem_max;
     P->fused_tw = 0;
-    int64_t max_words32 = 0;
-    for (int64_t n : {P->n_meas, P->n_det, P->n_obs}) max_words32 = std::max<int64_t>(max_words32, 2 * ((n + 63) / 64));
-    for (int tw : {2, 1}) {
-        const int64_t bwords = ((P->n_sym + 1) * tw + 3) / 4 * 4;
-        const int64_t rwords = R * tw;
-        const int64_t stage_words = 32 * tw * (max_words32 + 1);
-        const int64_t words = std::max(bwords, stage_words) + rwords;
-        const int64_t bytes = words * 4;
-        if (bytes <= smem_max && R > 0 && nb > 0) {
-            P->fused_tw = tw;
-            P->fused_smem = (size_t)bytes;
-            P->fused_rec_off = (uint32_t)std::max(bwords, stage_words);
-            break;
-        }
-    }
-    if (P->fused_tw) {
-        void (*fn)(FusedParams) = P->fused_tw == 2 ? (P->fused_idx16 ? k_fused<2, true> : k_fused<2, false>)
-                                                   : (P->fused_idx16 ? k_fused<1, true> : k_fused<1, false>);
-        SP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->fused_smem));
-        int occ = 0;
-        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FUSED_THREADS, P->fused_smem));
-        P->fused_ctas_per_sm = std::max(occ, 1);
+    P->nw_half = min_windows(P, 1, (size_t)smem_max / 2 - 1024);
+    P->nw_full1 = min_windows(P, 1, (size_t)smem_max);
+    P->nw_full2 = min_windows(P, 2, (size_t)smem_max);
+    if (R > 0 && nb > 0) {
+        if (P->nw_half > 0) st = fused_select(P, 1, P->nw_half, 2);
+        else if (P->nw_full1 > 0) st = fused_select(P, 1, P->nw_full1, 2);
+        if (st != SP_OK) return st;
     }
     return SP_OK;
+}
+
+// Window boundaries (in channel blocks) for about nw windows of equal size.
+static std::vector<uint32_t> split_windows(const sp_program *P, int nw)
+{
+    const std::vector<uint32_t> &sym0 = P->h_blkSym0;
+    const uint32_t nb = (uint32_t)P->n_blk;
+    const uint64_t target = ((uint64_t)P->n_sym + nw - 1) / (uint64_t)nw;
+    std::vector<uint32_t> wb{0};
+    for (uint32_t b = 0; b < nb; b++) {
+        const uint64_t cur = sym0[b] - sym0[wb.back()];
+        const uint64_t add = sym0[b + 1] - sym0[b];
+        if (cur > 0 && cur + add > target) wb.push_back(b);
+    }
+    wb.push_back(nb);
+    return wb;
+}
+
+static uint32_t max_window(const sp_program *P, const std::vector<uint32_t> &wb)
+{
+    uint32_t mx = 0;
+    for (size_t w = 0; w + 1 < wb.size(); w++) mx = std::max(mx, P->h_blkSym0[wb[w + 1]] - P->h_blkSym0[wb[w]]);
+    return mx;
+}
+
+static size_t fused_words(const sp_program *P, int tw, uint32_t maxw, uint32_t *rec_off)
+{
+    int64_t max_words32 = 0;
+    for (int64_t n : {P->n_meas, P->n_det, P->n_obs}) max_words32 = std::max<int64_t>(max_words32, 2 * ((n + 63) / 64));
+    const int64_t bwords = (((int64_t)maxw + 1) * tw + 3) / 4 * 4;
+    const int64_t stage_words = 32 * tw * (max_words32 + 1);
+    if (rec_off) *rec_off = (uint32_t)std::max(bwords, stage_words);
+    return (size_t)(std::max(bwords, stage_words) + P->n_rows * tw);
+}
+
+int min_windows(const sp_program *P, int tw, size_t budget_bytes)
+{
+    if (P->n_rows == 0 || P->n_blk == 0) return 0;
+    for (int nw = 1; nw <= 1024; nw = nw < 8 ? nw + 1 : nw * 2) {
+        const std::vector<uint32_t> wb = split_windows(P, nw);
+        const uint32_t mx = max_window(P, wb);
+        if (mx >= 65535u) continue;   // window-relative indices are 16-bit
+        if (fused_words(P, tw, mx, nullptr) * 4 <= budget_bytes) return nw;
+        if (mx <= 16) break;          // windows cannot get smaller than a block
+    }
+    return 0;
+}
+
+// The (window, thread) item lists of one window count, built on demand.
+static sp_status get_layout(sp_program *P, int nw, FusedLayout **out)
+{
+    for (FusedLayout &L : P->layouts)
+        if (L.nw_req == nw) { *out = &L; return SP_OK; }
+    const std::vector<uint32_t> wb = split_windows(P, nw);
+    const int W = (int)wb.size() - 1;
+    const int NT = FUSED_THREADS;
+    const int64_t M = P->n_meas;
+    std::vector<uint32_t> wsym((size_t)W + 1);
+    for (int w = 0; w <= W; w++) wsym[w] = P->h_blkSym0[wb[w]];
+    std::vector<uint4> idx4, aItem;
+    std::vector<uint32_t> aOff((size_t)W * (NT + 1), 0);
+    std::vector<uint32_t> cursor(P->h_own_off.begin(), P->h_own_off.end() - 1);
+    for (int w = 0; w < W; w++) {
+        const uint32_t lo = wsym[w], hi = wsym[w + 1], zero = hi - lo;
+        std::vector<int64_t> items;          // rows with symbols in this window
+        std::vector<uint32_t> g0((size_t)M), ng((size_t)M, 0);
+        std::vector<double> cost((size_t)M, 0.0);
+        for (int64_t j = 0; j < M; j++) {
+            uint32_t a = cursor[j];
+            const uint32_t e = P->h_own_off[j + 1];
+            uint32_t b = a;
+            while (b < e && P->h_own_idx[b] < hi) b++;
+            cursor[j] = b;
+            if (b == a) continue;
+            g0[j] = (uint32_t)idx4.size();
+            for (uint32_t k = a; k < b; k += 8) {
+                uint32_t v[8];
+                for (uint32_t i = 0; i < 8; i++) v[i] = k + i < b ? P->h_own_idx[k + i] - lo : zero;
+                idx4.push_back(make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16)));
+            }
+            ng[j] = (uint32_t)(idx4.size() - g0[j]);
+            cost[j] = 1.0 + ng[j];
+            items.push_back(j);
+        }
+        std::stable_sort(items.begin(), items.end(), [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
+        std::vector<int32_t> owner((size_t)M, 0);
+        lpt_assign(items, cost, NT, owner);
+        uint32_t *ao = aOff.data() + (size_t)w * (NT + 1);
+        std::vector<uint32_t> cnt((size_t)NT, 0);
+        for (int64_t j : items) cnt[owner[j]]++;
+        ao[0] = (uint32_t)aItem.size();
+        for (int t = 0; t < NT; t++) ao[t + 1] = ao[t] + cnt[t];
+        std::vector<uint32_t> pos(ao, ao + NT);
+        aItem.resize(aItem.size() + items.size());
+        for (int64_t j : items) aItem[pos[owner[j]]++] = make_uint4(g0[j], ng[j], (uint32_t)j, 0u);
+    }
+    FusedLayout L;
+    L.nw_req = nw;
+    L.nw = W;
+    L.maxw = max_window(P, wb);
+    L.groups = (int64_t)idx4.size();
+    sp_status st;
+    if ((st = upload(&L.d_winBlk, wb, nullptr)) || (st = upload(&L.d_aItem, aItem, nullptr)) ||
+        (st = upload(&L.d_aOff, aOff, nullptr)) || (st = upload(&L.d_idx4, idx4, nullptr))) {
+        L.release();
+        return st;
+    }
+    SP_CUDA(cudaDeviceSynchronize());
+    P->layouts.push_back(L);
+    *out = &P->layouts.back();
+    return SP_OK;
+}
+
+typedef void (*FusedFn)(FusedParams);
+
+static FusedFn fused_kernel(int tw, int unroll)
+{
+    if (tw == 2) return unroll == 2 ? k_fused<2, 2> : k_fused<2, 1>;
+    return unroll == 2 ? k_fused<1, 2> : k_fused<1, 1>;
+}
+
+sp_status fused_select(sp_program *P, int tw, int nw, int unroll)
+{
+    if ((tw != 1 && tw != 2) || (unroll != 1 && unroll != 2) || nw < 1)
+        return set_error(SP_ERR_INVALID_ARG, "tile words must be 1 or 2, blocks per iteration 1 or 2, windows >= 1");
+    if (P->n_rows == 0 || P->n_blk == 0) return set_error(SP_ERR_INVALID_ARG, "nothing to sample on the fused path");
+    FusedLayout *L = nullptr;
+    sp_status st = get_layout(P, nw, &L);
+    if (st != SP_OK) return st;
+    uint32_t rec_off = 0;
+    const size_t bytes = fused_words(P, tw, L->maxw, &rec_off) * 4;
+    if (bytes > (size_t)P->smem_max)
+        return set_error(SP_ERR_INVALID_ARG, "that fused tile does not fit in shared memory; use more windows");
+    FusedFn fn = fused_kernel(tw, unroll);
+    // The limit is a property of the kernel, shared by every program: keep it
+    // at the device maximum so that no program's choice lowers another's.
+    SP_CUDA(max_dynamic_smem(fn));
+    int occ = 0;
+    SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FUSED_THREADS, bytes));
+    P->fused_tw = tw;
+    P->fused_unroll = unroll;
+    P->fused_layout = (int)(L - P->layouts.data());
+    P->fused_smem = bytes;
+    P->fused_rec_off = rec_off;
+    P->fused_ctas_per_sm = std::max(occ, 1);
+    return SP_OK;
+}
+
+// Autotuner: time the fused variants that fit -- 32-shot tiles with the
+// window count that allows two CTAs per SM or one, 64-shot tiles, one or
+// two channel blocks per draw iteration -- on a few tiles per SM and keep
+// the fastest.  The choice is cached per circuit shape for the process.
+sp_status autotune(sp_program *P, cudaStream_t s)
+{
+    if (!P->fused_tw) return SP_OK;
+    typedef std::tuple<int, int64_t, int64_t, int64_t, int64_t, int64_t> Key;
+    static std::mutex mu;
+    static std::map<Key, std::tuple<int, int, int>> cache;
+    const Key key{P->device, P->n_sym, P->n_rows, P->n_blk, P->nnz_delta, P->n_meas};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            P->tuned = true;
+            return fused_select(P, std::get<0>(it->second), std::get<1>(it->second), std::get<2>(it->second));
+        }
+    }
+    std::vector<std::tuple<int, int, int>> cand;
+    for (int u : {2, 1}) {
+        if (P->nw_half) cand.emplace_back(1, P->nw_half, u);
+        if (P->nw_full1 && P->nw_full1 != P->nw_half) cand.emplace_back(1, P->nw_full1, u);
+        if (P->nw_full2) cand.emplace_back(2, P->nw_full2, u);
+    }
+    const uint64_t shots = (uint64_t)P->num_sms * 2u * 64u * 4u;
+    const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
+    uint64_t *out = nullptr;
+    if (cudaMalloc((void **)&out, (size_t)shots * (size_t)std::max<int64_t>(wm + wd + wo, 1) * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SP_ERR_OOM, "cudaMalloc of the autotuner outputs failed");
+    }
+    uint64_t *om = out, *od = out + shots * wm, *oo = od + shots * wd;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::tuple<int, int, int> pick(P->fused_tw, P->layouts[P->fused_layout].nw_req, P->fused_unroll);
+    sp_status st = SP_OK;
+    const bool prof = P->profiling;
+    P->profiling = false;
+    for (const auto &c : cand) {
+        if ((st = fused_select(P, std::get<0>(c), std::get<1>(c), std::get<2>(c))) != SP_OK) break;
+        if ((st = fused_chunk(P, 1, 0, shots, om, od, oo, s)) != SP_OK) break;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 2 && st == SP_OK; k++) st = fused_chunk(P, 1, shots * (k + 1), shots, om, od, oo, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_error(cudaGetLastError(), "autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = c; }
+    }
+    P->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (st != SP_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[key] = pick;
+    }
+    P->tuned = true;
+    return fused_select(P, std::get<0>(pick), std::get<1>(pick), std::get<2>(pick));
 }
 
 sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *B,
@@ -565,34 +807,212 @@ sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0,
     return SP_OK;
 }
 
+static FusedParams fused_params(const sp_program *P, const FusedLayout &L, uint32_t rec_off, uint64_t seed,
+                                uint64_t shot0, uint64_t nshots, uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs)
+{
+    FusedParams fp;
+    fp.blkT = P->d_blkT; fp.blkMeta = P->d_blkMeta; fp.blkSym0 = P->d_blkSym0;
+    fp.n_sym = P->n_sym; fp.n_rows = P->n_rows; fp.n_meas = P->n_meas; fp.n_det = P->n_det; fp.n_obs = P->n_obs;
+    fp.nw = L.nw; fp.winBlk = L.d_winBlk; fp.aItem = L.d_aItem; fp.aOff = L.d_aOff; fp.idx4 = L.d_idx4;
+    fp.cflag = P->d_fCflag; fp.bItem = P->d_fChain; fp.bOff = P->d_fBOff;
+    fp.cOff = P->d_fCOff; fp.cRefs = P->d_fCRefs;
+    fp.seed = seed; fp.shot0 = shot0; fp.nshots = nshots;
+    fp.out[0] = d_meas; fp.out[1] = d_det; fp.out[2] = d_obs;
+    fp.rows0[0] = 0; fp.rows0[1] = P->n_meas; fp.rows0[2] = P->n_meas + P->n_det;
+    fp.nrow[0] = P->n_meas; fp.nrow[1] = P->n_det; fp.nrow[2] = P->n_obs;
+    fp.rec_off_words = rec_off;
+    return fp;
+}
+
 sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
                       uint64_t *d_det, uint64_t *d_obs, cudaStream_t s)
 {
     if (nshots == 0) return SP_OK;
     if (!P->fused_tw) return set_error(SP_ERR_INVALID_ARG, "fused path unavailable for this program");
-    FusedParams fp;
-    fp.blkT = P->d_blkT; fp.blkMeta = P->d_blkMeta; fp.blkSym0 = P->d_blkSym0; fp.n_blk = P->n_blk;
-    fp.n_sym = P->n_sym; fp.n_rows = P->n_rows; fp.n_meas = P->n_meas; fp.n_det = P->n_det; fp.n_obs = P->n_obs;
-    fp.aItem = P->d_fRowMeta; fp.aOff = P->d_fAOff; fp.bItem = P->d_fChain; fp.bOff = P->d_fBOff;
-    fp.cOff = P->d_fCOff; fp.cRefs = P->d_fCRefs; fp.idx4 = P->d_fIdx4;
-    fp.seed = seed; fp.shot0 = shot0; fp.nshots = nshots;
-    fp.out[0] = d_meas; fp.out[1] = d_det; fp.out[2] = d_obs;
-    fp.rows0[0] = 0; fp.rows0[1] = P->n_meas; fp.rows0[2] = P->n_meas + P->n_det;
-    fp.nrow[0] = P->n_meas; fp.nrow[1] = P->n_det; fp.nrow[2] = P->n_obs;
-    fp.rec_off_words = P->fused_rec_off;
+    const FusedParams fp = fused_params(P, P->layouts[P->fused_layout], P->fused_rec_off, seed, shot0, nshots,
+                                        d_meas, d_det, d_obs);
     const uint64_t per_tile = 32u * (uint64_t)P->fused_tw;
     const uint64_t ntiles = (nshots + per_tile - 1) / per_tile;
     const uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)P->num_sms * (uint64_t)P->fused_ctas_per_sm);
     ProfScope ps(P, SP_KERNEL_FUSED, s);
-    const dim3 g((unsigned)grid), b(FUSED_THREADS);
-    if (P->fused_tw == 2) {
-        if (P->fused_idx16) k_fused<2, true><<<g, b, P->fused_smem, s>>>(fp);
-        else k_fused<2, false><<<g, b, P->fused_smem, s>>>(fp);
-    } else {
-        if (P->fused_idx16) k_fused<1, true><<<g, b, P->fused_smem, s>>>(fp);
-        else k_fused<1, false><<<g, b, P->fused_smem, s>>>(fp);
-    }
+    FusedFn fn = fused_kernel(P->fused_tw, P->fused_unroll);
+    fn<<<dim3((unsigned)grid), dim3(FUSED_THREADS), P->fused_smem, s>>>(fp);
     SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched sampling: plan, capture, replay
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchClass {
+    FusedParams *d_params = nullptr;
+    uint64_t *d_tileEnd = nullptr;
+    unsigned long long *d_counter = nullptr;
+    int nprog = 0;
+    size_t smem = 0;
+    int minb = 1;
+    int grid = 0;
+};
+
+struct BatchPlan {
+    std::vector<uint64_t> key;
+    std::vector<const sp_program *> progs;
+    BatchClass cls[2];                 // [0] two CTAs per SM fit, [1] one
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~BatchPlan()
+    {
+        for (auto &c : cls) {
+            cudaFree(c.d_params);
+            cudaFree(c.d_tileEnd);
+            cudaFree(c.d_counter);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchPlan *> g_plans;
+cudaStream_t g_capture_stream[64] = {};
+
+}  // namespace
+
+void batch_forget(const sp_program *P)
+{
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (size_t i = 0; i < g_plans.size();) {
+        BatchPlan *b = g_plans[i];
+        if (std::find(b->progs.begin(), b->progs.end(), P) != b->progs.end()) {
+            delete b;
+            g_plans.erase(g_plans.begin() + i);
+        } else {
+            i++;
+        }
+    }
+}
+
+sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *seeds, const uint64_t *nshots,
+                       uint64_t *const *d_meas, uint64_t *const *d_det, uint64_t *const *d_obs, cudaStream_t s)
+{
+    int dev = 0;
+    SP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(SP_ERR_INVALID_ARG, "device ordinal out of range");
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)dev);
+    for (uint32_t i = 0; i < n; i++) {
+        if (progs[i]->device != dev) return set_error(SP_ERR_INVALID_ARG, "all programs must live on the current device");
+        key.insert(key.end(), {(uint64_t)(uintptr_t)progs[i], seeds[i], nshots[i],
+                               (uint64_t)(uintptr_t)(d_meas ? d_meas[i] : nullptr),
+                               (uint64_t)(uintptr_t)(d_det ? d_det[i] : nullptr),
+                               (uint64_t)(uintptr_t)(d_obs ? d_obs[i] : nullptr)});
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (BatchPlan *b : g_plans)
+        if (b->key == key) {
+            SP_CUDA(cudaGraphLaunch(b->exec, s));
+            return SP_OK;
+        }
+    // ---- new plan ---------------------------------------------------------
+    std::unique_ptr<BatchPlan> plan(new BatchPlan());
+    plan->key = key;
+    int smem_max = 0, nsm = 0;
+    SP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    SP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    struct Entry { uint32_t i; double cost; int nw; };
+    std::vector<Entry> fused[2];
+    std::vector<uint32_t> staged;
+    for (uint32_t i = 0; i < n; i++) {
+        const sp_program *P = progs[i];
+        plan->progs.push_back(P);
+        if (nshots[i] == 0) continue;
+        const bool fused_ok = P->path == SP_PATH_FUSED && P->fused_tw;
+        if (fused_ok && P->nw_half) fused[0].push_back({i, (double)P->n_blk, P->nw_half});
+        else if (fused_ok && P->nw_full1) fused[1].push_back({i, (double)P->n_blk, P->nw_full1});
+        else staged.push_back(i);
+    }
+    for (uint32_t i : staged) {
+        sp_program *P = progs[i];
+        sp_status st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots[i], (uint64_t)P->chunk_shots));
+        if (st != SP_OK) return st;
+    }
+    for (int c = 0; c < 2; c++) {
+        auto &v = fused[c];
+        if (v.empty()) continue;
+        std::stable_sort(v.begin(), v.end(), [](const Entry &a, const Entry &b) { return a.cost > b.cost; });
+        std::vector<FusedParams> params;
+        std::vector<uint64_t> tileEnd;
+        uint64_t acc = 0;
+        size_t smem = 0;
+        for (const Entry &e : v) {
+            sp_program *P = progs[e.i];
+            FusedLayout *L = nullptr;
+            sp_status st = get_layout(P, e.nw, &L);
+            if (st != SP_OK) return st;
+            uint32_t rec_off = 0;
+            const size_t bytes = fused_words(P, 1, L->maxw, &rec_off) * 4;
+            params.push_back(fused_params(P, *L, rec_off, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
+                                          d_det ? d_det[e.i] : nullptr, d_obs ? d_obs[e.i] : nullptr));
+            acc += (nshots[e.i] + 31) / 32;
+            tileEnd.push_back(acc);
+            smem = std::max(smem, bytes);
+        }
+        BatchClass &bc = plan->cls[c];
+        bc.nprog = (int)params.size();
+        bc.smem = smem;
+        bc.minb = c == 0 ? 2 : 1;
+        bc.grid = (int)std::min<uint64_t>(acc, (uint64_t)nsm * (uint64_t)bc.minb);
+        if (cudaMalloc((void **)&bc.d_params, params.size() * sizeof(FusedParams)) != cudaSuccess ||
+            cudaMalloc((void **)&bc.d_tileEnd, tileEnd.size() * 8) != cudaSuccess ||
+            cudaMalloc((void **)&bc.d_counter, 8) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(SP_ERR_OOM, "cudaMalloc of the batch plan failed");
+        }
+        SP_CUDA(cudaMemcpy(bc.d_params, params.data(), params.size() * sizeof(FusedParams), cudaMemcpyHostToDevice));
+        SP_CUDA(cudaMemcpy(bc.d_tileEnd, tileEnd.data(), tileEnd.size() * 8, cudaMemcpyHostToDevice));
+        if (c == 0) SP_CUDA(max_dynamic_smem(k_fused_batch<2>));
+        else SP_CUDA(max_dynamic_smem(k_fused_batch<1>));
+    }
+    // ---- capture on a library stream, replay on the caller's --------------
+    if (!g_capture_stream[dev]) SP_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
+    cudaStream_t cs = g_capture_stream[dev];
+    SP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    sp_status st = SP_OK;
+    for (int c = 0; c < 2 && st == SP_OK; c++) {
+        BatchClass &bc = plan->cls[c];
+        if (!bc.nprog) continue;
+        if (cudaMemsetAsync(bc.d_counter, 0, 8, cs) != cudaSuccess) { st = cuda_error(cudaGetLastError(), "memset"); break; }
+        if (c == 0) k_fused_batch<2><<<bc.grid, FUSED_THREADS, bc.smem, cs>>>(bc.d_params, bc.nprog, bc.d_tileEnd, bc.d_counter);
+        else k_fused_batch<1><<<bc.grid, FUSED_THREADS, bc.smem, cs>>>(bc.d_params, bc.nprog, bc.d_tileEnd, bc.d_counter);
+        if (cudaGetLastError() != cudaSuccess) st = set_error(SP_ERR_CUDA, "batch kernel launch failed during capture");
+    }
+    for (uint32_t i : staged) {
+        if (st != SP_OK) break;
+        sp_program *P = progs[i];
+        const int64_t pitch = (int64_t)((P->scratch_shots + 31) / 32);
+        const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
+        for (uint64_t done = 0; done < nshots[i] && st == SP_OK;) {
+            const uint64_t k = std::min<uint64_t>(nshots[i] - done, (uint64_t)pitch * 32u);
+            st = sample_chunk_into(P, P->d_B, P->d_recT, pitch, seeds[i], done, k,
+                                   d_meas && d_meas[i] ? d_meas[i] + done * wm : nullptr,
+                                   d_det && d_det[i] ? d_det[i] + done * wd : nullptr,
+                                   d_obs && d_obs[i] ? d_obs[i] + done * wo : nullptr, cs);
+            done += k;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (st != SP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ec != cudaSuccess) return cuda_error(ec, "cudaStreamEndCapture");
+    plan->graph = graph;
+    SP_CUDA(cudaGraphInstantiate(&plan->exec, graph, 0));
+    SP_CUDA(cudaGraphLaunch(plan->exec, s));
+    g_plans.push_back(plan.release());
     return SP_OK;
 }
 

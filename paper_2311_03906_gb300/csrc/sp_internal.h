@@ -53,9 +53,23 @@ struct TraverseCounts {
     uint32_t pad[2];
 };
 
-struct DeviceBuffer {
-    void *ptr = nullptr;
-    size_t bytes = 0;
+// Step-A program of the fused kernel for one window count: window
+// boundaries and, per (window, thread), the rows whose own part has symbols
+// in that window, with 16-bit window-relative symbol indices.
+struct FusedLayout {
+    int nw_req = 0;                   // window count asked for
+    int nw = 0;                       // windows produced
+    uint32_t maxw = 0;                // symbols in the largest window
+    int64_t groups = 0;
+    uint32_t *d_winBlk = nullptr;
+    uint4 *d_aItem = nullptr;
+    uint32_t *d_aOff = nullptr;
+    uint4 *d_idx4 = nullptr;
+    void release()
+    {
+        cudaFree(d_winBlk); cudaFree(d_aItem); cudaFree(d_aOff); cudaFree(d_idx4);
+        d_winBlk = nullptr; d_aItem = nullptr; d_aOff = nullptr; d_idx4 = nullptr;
+    }
 };
 
 // ----------------------------------------------------------------------------
@@ -120,20 +134,22 @@ struct sp_program {
     uint4 *d_blkT = nullptr;
     uint32_t *d_blkMeta = nullptr;
     uint32_t *d_blkSym0 = nullptr;
-    // fused product program (three steps, see sp_fused.cu)
-    uint4 *d_fRowMeta = nullptr;      // step A items {group offset, groups, row, const flag}, per thread
-    uint32_t *d_fAOff = nullptr;      // [threads+1]
+    // fused product program (see sp_fused.cu)
+    uint8_t *d_fCflag = nullptr;      // step 0: constant bit of each measurement row's own part
     uint2 *d_fChain = nullptr;        // step B items (row, parent), per thread, parents first
     uint32_t *d_fBOff = nullptr;      // [threads+1]
     uint32_t *d_fCOff = nullptr;      // step C: target t = XOR of measurement rows d_fCRefs[off[t]..off[t+1])
     uint32_t *d_fCRefs = nullptr;
-    uint4 *d_fIdx4 = nullptr;
-    int64_t fused_idx4 = 0;
-    bool fused_idx16 = false;        // 16-bit symbol indices (n_sym < 65535)
-    double fused_max_load = 0.0;     // largest per-thread product load (index groups + rows)
-    int fused_tw = 0;                 // shots per tile / 32 (0 = tile does not fit)
+    std::vector<sp::FusedLayout> layouts;   // per window count: windows and step-A items
+    std::vector<uint32_t> h_own_off, h_own_idx, h_blkSym0;  // host copies used to build layouts
+    int nw_half = 0, nw_full1 = 0, nw_full2 = 0;  // window counts that fit (0 = none)
+    int smem_max = 0;
+    int fused_tw = 0;                 // shots per tile / 32 (0 = fused path off)
+    int fused_unroll = 2;             // channel blocks per draw iteration
+    int fused_layout = 0;             // index into layouts
     size_t fused_smem = 0;
     uint32_t fused_rec_off = 0;
+    bool tuned = false;
     int fused_ctas_per_sm = 1;
     int num_sms = 0;
     // per-kernel event profiling (sp_profile_enable)
@@ -176,6 +192,12 @@ int64_t default_chunk(const sp_program *P);
 sp_status build_fused_program(sp_program *P, cudaStream_t s);
 sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
                       uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
+int min_windows(const sp_program *P, int tw, size_t budget_bytes);
+sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *seeds, const uint64_t *nshots,
+                       uint64_t *const *d_meas, uint64_t *const *d_det, uint64_t *const *d_obs, cudaStream_t s);
+void batch_forget(const sp_program *P);
+sp_status fused_select(sp_program *P, int tw, int nw, int unroll);
+sp_status autotune(sp_program *P, cudaStream_t s);
 sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *B,
                              int64_t pitch, cudaStream_t s);
 sp_status sample_chunk_into(const sp_program *P, uint32_t *B, uint32_t *recT, int64_t pitch,
@@ -187,5 +209,22 @@ sp_status expect_fwd(sp_program *P, const float *d_p, float *d_logE, cudaStream_
 sp_status expect_bwd(sp_program *P, const float *d_p, const float *d_g, float *d_grad, cudaStream_t s);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Raise a kernel's dynamic shared-memory limit to the most the device
+// allows next to its static shared memory.  The limit belongs to the kernel,
+// not to a program, so it is never lowered for one program's needs.
+template <typename F>
+inline cudaError_t max_dynamic_smem(F *kernel)
+{
+    int dev = 0, opt = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&opt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes a;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void *)kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 opt - (int)a.sharedSizeBytes);
+    return e;
+}
 
 }  // namespace sp

@@ -94,6 +94,24 @@ def test_records_match_oracle(name, shot0, shots, path):
     np.testing.assert_array_equal(_u64(o), ro)
 
 
+@pytest.mark.parametrize("tile,unroll,windows", [(32, 1, 0), (32, 2, 0), (64, 1, 0), (64, 2, 0),
+                                                 (32, 2, 3), (64, 1, 5), (32, 1, 16)])
+@pytest.mark.parametrize("name", ["rep5", "surf5", "layered40", "rand6"])
+def test_every_fused_variant_matches_oracle(name, tile, unroll, windows):
+    c = CIRCUITS[name]()
+    prog, ref = sp.build(c), oracle.Program(c)
+    prog.set_fused_config(tile, unroll, windows)
+    assert prog.info["fused_tile_shots"] == tile and prog.info["fused_blocks_per_iter"] == unroll
+    if windows:
+        assert prog.info["fused_windows"] >= min(windows, 2)
+    m, d, o = prog.sample(2113, seed=5, shot0=77)
+    torch.cuda.synchronize()
+    rm, rd, ro = ref.sample(5, 77, 2113)
+    np.testing.assert_array_equal(_u64(m), rm)
+    np.testing.assert_array_equal(_u64(d), rd)
+    np.testing.assert_array_equal(_u64(o), ro)
+
+
 def test_chunking_and_host_path_give_identical_records():
     c = surface_code(5, 5, 5e-3)
     prog = sp.build(c)
@@ -150,13 +168,16 @@ def test_full_size_d11_both_paths_agree(d11, path):
         prog.set_path(sp.PATH_AUTO)
 
 
-def test_full_size_d17_in_64k_chunks():
-    """d=17 r=17 p=2e-3 (the staged path: its fault tile does not fit in
-    shared memory), 1e6 shots sampled in 65536-shot chunks; 48 shots spread
-    over the range are recomputed by the oracle."""
+@pytest.mark.parametrize("path", ["fused", "staged"])
+def test_full_size_d17_in_64k_chunks(path):
+    """d=17 r=17 p=2e-3 (symbols drawn in several windows per tile on the
+    fused path), 1e6 shots sampled in 65536-shot chunks on the staged path;
+    48 shots spread over the range are recomputed by the oracle."""
     c = surface_code(17, 17, 2e-3)
     prog, ref = sp.build(c), oracle.Program(c)
-    assert prog.info["path"] == sp.PATH_SPARSE
+    assert prog.info["path"] == sp.PATH_FUSED and prog.info["fused_windows"] > 1
+    if path == "staged":
+        prog.set_path(sp.PATH_SPARSE)
     prog.set_chunk(65536)
     shots = 1_000_000
     m, d, o = prog.sample(shots, seed=3, shot0=0)
