@@ -193,6 +193,25 @@ def _batched_vs_plain(args):
     return res
 
 
+def run_profile_case():
+    """Small case for ncu: build the d=11 program, then sample 65536 shots
+    once. The autotuner's timing launches of the fused kernel come first;
+    their number is printed so a capture can skip them."""
+    import torch
+    import paper_2311_03906_gb300 as sp
+    from workloads import surface_code
+    prog = sp.build(surface_code(WORKLOAD["distance"], WORKLOAD["rounds"], WORKLOAD["p"]))
+    i = prog.info
+    shots = 65536
+    out = prog.alloc_outputs(shots)
+    prog.sample(shots, seed=1, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": WORKLOAD["name"], "shots": shots, "path": i["path"],
+                      "fused_tile_shots": i["fused_tile_shots"], "fused_windows": i["fused_windows"],
+                      "fused_blocks_per_iter": i["fused_blocks_per_iter"],
+                      "autotune_fused_launches": i["autotune_launches"]}))
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -344,9 +363,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-shots", type=int, default=100_000)
+    ap.add_argument("--profile", action="store_true",
+                    help="build, then one 65536-shot sample only (the case captured by ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile_case()
     else:
         run_ours(args)
 

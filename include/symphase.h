@@ -118,6 +118,8 @@ typedef struct {
     int32_t fused_tile_shots;      /* shots per fused tile (32 or 64; 0 = fused path unavailable) */
     int32_t fused_blocks_per_iter; /* channel blocks drawn per iteration of the fused kernel */
     int32_t fused_windows;         /* symbol windows per tile of the fused kernel */
+    int32_t autotune_launches;     /* fused-kernel launches the build-time autotuner made */
+    int32_t reserved;
     uint64_t chunk_shots;          /* shots per internal sampling chunk */
     double build_ms;               /* wall time of sp_build */
 } sp_info_t;

@@ -55,7 +55,8 @@ class sp_info_t(C.Structure):
                 ("num_random", C.c_uint64), ("nnz_rows", C.c_uint64), ("nnz_delta", C.c_uint64),
                 ("log_words", C.c_uint64), ("density", C.c_double), ("path", C.c_int32),
                 ("fused_tile_shots", C.c_int32), ("fused_blocks_per_iter", C.c_int32),
-                ("fused_windows", C.c_int32), ("chunk_shots", C.c_uint64), ("build_ms", C.c_double)]
+                ("fused_windows", C.c_int32), ("autotune_launches", C.c_int32), ("reserved", C.c_int32),
+                ("chunk_shots", C.c_uint64), ("build_ms", C.c_double)]
 
 
 _lib = None

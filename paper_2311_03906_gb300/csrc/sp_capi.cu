@@ -127,6 +127,7 @@ sp_status sp_info(const sp_program *P, sp_info_t *o)
     o->fused_tile_shots = 32 * P->fused_tw;
     o->fused_blocks_per_iter = P->fused_unroll;
     o->fused_windows = P->fused_tw ? P->layouts[P->fused_layout].nw : 0;
+    o->autotune_launches = P->autotune_launches;
     o->chunk_shots = (uint64_t)P->chunk_shots;
     o->build_ms = P->build_ms;
     return SP_OK;

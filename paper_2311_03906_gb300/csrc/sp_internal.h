@@ -150,6 +150,7 @@ struct sp_program {
     size_t fused_smem = 0;
     uint32_t fused_rec_off = 0;
     bool tuned = false;
+    int autotune_launches = 0;        // fused-kernel launches made by the autotuner
     int fused_ctas_per_sm = 1;
     int num_sms = 0;
     // per-kernel event profiling (sp_profile_enable)
