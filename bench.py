@@ -93,10 +93,8 @@ class ClockSampler:
 
 
 def _dist():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2311_03906_gb300.dist import world
+    return world()
 
 
 def _cpu_baseline(circuit, budget_s: float = 12.0, seed: int = 1):
@@ -232,10 +230,11 @@ def run_ours(args):
     shots = args.shots
     out = prog.alloc_outputs(shots)
     stream = torch.cuda.current_stream()
-    base = rank * shots * (args.steps + args.warmup + 2)
+    from paper_2311_03906_gb300.dist import max_over_ranks, shard_range
+    steps_total = args.steps + args.warmup + 4
 
     def step(i):
-        prog.sample(shots, seed=1, shot0=base + i * shots, out=out)
+        prog.sample(shots, seed=1, shot0=shard_range(rank, world, shots, i, steps_total)[0], out=out)
 
     for i in range(args.warmup):
         step(i)
@@ -257,19 +256,17 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, device="cuda")
         torch.distributed.barrier()
 
     # end to end through the public API with host buffers: D2H of every record
     hout = prog.alloc_outputs(shots, device="cpu", pin_memory=True)
-    prog.sample_host(shots, seed=7, shot0=base, out=hout)   # warm
+    prog.sample_host(shots, seed=7, shot0=shard_range(rank, world, shots, 0, steps_total)[0], out=hout)  # warm
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for i in range(e2e_steps):
-        prog.sample_host(shots, seed=7, shot0=base + i * shots, out=hout)
+        prog.sample_host(shots, seed=7, shot0=shard_range(rank, world, shots, i, steps_total)[0], out=hout)
     e2e_s = (time.perf_counter() - t1) / e2e_steps
     d2h = sum(t.numel() * 8 for t in hout)
 

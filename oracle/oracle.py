@@ -46,7 +46,9 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        # a test may point the wrapper at a deliberately broken copy of the
+        # oracle to check that the pins catch it
+        lib = C.CDLL(os.environ.get("SYMPHASE_ORACLE_LIB") or build())
         P, I64, U64 = C.c_void_p, C.c_int64, C.c_uint64
         ptr = C.c_void_p
         lib.or_build.restype = P

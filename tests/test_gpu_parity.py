@@ -8,8 +8,8 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import (Circuit, random_layered, random_small_circuit, repetition_code,
-                       surface_code)
+from workloads import (Circuit, random_clifford_circuit, random_layered, random_small_circuit,
+                       repetition_code, surface_code)
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +46,8 @@ CIRCUITS = {
 }
 for _s in range(8):
     CIRCUITS[f"rand{_s}"] = (lambda s=_s: random_small_circuit(3 + 7 * s, 60 + 30 * s, seed=900 + s))
+for _s in range(6):
+    CIRCUITS[f"cliff{_s}"] = (lambda s=_s: random_clifford_circuit(2 + 3 * s, 80 + 40 * s, seed=700 + s))
 
 
 def _u64(t):
@@ -77,7 +79,8 @@ def test_rows_match_oracle(name):
 
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
-@pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "wide1000", "rand3", "rand7"])
+@pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "wide1000", "rand3", "rand7",
+                                  "cliff2", "cliff5"])
 @pytest.mark.parametrize("shot0,shots", [(0, 1), (5, 31), (64, 33), (1 << 33, 1061), (7, 4101)])
 def test_records_match_oracle(name, shot0, shots, path):
     c = CIRCUITS[name]()

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from checkers import chp
-from workloads import random_small_circuit, repetition_code, surface_code
+from workloads import random_clifford_circuit, random_small_circuit, repetition_code, surface_code
 
 
 def _check(circuit, nassign, seed, density):
@@ -30,6 +30,15 @@ def test_random_circuits(seed):
     n = int(rng.integers(1, 21))
     circuit = random_small_circuit(n, int(rng.integers(10, 120)), seed=seed)
     _check(circuit, 6, seed, density=0.5)
+
+
+@pytest.mark.parametrize("seed", range(48))
+def test_clifford_heavy_circuits(seed):
+    """Long H/S/CX sequences with few measurements: deterministic outcomes
+    then depend on Y phases and on long products of stabilizer rows."""
+    rng = np.random.default_rng(2000 + seed)
+    circuit = random_clifford_circuit(int(rng.integers(2, 9)), int(rng.integers(20, 90)), seed=3000 + seed)
+    _check(circuit, 4, seed, density=0.5)
 
 
 def test_repetition_code():

@@ -367,6 +367,27 @@ def channel_probabilities(n_channels: int, lo: float = 5e-4, hi: float = 2e-3, s
     return rng.uniform(lo, hi, size=n_channels)
 
 
+def random_clifford_circuit(num_qubits: int, num_ops: int, seed: int, p_noise: float = 0.2) -> Circuit:
+    """Clifford-heavy random circuits: mostly H, S and CX (building Y
+    components and long products of stabilizers), some faults, rare
+    mid-circuit measurements, and a final measurement of every qubit."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(num_qubits)
+    kinds = ["H", "S", "CX", "X_ERROR", "DEPOLARIZE1", "DEPOLARIZE2", "M"]
+    probs = [0.3, 0.3, 0.25, 0.04, 0.04, 0.03, 0.04]
+    for _ in range(num_ops):
+        k = kinds[rng.choice(len(kinds), p=probs)]
+        if k in ("CX", "DEPOLARIZE2"):
+            if num_qubits < 2:
+                continue
+            a, b = rng.choice(num_qubits, size=2, replace=False)
+            c.append(k, [int(a), int(b)], p_noise if k == "DEPOLARIZE2" else 0.0)
+        else:
+            c.append(k, [int(rng.integers(num_qubits))], p_noise if k in NOISE_1Q else 0.0)
+    c.append("M", list(range(num_qubits)))
+    return c
+
+
 def random_small_circuit(num_qubits: int, num_ops: int, seed: int, p_noise: float = 0.2,
                          allow_reset: bool = True) -> Circuit:
     """Small random circuits over the whole op vocabulary for cross-checks:
