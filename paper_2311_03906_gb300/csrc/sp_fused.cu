@@ -168,43 +168,60 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
     // symbols, so U <= 2 keeps every inserted bit inside the 64-bit word.
     static_assert(U == 1 || U == 2, "at most two blocks per iteration");
     uint32_t b = b0;
+    // round-1 product M1*b, advanced by addition (it is the same in all lanes)
+    uint64_t ub = (uint64_t)PH_M1 * b;
     for (; b + U <= b1; b += U) {
         uint4 T[U];
         uint32_t meta[U];
         uint32_t r[U][TW][4];
-        uint32_t fm[U];
+        bool fire = false;
 #pragma unroll
         for (int v = 0; v < U; v++) {
             T[v] = blkT[b + v];
             meta[v] = blkMeta[b + v];
-            const uint64_t ub = (uint64_t)PH_M1 * (b + (uint32_t)v);
-            fm[v] = 0;
+            const uint64_t uv = ub + (uint64_t)v * PH_M1;
 #pragma unroll
             for (int t = 0; t < TW; t++) {
-                philox_block(sc.s[t], (uint32_t)(ub >> 32), (uint32_t)ub, K, r[v][t][0], r[v][t][1], r[v][t][2], r[v][t][3]);
-                fm[v] |= ((uint32_t)(r[v][t][0] < T[v].x) | ((uint32_t)(r[v][t][1] < T[v].y) << 1) |
-                          ((uint32_t)(r[v][t][2] < T[v].z) << 2) | ((uint32_t)(r[v][t][3] < T[v].w) << 3)) << (4 * t);
+                philox_block(sc.s[t], (uint32_t)(uv >> 32), (uint32_t)uv, K, r[v][t][0], r[v][t][1], r[v][t][2], r[v][t][3]);
+                fire |= (r[v][t][0] < T[v].x) | (r[v][t][1] < T[v].y) | (r[v][t][2] < T[v].z) | (r[v][t][3] < T[v].w);
             }
         }
+        ub += (uint64_t)U * PH_M1;
+        // Faults are rare: one vote decides whether any lane needs the
+        // channel bits of these blocks; then only the channels that fired in
+        // some lane are visited.
+        if (__any_sync(FM, fire)) {
+            uint32_t at = fill;
 #pragma unroll
-        for (int v = 0; v < U; v++) {
-            if (__any_sync(FM, fm[v] != 0u)) {
-                const uint32_t Ts[4] = {T[v].x, T[v].y, T[v].z, T[v].w};
+            for (int v = 0; v < U; v++) {
+                uint32_t fm[TW];
+                uint32_t any = 0;
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
+                for (int t = 0; t < TW; t++) {
+                    fm[t] = (uint32_t)(r[v][t][0] < T[v].x) | ((uint32_t)(r[v][t][1] < T[v].y) << 1) |
+                            ((uint32_t)(r[v][t][2] < T[v].z) << 2) | ((uint32_t)(r[v][t][3] < T[v].w) << 3);
+                    any |= fm[t];
+                }
+                uint32_t wm = __reduce_or_sync(FM, any);
+                while (wm) {
+                    const int i = __ffs(wm) - 1;
+                    wm &= wm - 1;
+                    const uint32_t kind = (meta[v] >> (2 * i)) & 3u;
+                    const uint32_t off = at + ((meta[v] >> (8 + 4 * i)) & 15u);
+                    const uint32_t Ti = i == 0 ? T[v].x : i == 1 ? T[v].y : i == 2 ? T[v].z : T[v].w;
 #pragma unroll
                     for (int t = 0; t < TW; t++) {
-                        const bool hit = (fm[v] >> (4 * t + i)) & 1u;
-                        if (__any_sync(FM, hit)) {
-                            const uint32_t kind = (meta[v] >> (2 * i)) & 3u;
-                            const uint32_t off = fill + ((meta[v] >> (8 + 4 * i)) & 15u);
-                            if (hit) acc[t] |= (uint64_t)chan_bits(r[v][t][i], Ts[i], kind) << off;
+                        if ((fm[t] >> i) & 1u) {
+                            const uint32_t u = i == 0 ? r[v][t][0] : i == 1 ? r[v][t][1] : i == 2 ? r[v][t][2] : r[v][t][3];
+                            acc[t] |= (uint64_t)chan_bits(u, Ti, kind) << off;
                         }
                     }
                 }
+                at += meta[v] >> 24;
             }
-            fill += meta[v] >> 24;
         }
+#pragma unroll
+        for (int v = 0; v < U; v++) fill += meta[v] >> 24;
         if (fill >= 32) flush();
     }
     for (; b < b1; b++) {
@@ -382,8 +399,10 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
     __syncthreads();
 }
 
+// Two CTAs per SM (64 registers) except the 64-shot, two-block variant,
+// which needs more registers than that without spilling.
 template <int TW, int U>
-__global__ void __launch_bounds__(FUSED_THREADS, (TW == 1 ? 2 : 1)) k_fused(FusedParams p)
+__global__ void __launch_bounds__(FUSED_THREADS, (TW == 2 && U == 2) ? 1 : 2) k_fused(FusedParams p)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const uint64_t per_tile = 32u * TW;
@@ -578,6 +597,7 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     P->nw_half = min_windows(P, 1, (size_t)smem_max / 2 - 1024);
     P->nw_full1 = min_windows(P, 1, (size_t)smem_max);
     P->nw_full2 = min_windows(P, 2, (size_t)smem_max);
+    P->nw_half2 = min_windows(P, 2, (size_t)smem_max / 2 - 1024);
     if (R > 0 && nb > 0) {
         if (P->nw_half > 0) st = fused_select(P, 1, P->nw_half, 2);
         else if (P->nw_full1 > 0) st = fused_select(P, 1, P->nw_full1, 2);
@@ -756,6 +776,7 @@ sp_status autotune(sp_program *P, cudaStream_t s)
         if (P->nw_half) cand.emplace_back(1, P->nw_half, u);
         if (P->nw_full1 && P->nw_full1 != P->nw_half) cand.emplace_back(1, P->nw_full1, u);
         if (P->nw_full2) cand.emplace_back(2, P->nw_full2, u);
+        if (P->nw_half2 && P->nw_half2 != P->nw_full2) cand.emplace_back(2, P->nw_half2, u);
     }
     const uint64_t shots = (uint64_t)P->num_sms * 2u * 64u * 4u;
     const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;

@@ -142,7 +142,7 @@ struct sp_program {
     uint32_t *d_fCRefs = nullptr;
     std::vector<sp::FusedLayout> layouts;   // per window count: windows and step-A items
     std::vector<uint32_t> h_own_off, h_own_idx, h_blkSym0;  // host copies used to build layouts
-    int nw_half = 0, nw_full1 = 0, nw_full2 = 0;  // window counts that fit (0 = none)
+    int nw_half = 0, nw_full1 = 0, nw_full2 = 0, nw_half2 = 0;  // window counts that fit (0 = none)
     int smem_max = 0;
     int fused_tw = 0;                 // shots per tile / 32 (0 = fused path off)
     int fused_unroll = 2;             // channel blocks per draw iteration
