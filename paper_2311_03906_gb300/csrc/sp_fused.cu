@@ -3,9 +3,14 @@
 // Algorithm 1 "Sampling" (arXiv 2311.03906, Sec. 3.2.3, Eq. sampling) for a
 // tile of 32*TW shots per CTA iteration, entirely in shared memory:
 //   phase 1  draw: Philox4x32-10 keyed by (seed, shot, channel/4); each warp
-//            owns a contiguous range of 4-channel blocks, lane = shot, and
-//            writes the bit-sliced fault word of every symbol of its range
-//            (bit = shot within the tile) into the tile B_s;
+//            owns a contiguous range of 4-channel blocks and the symbols they
+//            feed, lane = shot.  It zeroes those symbols in the tile B_s, then
+//            per block draws, compares with the four thresholds and votes;
+//            only a block where some channel fired in some lane (rare at
+//            circuit-level noise) writes: a warp ballot per fired one-symbol
+//            channel (bit = shot within the tile), and a queued event per
+//            lane whose depolarizing channels fired, resolved later by all
+//            lanes of the warp together;
 //   phase 2  product: (A) every measurement row's own part, c'_j ^ XOR of
 //            B_s over its delta symbols, for all rows in parallel; (B) the
 //            parent chains m_j ^= m_parent; (C) detectors and observables as
@@ -13,8 +18,8 @@
 //   phase 3  emit: 32x32 warp transposes turn the bit-sliced rows into
 //            shot-major packed words, staged in shared memory and written as
 //            contiguous per-shot segments.
-// Nothing but the records touches HBM.  The same draw code also serves the
-// staged path (fault bits to global memory) used when the tile does not fit.
+// Nothing but the records touches HBM.  The staged path (fault bits to global
+// memory) draws with a dense variant that transposes 32-symbol groups.
 //
 // Philox per (shot, channel block b): counter (shot lo, shot hi, b, 0).
 // Round 1's product M1*b is the same for every lane (one per warp), and the
@@ -89,18 +94,10 @@ __device__ __forceinline__ Keys make_keys(uint32_t k0, uint32_t k1)
     return K;
 }
 
-// Rounds 1..10 of Philox4x32-10 for counter (shot, b): uhi/ulo = M1*b.
-__device__ __forceinline__ void philox_block(const ShotConst &s, uint32_t uhi, uint32_t ulo, const Keys &K,
-                                             uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
+// Rounds 3..10 of Philox4x32-10 from the state (c0, c1, c2, c3) after round 2.
+__device__ __forceinline__ void philox_tail(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const Keys &K,
+                                            uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
 {
-    // round 1 (counter word 3 is 0)
-    const uint32_t x0 = uhi ^ s.c1 ^ K.k0[0];
-    // round 2
-    const uint64_t p = (uint64_t)PH_M0 * x0;
-    uint32_t c0 = s.r2hi ^ ulo ^ K.k0[1];
-    uint32_t c1 = s.r2lo;
-    uint32_t c2 = (uint32_t)(p >> 32) ^ s.x3 ^ K.k1[1];
-    uint32_t c3 = (uint32_t)p;
 #pragma unroll
     for (int r = 2; r < 10; r++) {
         const uint64_t p0 = (uint64_t)PH_M0 * c0;
@@ -113,6 +110,24 @@ __device__ __forceinline__ void philox_block(const ShotConst &s, uint32_t uhi, u
         c2 = n2;
     }
     o0 = c0; o1 = c1; o2 = c2; o3 = c3;
+}
+
+// Rounds 1..10 of Philox4x32-10 for counter (shot, b): uhi/ulo = M1*b and
+// shot_hi = the shot's high word s.c1.  Round 1's output word 0 is
+// uhi ^ shot_hi ^ k0 and round 2 multiplies it by M0: that product p is all
+// of round 2 that depends on b, so a caller that knows it to be the same in
+// several evaluations may compute it once and call philox_from_p.
+__device__ __forceinline__ void philox_from_p(const ShotConst &s, uint64_t p, uint32_t ulo, const Keys &K,
+                                              uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
+{
+    philox_tail(s.r2hi ^ ulo ^ K.k0[1], s.r2lo, (uint32_t)(p >> 32) ^ s.x3 ^ K.k1[1], (uint32_t)p, K, o0, o1, o2, o3);
+}
+
+__device__ __forceinline__ void philox_block(const ShotConst &s, uint32_t shot_hi, uint32_t uhi, uint32_t ulo,
+                                             const Keys &K, uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
+{
+    const uint64_t p = (uint64_t)PH_M0 * (uhi ^ shot_hi ^ K.k0[0]);
+    philox_from_p(s, p, ulo, K, o0, o1, o2, o3);
 }
 
 // floor(u*m/T) for u < T, exactly: a single-precision estimate (relative
@@ -182,7 +197,7 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
             const uint64_t uv = ub + (uint64_t)v * PH_M1;
 #pragma unroll
             for (int t = 0; t < TW; t++) {
-                philox_block(sc.s[t], (uint32_t)(uv >> 32), (uint32_t)uv, K, r[v][t][0], r[v][t][1], r[v][t][2], r[v][t][3]);
+                philox_block(sc.s[t], sc.s[t].c1, (uint32_t)(uv >> 32), (uint32_t)uv, K, r[v][t][0], r[v][t][1], r[v][t][2], r[v][t][3]);
                 fire |= (r[v][t][0] < T[v].x) | (r[v][t][1] < T[v].y) | (r[v][t][2] < T[v].z) | (r[v][t][3] < T[v].w);
             }
         }
@@ -232,7 +247,7 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
 #pragma unroll
         for (int t = 0; t < TW; t++) {
             uint32_t r[4];
-            philox_block(sc.s[t], (uint32_t)(ub >> 32), (uint32_t)ub, K, r[0], r[1], r[2], r[3]);
+            philox_block(sc.s[t], sc.s[t].c1, (uint32_t)(ub >> 32), (uint32_t)ub, K, r[0], r[1], r[2], r[3]);
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const uint32_t kind = (meta >> (2 * i)) & 3u;
@@ -254,6 +269,187 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
     }
 }
 
+// Fired-event queue of one warp: FUSED_QCAP 32-bit words in shared memory.
+// An event is one (channel block, shot) in which at least one of the block's
+// depolarizing channels fired: bits 16..31 block - first block of the
+// window, bit 9 tile word t, bits 4..8 lane, bits 0..3 the fired channels.
+constexpr uint32_t FUSED_QCAP = 128;
+// Channel blocks whose compare results are gathered before one vote.
+constexpr uint32_t DRAW_GROUP = 8;
+
+// Apply the queued events e = lane, lane+32, ... < n: recompute the event's
+// Philox block, turn each fired channel into its symbol bits and set the
+// shot's bit in those symbols' words of the tile Bw (shared atomics: two
+// shots of one channel may meet in a word, rarely at circuit-level noise).
+template <int TW>
+__device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const uint4 *__restrict__ blkT,
+                                            const uint32_t *__restrict__ blkMeta, const uint32_t *__restrict__ blkSym0,
+                                            uint32_t wb0, uint32_t wsym0, uint64_t shot_base, const Keys &K,
+                                            uint32_t k1, int lane, uint32_t *Bw)
+{
+    __syncwarp();
+    for (uint32_t e = lane; e < n; e += 32) {
+        const uint32_t ev = q[e];
+        const uint32_t b = wb0 + (ev >> 16);
+        const uint32_t t = (ev >> 9) & 1u, ln = (ev >> 4) & 31u;
+        uint32_t fmask = ev & 15u;
+        const ShotConst s = shot_const(shot_base + 32u * t + ln, k1);
+        const uint64_t ub = (uint64_t)PH_M1 * b;
+        uint32_t r0, r1, r2, r3;
+        philox_block(s, s.c1, (uint32_t)(ub >> 32), (uint32_t)ub, K, r0, r1, r2, r3);
+        const uint4 T = blkT[b];
+        const uint32_t meta = blkMeta[b], s0 = blkSym0[b] - wsym0;
+        while (fmask) {
+            const int i = __ffs(fmask) - 1;
+            fmask &= fmask - 1;
+            const uint32_t kind = (meta >> (2 * i)) & 3u;
+            const uint32_t off = s0 + ((meta >> (8 + 4 * i)) & 15u);
+            const uint32_t Ti = i == 0 ? T.x : i == 1 ? T.y : i == 2 ? T.z : T.w;
+            const uint32_t u = i == 0 ? r0 : i == 1 ? r1 : i == 2 ? r2 : r3;
+            uint32_t val = chan_bits(u, Ti, kind);
+            while (val) {
+                const int j = __ffs(val) - 1;
+                val &= val - 1;
+                atomicOr(&Bw[(off + j) * TW + t], 1u << ln);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Fired mask of one Philox block: bit i = channel i of the block fired.
+__device__ __forceinline__ uint32_t fired4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, const uint4 T)
+{
+    return (uint32_t)(r0 < T.x) | ((uint32_t)(r1 < T.y) << 1) | ((uint32_t)(r2 < T.z) << 2) |
+           ((uint32_t)(r3 < T.w) << 3);
+}
+
+// Draw the symbols of blocks [b0, b1) of the window starting at block wb0
+// (symbol wsym0) for 32*TW shots into the bit-sliced tile Bw (TW 32-bit
+// words per symbol, index (s - wsym0)*TW + t).  The warp owns the symbols of
+// its blocks and zeroes them first.  Per group of DRAW_GROUP blocks each lane
+// gathers the fired masks of its shots' channels (4 bits per block) into one
+// word per tile word, and the warp votes once.  Faults are rare at
+// circuit-level noise: for a group that fired, a one-symbol channel (a
+// Pauli error or a random outcome) has its symbol word as a ballot of the
+// fired bits, stored directly, and the lanes whose depolarizing channels
+// fired append one event per (block, shot) to the warp's queue q, which all
+// 32 lanes drain together when it fills and at the end.  UHI: every shot of
+// the tile has the same high counter word c1u, so round 2's M0 product is the
+// same in all lanes.
+template <int TW, int U, bool UHI>
+__device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
+                                                const uint32_t *__restrict__ blkSym0, uint32_t wb0, uint32_t b0,
+                                                uint32_t b1, uint32_t wsym0, const Shots<TW> sc, uint64_t shot_base,
+                                                uint32_t k0, uint32_t k1, int lane, uint32_t *Bw, uint32_t *q)
+{
+    static_assert(U == 1 || U == 2, "one or two blocks per step");
+    static_assert(TW == 1 || TW == 2, "one or two tile words");
+    {
+        const uint32_t lo = (blkSym0[b0] - wsym0) * TW, hi = (blkSym0[b1] - wsym0) * TW;
+        for (uint32_t i = lo + lane; i < hi; i += 32) Bw[i] = 0u;
+    }
+    __syncwarp();   // lane 0 may store into words that other lanes zeroed
+    const Keys K = make_keys(k0, k1);
+    const uint32_t c1u = (uint32_t)(shot_base >> 32);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t cnt = 0;
+    auto resolve = [&](uint32_t g, const uint32_t (&word)[TW]) {
+        uint32_t any = 0;
+#pragma unroll
+        for (int t = 0; t < TW; t++) any |= word[t];
+        uint32_t wm = __reduce_or_sync(FM, any);
+        uint32_t dep = 0;
+        while (wm) {
+            const int bit = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const uint32_t b = g + (uint32_t)(bit >> 2);
+            const int i = bit & 3;
+            const uint32_t meta = blkMeta[b];
+            const uint32_t kind = (meta >> (2 * i)) & 3u;
+            if (kind == CK_DEP1 || kind == CK_DEP2) {
+                dep |= 1u << bit;
+                continue;
+            }
+            const uint32_t off = blkSym0[b] - wsym0 + ((meta >> (8 + 4 * i)) & 15u);
+#pragma unroll
+            for (int t = 0; t < TW; t++) {
+                const uint32_t w = __ballot_sync(FM, (word[t] >> bit) & 1u);
+                if (lane == 0 && w) Bw[off * TW + t] = w;
+            }
+        }
+        if (!dep) return;
+#pragma unroll
+        for (int t = 0; t < TW; t++) {
+            uint32_t m = word[t] & dep;
+            while (__any_sync(FM, m != 0u)) {
+                if (cnt > FUSED_QCAP - 32u) {
+                    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, wb0, wsym0, shot_base, K, k1, lane, Bw);
+                    cnt = 0;
+                }
+                const int k = m ? (__ffs(m) - 1) >> 2 : 0;
+                const uint32_t nib = (m >> (4 * k)) & 15u;
+                const uint32_t bal = __ballot_sync(FM, nib != 0u);
+                if (nib)
+                    q[cnt + __popc(bal & lt)] =
+                        ((g + (uint32_t)k - wb0) << 16) | ((uint32_t)t << 9) | ((uint32_t)lane << 4) | nib;
+                cnt += __popc(bal);
+                m &= ~(15u << (4 * k));
+            }
+        }
+    };
+    // block g+kk of a group: bit 4*kk+i of word[t] = channel i fired in
+    // shot t of this lane
+    auto step = [&](uint32_t g, uint32_t kk, uint64_t ub, uint32_t (&word)[TW]) {
+        const uint4 T = blkT[g + kk];
+        const uint32_t uhi = (uint32_t)(ub >> 32), ulo = (uint32_t)ub;
+        const uint32_t bit = 1u << (4 * kk);
+        uint64_t p = 0;
+        if (UHI) p = (uint64_t)PH_M0 * (uhi ^ c1u ^ K.k0[0]);
+#pragma unroll
+        for (int t = 0; t < TW; t++) {
+            if (!UHI) p = (uint64_t)PH_M0 * (uhi ^ sc.s[t].c1 ^ K.k0[0]);
+            uint32_t r0, r1, r2, r3;
+            philox_from_p(sc.s[t], p, ulo, K, r0, r1, r2, r3);
+            if (r0 < T.x) word[t] |= bit;
+            if (r1 < T.y) word[t] |= bit << 1;
+            if (r2 < T.z) word[t] |= bit << 2;
+            if (r3 < T.w) word[t] |= bit << 3;
+        }
+    };
+    for (uint32_t g = b0; g < b1; g += DRAW_GROUP) {
+        uint32_t word[TW];
+#pragma unroll
+        for (int t = 0; t < TW; t++) word[t] = 0u;
+        const uint64_t ug = (uint64_t)PH_M1 * g;
+        if (b1 - g >= DRAW_GROUP) {
+#pragma unroll
+            for (uint32_t kk = 0; kk < DRAW_GROUP; kk++) step(g, kk, ug + (uint64_t)kk * PH_M1, word);
+        } else {
+#pragma unroll 1
+            for (uint32_t kk = 0; kk < b1 - g; kk++) step(g, kk, ug + (uint64_t)kk * PH_M1, word);
+        }
+        uint32_t any = 0;
+#pragma unroll
+        for (int t = 0; t < TW; t++) any |= word[t];
+        if (__any_sync(FM, any != 0u)) resolve(g, word);
+    }
+    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, wb0, wsym0, shot_base, K, k1, lane, Bw);
+}
+
+template <int TW, int U>
+__device__ __forceinline__ void draw_scatter(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
+                                             const uint32_t *__restrict__ blkSym0, uint32_t wb0, uint32_t b0,
+                                             uint32_t b1, uint32_t wsym0, const Shots<TW> sc, uint64_t shot_base,
+                                             uint32_t k0, uint32_t k1, int lane, uint32_t *Bw, uint32_t *q)
+{
+    // a tile straddles a multiple of 2^32 shots only if shot0 is unaligned
+    if ((shot_base >> 32) == ((shot_base + 32u * TW - 1u) >> 32))
+        draw_group_impl<TW, U, true>(blkT, blkMeta, blkSym0, wb0, b0, b1, wsym0, sc, shot_base, k0, k1, lane, Bw, q);
+    else
+        draw_group_impl<TW, U, false>(blkT, blkMeta, blkSym0, wb0, b0, b1, wsym0, sc, shot_base, k0, k1, lane, Bw, q);
+}
+
 struct FusedParams {
     const uint4 *blkT;
     const uint32_t *blkMeta;
@@ -273,6 +469,7 @@ struct FusedParams {
     uint64_t *out[3];
     int64_t rows0[3], nrow[3];
     uint32_t rec_off_words;    // offset of R_s in shared memory (u32 words)
+    uint32_t q_off_words;      // offset of the warps' fired-event queues (u32 words)
 };
 
 template <int TW> struct TileWord;
@@ -326,12 +523,9 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
         const uint32_t nbw = wb1 - wb0;
         const uint32_t b0 = wb0 + (uint32_t)((uint64_t)warp * nbw / nwarps);
         const uint32_t b1 = wb0 + (uint32_t)((uint64_t)(warp + 1) * nbw / nwarps);
-        const uint32_t send = p.blkSym0[b1];
         if (tid == 0) Bs[wsize] = TWd::zero();
-        draw_blocks<TW, U>(p.blkT, p.blkMeta, b0, b1, p.blkSym0[b0], sc, k0, k1, lane,
-                           [=](uint32_t base, const Cols<TW> col) {
-                               if (base + lane < send) Bs[base + lane - wsym0] = TWd::make(col);
-                           });
+        draw_scatter<TW, U>(p.blkT, p.blkMeta, p.blkSym0, wb0, b0, b1, wsym0, sc, p.shot0 + trel, k0, k1, lane,
+                            reinterpret_cast<uint32_t *>(Bs), sm + p.q_off_words + warp * FUSED_QCAP);
         __syncthreads();
         // ---- phase 2A: own parts over this window's symbols -------------------
         {
@@ -636,7 +830,7 @@ static size_t fused_words(const sp_program *P, int tw, uint32_t maxw, uint32_t *
     const int64_t bwords = (((int64_t)maxw + 1) * tw + 3) / 4 * 4;
     const int64_t stage_words = 32 * tw * (max_words32 + 1);
     if (rec_off) *rec_off = (uint32_t)std::max(bwords, stage_words);
-    return (size_t)(std::max(bwords, stage_words) + P->n_rows * tw);
+    return (size_t)(std::max(bwords, stage_words) + P->n_rows * tw) + (FUSED_THREADS / 32) * FUSED_QCAP;
 }
 
 int min_windows(const sp_program *P, int tw, size_t budget_bytes)
@@ -839,7 +1033,7 @@ sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0,
     return SP_OK;
 }
 
-static FusedParams fused_params(const sp_program *P, const FusedLayout &L, uint32_t rec_off, uint64_t seed,
+static FusedParams fused_params(const sp_program *P, const FusedLayout &L, int tw, uint32_t rec_off, uint64_t seed,
                                 uint64_t shot0, uint64_t nshots, uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs)
 {
     FusedParams fp;
@@ -853,6 +1047,7 @@ static FusedParams fused_params(const sp_program *P, const FusedLayout &L, uint3
     fp.rows0[0] = 0; fp.rows0[1] = P->n_meas; fp.rows0[2] = P->n_meas + P->n_det;
     fp.nrow[0] = P->n_meas; fp.nrow[1] = P->n_det; fp.nrow[2] = P->n_obs;
     fp.rec_off_words = rec_off;
+    fp.q_off_words = rec_off + (uint32_t)(P->n_rows * tw);
     return fp;
 }
 
@@ -861,7 +1056,7 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
 {
     if (nshots == 0) return SP_OK;
     if (!P->fused_tw) return set_error(SP_ERR_INVALID_ARG, "fused path unavailable for this program");
-    const FusedParams fp = fused_params(P, P->layouts[P->fused_layout], P->fused_rec_off, seed, shot0, nshots,
+    const FusedParams fp = fused_params(P, P->layouts[P->fused_layout], P->fused_tw, P->fused_rec_off, seed, shot0, nshots,
                                         d_meas, d_det, d_obs);
     const uint64_t per_tile = 32u * (uint64_t)P->fused_tw;
     const uint64_t ntiles = (nshots + per_tile - 1) / per_tile;
@@ -985,7 +1180,7 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
             if (st != SP_OK) return st;
             uint32_t rec_off = 0;
             const size_t bytes = fused_words(P, 1, L->maxw, &rec_off) * 4;
-            params.push_back(fused_params(P, *L, rec_off, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
+            params.push_back(fused_params(P, *L, 1, rec_off, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
                                           d_det ? d_det[e.i] : nullptr, d_obs ? d_obs[e.i] : nullptr));
             acc += (nshots[e.i] + 31) / 32;
             tileEnd.push_back(acc);
