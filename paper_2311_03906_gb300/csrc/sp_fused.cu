@@ -276,6 +276,7 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
 constexpr uint32_t FUSED_QCAP = 128;
 // Channel blocks whose compare results are gathered before one vote.
 constexpr uint32_t DRAW_GROUP = 8;
+static_assert(4 * DRAW_GROUP == 32, "a group's channels map one to one onto the lanes");
 
 // Apply the queued events e = lane, lane+32, ... < n: recompute the event's
 // Philox block, turn each fired channel into its symbol bits and set the
@@ -327,16 +328,15 @@ __device__ __forceinline__ uint32_t fired4(uint32_t r0, uint32_t r1, uint32_t r2
 // Draw the symbols of blocks [b0, b1) of the window starting at block wb0
 // (symbol wsym0) for 32*TW shots into the bit-sliced tile Bw (TW 32-bit
 // words per symbol, index (s - wsym0)*TW + t).  The warp owns the symbols of
-// its blocks and zeroes them first.  Per group of DRAW_GROUP blocks each lane
-// gathers the fired masks of its shots' channels (4 bits per block) into one
-// word per tile word, and the warp votes once.  Faults are rare at
-// circuit-level noise: for a group that fired, a one-symbol channel (a
-// Pauli error or a random outcome) has its symbol word as a ballot of the
-// fired bits, stored directly, and the lanes whose depolarizing channels
-// fired append one event per (block, shot) to the warp's queue q, which all
-// 32 lanes drain together when it fills and at the end.  UHI: every shot of
-// the tile has the same high counter word c1u, so round 2's M0 product is the
-// same in all lanes.
+// its blocks and zeroes them first.  Per group of DRAW_GROUP blocks (32
+// channels) each lane gathers the fired bits of its shots' channels into one
+// word per tile word, and the warp votes once; faults are rare at
+// circuit-level noise, so most of the time goes to Philox.  A group that
+// fired is resolved lane-parallel (lane j = channel j of the group), with
+// the depolarizing channels' events queued in q and drained by all 32 lanes
+// when it fills and at the end.  UHI: every shot of the tile has the same
+// high counter word c1u, so round 2's M0 product is the same in all lanes
+// and tile words.
 template <int TW, int U, bool UHI>
 __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
                                                 const uint32_t *__restrict__ blkSym0, uint32_t wb0, uint32_t b0,
@@ -354,28 +354,29 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
     const uint32_t c1u = (uint32_t)(shot_base >> 32);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t cnt = 0;
-    auto resolve = [&](uint32_t g, const uint32_t (&word)[TW]) {
+    // A group that fired in some lane.  Lane j stands for channel j&3 of
+    // block g + j/4 (its descriptor jmeta, first symbol js0).  One 32x32
+    // transpose per tile word gives lane j the shots in which its channel
+    // fired; a one-symbol channel (a Pauli error or a random outcome) stores
+    // that word as its symbol's word.  Depolarizing channels need the
+    // category index: the lanes whose shots fired one are queued, one event
+    // per (block, shot), with room for 32 events ensured before each append.
+    auto resolve = [&](uint32_t g, const uint32_t (&word)[TW], uint32_t jmeta, uint32_t js0) {
         uint32_t any = 0;
 #pragma unroll
         for (int t = 0; t < TW; t++) any |= word[t];
-        uint32_t wm = __reduce_or_sync(FM, any);
-        uint32_t dep = 0;
-        while (wm) {
-            const int bit = __ffs(wm) - 1;
-            wm &= wm - 1;
-            const uint32_t b = g + (uint32_t)(bit >> 2);
-            const int i = bit & 3;
-            const uint32_t meta = blkMeta[b];
-            const uint32_t kind = (meta >> (2 * i)) & 3u;
-            if (kind == CK_DEP1 || kind == CK_DEP2) {
-                dep |= 1u << bit;
-                continue;
-            }
-            const uint32_t off = blkSym0[b] - wsym0 + ((meta >> (8 + 4 * i)) & 15u);
+        const uint32_t wm = __reduce_or_sync(FM, any);
+        const int i = lane & 3;
+        const uint32_t kind = (jmeta >> (2 * i)) & 3u;
+        const bool mine = (wm >> lane) & 1u;
+        const bool is_dep = kind == CK_DEP1 || kind == CK_DEP2;
+        const uint32_t dep = __ballot_sync(FM, mine && is_dep);
+        if (wm & ~dep) {
+            const uint32_t off = js0 - wsym0 + ((jmeta >> (8 + 4 * i)) & 15u);
 #pragma unroll
             for (int t = 0; t < TW; t++) {
-                const uint32_t w = __ballot_sync(FM, (word[t] >> bit) & 1u);
-                if (lane == 0 && w) Bw[off * TW + t] = w;
+                const uint32_t col = transpose32(word[t], lane);
+                if (mine && !is_dep) Bw[off * TW + t] = col;
             }
         }
         if (!dep) return;
@@ -418,6 +419,12 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
         }
     };
     for (uint32_t g = b0; g < b1; g += DRAW_GROUP) {
+        // descriptor of lane j's channel, used only if the group fired
+        uint32_t jmeta = 0, js0 = 0;
+        if (g + (uint32_t)(lane >> 2) < b1) {
+            jmeta = blkMeta[g + (lane >> 2)];
+            js0 = blkSym0[g + (lane >> 2)];
+        }
         uint32_t word[TW];
 #pragma unroll
         for (int t = 0; t < TW; t++) word[t] = 0u;
@@ -432,7 +439,7 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
         uint32_t any = 0;
 #pragma unroll
         for (int t = 0; t < TW; t++) any |= word[t];
-        if (__any_sync(FM, any != 0u)) resolve(g, word);
+        if (__any_sync(FM, any != 0u)) resolve(g, word, jmeta, js0);
     }
     drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, wb0, wsym0, shot_base, K, k1, lane, Bw);
 }
