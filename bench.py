@@ -205,8 +205,8 @@ def run_profile_case():
     prog.sample(shots, seed=1, out=out)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": WORKLOAD["name"], "shots": shots, "path": i["path"],
-                      "fused_tile_shots": i["fused_tile_shots"], "fused_windows": i["fused_windows"],
-                      "fused_blocks_per_iter": i["fused_blocks_per_iter"],
+                      "fused_tile_shots": i["fused_tile_shots"], "fused_ctas_per_sm": i["fused_ctas_per_sm"],
+                      "fused_variant": i["fused_variant"],
                       "autotune_fused_launches": i["autotune_launches"]}))
 
 
@@ -326,7 +326,7 @@ def run_ours(args):
                    "observables": info["num_observables"], "nnz_delta": info["nnz_delta"],
                    "path": {1: "staged-sparse", 2: "dense", 3: "fused"}.get(info["path"], "?"),
                    "fused_tile_shots": info["fused_tile_shots"],
-                   "fused_blocks_per_iter": info["fused_blocks_per_iter"],
+                   "fused_variant": info["fused_variant"],
                    "chunk_shots": info["chunk_shots"],
                    "parallelism": f"shot-sharded x{world}" if world > 1 else "single GPU",
                    "l2": "outputs larger than L2: records %.2f GB per step (fault bits %.2f GB, in shared "

@@ -116,8 +116,8 @@ typedef struct {
     double density;                /* nnz_rows / (rows * n_s) */
     int32_t path;                  /* SP_PATH_SPARSE, SP_PATH_DENSE or SP_PATH_FUSED */
     int32_t fused_tile_shots;      /* shots per fused tile (32 or 64; 0 = fused path unavailable) */
-    int32_t fused_blocks_per_iter; /* channel blocks drawn per iteration of the fused kernel */
-    int32_t fused_windows;         /* symbol windows per tile of the fused kernel */
+    int32_t fused_variant;         /* 1, or 2 = the 64-shot kernel built for one CTA per SM */
+    int32_t fused_ctas_per_sm;     /* resident CTAs per SM of the chosen fused kernel */
     int32_t autotune_launches;     /* fused-kernel launches the build-time autotuner made */
     int32_t reserved;
     uint64_t chunk_shots;          /* shots per internal sampling chunk */
@@ -250,13 +250,13 @@ SP_API sp_status sp_set_path(sp_program *prog, int32_t path);
 
 /*
  * sp_set_fused_config -- choose the fused kernel variant by hand instead of
- * the build-time autotuner's choice: tile_shots 32 or 64, blocks_per_iter 1
- * or 2, windows = number of symbol windows a tile is drawn and consumed in
- * (0 = the fewest that fit in shared memory, allowing two CTAs per SM for
- * 32-shot tiles when possible).  INVALID_ARG if that tile does not fit.
- * Records are identical for every variant.
+ * the build-time autotuner's choice: tile_shots 32 or 64 (shots per CTA
+ * tile); variant 1 (two CTAs per SM) or 2 (64-shot tiles only: the kernel
+ * compiled for one CTA per SM with more registers; for 32-shot tiles it is
+ * the same kernel as 1).  INVALID_ARG if the tile's records do not fit in
+ * shared memory.  Records are identical for every variant.
  */
-SP_API sp_status sp_set_fused_config(sp_program *prog, int32_t tile_shots, int32_t blocks_per_iter, int32_t windows);
+SP_API sp_status sp_set_fused_config(sp_program *prog, int32_t tile_shots, int32_t variant);
 
 /* sp_set_chunk -- shots per internal chunk (multiple of 1024, 0 = default). */
 SP_API sp_status sp_set_chunk(sp_program *prog, uint64_t chunk_shots);

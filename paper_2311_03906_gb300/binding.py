@@ -54,8 +54,8 @@ class sp_info_t(C.Structure):
                 ("num_symbols", C.c_uint64), ("num_channels", C.c_uint64),
                 ("num_random", C.c_uint64), ("nnz_rows", C.c_uint64), ("nnz_delta", C.c_uint64),
                 ("log_words", C.c_uint64), ("density", C.c_double), ("path", C.c_int32),
-                ("fused_tile_shots", C.c_int32), ("fused_blocks_per_iter", C.c_int32),
-                ("fused_windows", C.c_int32), ("autotune_launches", C.c_int32), ("reserved", C.c_int32),
+                ("fused_tile_shots", C.c_int32), ("fused_variant", C.c_int32),
+                ("fused_ctas_per_sm", C.c_int32), ("autotune_launches", C.c_int32), ("reserved", C.c_int32),
                 ("chunk_shots", C.c_uint64), ("build_ms", C.c_double)]
 
 
@@ -88,7 +88,7 @@ def load() -> C.CDLL:
     lib.sp_export_channels.argtypes = [vp, vp, vp, vp]
     lib.sp_set_path.argtypes = [vp, i32]
     lib.sp_set_chunk.argtypes = [vp, u64]
-    lib.sp_set_fused_config.argtypes = [vp, i32, i32, i32]
+    lib.sp_set_fused_config.argtypes = [vp, i32, i32]
     lib.sp_profile_enable.argtypes = [vp, i32]
     lib.sp_profile_read.argtypes = [vp, vp, vp]
     lib.sp_free.argtypes = [vp]
@@ -222,8 +222,8 @@ class Program:
         _check(self._lib.sp_set_path(self._h, path))
         self.refresh_info()
 
-    def set_fused_config(self, tile_shots: int, blocks_per_iter: int, windows: int = 0):
-        _check(self._lib.sp_set_fused_config(self._h, tile_shots, blocks_per_iter, windows))
+    def set_fused_config(self, tile_shots: int, variant: int = 1):
+        _check(self._lib.sp_set_fused_config(self._h, tile_shots, variant))
         self.refresh_info()
 
     def set_chunk(self, chunk_shots: int):

@@ -33,9 +33,9 @@ static void release(sp_program *P)
     void *bufs[] = {P->d_A, P->d_chT, P->d_chKind, P->d_chP, P->d_chSym0, P->d_rowOff, P->d_idx,
                     P->d_parent, P->d_cflag, P->d_A64, P->d_const, P->d_inc, P->d_incT, P->d_kappa,
                     P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta,
-                    P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs};
+                    P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs,
+                    P->d_colOff, P->d_colRows};
     for (void *b : bufs) if (b) cudaFree(b);
-    for (auto &L : P->layouts) L.release();
     if (P->h_stage) cudaFreeHost(P->h_stage);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     for (auto &pe : P->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -125,8 +125,8 @@ sp_status sp_info(const sp_program *P, sp_info_t *o)
     o->density = P->density;
     o->path = P->path;
     o->fused_tile_shots = 32 * P->fused_tw;
-    o->fused_blocks_per_iter = P->fused_unroll;
-    o->fused_windows = P->fused_tw ? P->layouts[P->fused_layout].nw : 0;
+    o->fused_variant = P->fused_tw ? P->fused_unroll : 0;
+    o->fused_ctas_per_sm = P->fused_tw ? P->fused_ctas_per_sm : 0;
     o->autotune_launches = P->autotune_launches;
     o->chunk_shots = (uint64_t)P->chunk_shots;
     o->build_ms = P->build_ms;
@@ -293,15 +293,11 @@ sp_status sp_set_path(sp_program *P, int32_t path)
     return SP_OK;
 }
 
-sp_status sp_set_fused_config(sp_program *P, int32_t tile_shots, int32_t blocks_per_iter, int32_t windows)
+sp_status sp_set_fused_config(sp_program *P, int32_t tile_shots, int32_t variant)
 {
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
     if (tile_shots != 32 && tile_shots != 64) return set_error(SP_ERR_INVALID_ARG, "tile_shots must be 32 or 64");
-    const int tw = tile_shots / 32;
-    int nw = windows;
-    if (nw == 0) nw = tw == 1 ? (P->nw_half ? P->nw_half : P->nw_full1) : P->nw_full2;
-    if (nw <= 0) return set_error(SP_ERR_INVALID_ARG, "no window count makes that tile fit in shared memory");
-    return fused_select(P, tw, nw, blocks_per_iter);
+    return fused_select(P, tile_shots / 32, variant);
 }
 
 sp_status sp_set_chunk(sp_program *P, uint64_t chunk_shots)

@@ -271,35 +271,48 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
 
 // Fired-event queue of one warp: FUSED_QCAP 32-bit words in shared memory.
 // An event is one (channel block, shot) in which at least one of the block's
-// depolarizing channels fired: bits 16..31 block - first block of the
-// window, bit 9 tile word t, bits 4..8 lane, bits 0..3 the fired channels.
+// depolarizing channels fired: bits 10..31 block - the warp's first block,
+// bit 9 tile word t, bits 4..8 lane, bits 0..3 the fired channels.
 constexpr uint32_t FUSED_QCAP = 128;
+constexpr uint32_t EVENT_MAX_BLOCKS = 1u << 22;
 // Channel blocks whose compare results are gathered before one vote.
 constexpr uint32_t DRAW_GROUP = 8;
 static_assert(4 * DRAW_GROUP == 32, "a group's channels map one to one onto the lanes");
 
+// XOR the word x into tile word t of every measurement row whose own part
+// holds symbol s (Eq. sampling restricted to the symbol's column; shared
+// atomics, since several symbols of one row may be applied at once).
+template <int TW>
+__device__ __forceinline__ void xor_column(const uint32_t *__restrict__ colOff, const uint32_t *__restrict__ colRows,
+                                           uint32_t s, int t, uint32_t x, uint32_t *Rw)
+{
+    const uint32_t e = colOff[s + 1];
+    for (uint32_t k = colOff[s]; k < e; k++) atomicXor(&Rw[colRows[k] * TW + t], x);
+}
+
 // Apply the queued events e = lane, lane+32, ... < n: recompute the event's
-// Philox block, turn each fired channel into its symbol bits and set the
-// shot's bit in those symbols' words of the tile Bw (shared atomics: two
-// shots of one channel may meet in a word, rarely at circuit-level noise).
+// Philox block, turn each fired channel into its symbol bits and flip the
+// shot's bit in the rows of those symbols.
 template <int TW>
 __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const uint4 *__restrict__ blkT,
                                             const uint32_t *__restrict__ blkMeta, const uint32_t *__restrict__ blkSym0,
-                                            uint32_t wb0, uint32_t wsym0, uint64_t shot_base, const Keys &K,
-                                            uint32_t k1, int lane, uint32_t *Bw)
+                                            const uint32_t *__restrict__ colOff, const uint32_t *__restrict__ colRows,
+                                            uint32_t b0, uint64_t shot_base, const Keys &K, uint32_t k1, int lane,
+                                            uint32_t *Rw)
 {
     __syncwarp();
     for (uint32_t e = lane; e < n; e += 32) {
         const uint32_t ev = q[e];
-        const uint32_t b = wb0 + (ev >> 16);
-        const uint32_t t = (ev >> 9) & 1u, ln = (ev >> 4) & 31u;
+        const uint32_t b = b0 + (ev >> 10);
+        const int t = (ev >> 9) & 1u;
+        const uint32_t ln = (ev >> 4) & 31u;
         uint32_t fmask = ev & 15u;
-        const ShotConst s = shot_const(shot_base + 32u * t + ln, k1);
+        const ShotConst s = shot_const(shot_base + 32u * (uint32_t)t + ln, k1);
         const uint64_t ub = (uint64_t)PH_M1 * b;
         uint32_t r0, r1, r2, r3;
         philox_block(s, s.c1, (uint32_t)(ub >> 32), (uint32_t)ub, K, r0, r1, r2, r3);
         const uint4 T = blkT[b];
-        const uint32_t meta = blkMeta[b], s0 = blkSym0[b] - wsym0;
+        const uint32_t meta = blkMeta[b], s0 = blkSym0[b];
         while (fmask) {
             const int i = __ffs(fmask) - 1;
             fmask &= fmask - 1;
@@ -311,7 +324,7 @@ __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const
             while (val) {
                 const int j = __ffs(val) - 1;
                 val &= val - 1;
-                atomicOr(&Bw[(off + j) * TW + t], 1u << ln);
+                xor_column<TW>(colOff, colRows, off + (uint32_t)j, t, 1u << ln, Rw);
             }
         }
     }
@@ -325,42 +338,34 @@ __device__ __forceinline__ uint32_t fired4(uint32_t r0, uint32_t r1, uint32_t r2
            ((uint32_t)(r3 < T.w) << 3);
 }
 
-// Draw the symbols of blocks [b0, b1) of the window starting at block wb0
-// (symbol wsym0) for 32*TW shots into the bit-sliced tile Bw (TW 32-bit
-// words per symbol, index (s - wsym0)*TW + t).  The warp owns the symbols of
-// its blocks and zeroes them first.  Per group of DRAW_GROUP blocks (32
-// channels) each lane gathers the fired bits of its shots' channels into one
-// word per tile word, and the warp votes once; faults are rare at
-// circuit-level noise, so most of the time goes to Philox.  A group that
-// fired is resolved lane-parallel (lane j = channel j of the group), with
-// the depolarizing channels' events queued in q and drained by all 32 lanes
-// when it fills and at the end.  UHI: every shot of the tile has the same
-// high counter word c1u, so round 2's M0 product is the same in all lanes
-// and tile words.
-template <int TW, int U, bool UHI>
+// Phase 1 with the product folded in, for blocks [b0, b1) and 32*TW shots:
+// every fired symbol XORs its bit-sliced word (bit = shot in the tile) into
+// the rows Rw (TW 32-bit words per row) whose own part holds it.  Per group
+// of DRAW_GROUP blocks (32 channels) each lane gathers the fired bits of its
+// shots' channels into one word per tile word, and the warp votes once;
+// faults are rare at circuit-level noise, so most of the time goes to
+// Philox.  A group that fired is resolved lane-parallel: lane j stands for
+// channel j&3 of block g + j/4 (descriptor jmeta, first symbol js0, loaded
+// at the group's start), a 32x32 transpose per tile word gives it the shots
+// in which its channel fired, and a one-symbol channel (a Pauli error or a
+// random outcome) applies that word to its symbol's rows.  Depolarizing
+// channels need the category index: one event per (block, shot) goes to the
+// warp's queue q, drained by all 32 lanes when it fills and at the end.
+// UHI: every shot of the tile has the same high counter word c1u, so round
+// 2's M0 product is the same in all lanes and tile words.
+template <int TW, bool UHI>
 __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
-                                                const uint32_t *__restrict__ blkSym0, uint32_t wb0, uint32_t b0,
-                                                uint32_t b1, uint32_t wsym0, const Shots<TW> sc, uint64_t shot_base,
-                                                uint32_t k0, uint32_t k1, int lane, uint32_t *Bw, uint32_t *q)
+                                                const uint32_t *__restrict__ blkSym0,
+                                                const uint32_t *__restrict__ colOff,
+                                                const uint32_t *__restrict__ colRows, uint32_t b0, uint32_t b1,
+                                                const Shots<TW> sc, uint64_t shot_base, uint32_t k0, uint32_t k1,
+                                                int lane, uint32_t *Rw, uint32_t *q)
 {
-    static_assert(U == 1 || U == 2, "one or two blocks per step");
     static_assert(TW == 1 || TW == 2, "one or two tile words");
-    {
-        const uint32_t lo = (blkSym0[b0] - wsym0) * TW, hi = (blkSym0[b1] - wsym0) * TW;
-        for (uint32_t i = lo + lane; i < hi; i += 32) Bw[i] = 0u;
-    }
-    __syncwarp();   // lane 0 may store into words that other lanes zeroed
     const Keys K = make_keys(k0, k1);
     const uint32_t c1u = (uint32_t)(shot_base >> 32);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t cnt = 0;
-    // A group that fired in some lane.  Lane j stands for channel j&3 of
-    // block g + j/4 (its descriptor jmeta, first symbol js0).  One 32x32
-    // transpose per tile word gives lane j the shots in which its channel
-    // fired; a one-symbol channel (a Pauli error or a random outcome) stores
-    // that word as its symbol's word.  Depolarizing channels need the
-    // category index: the lanes whose shots fired one are queued, one event
-    // per (block, shot), with room for 32 events ensured before each append.
     auto resolve = [&](uint32_t g, const uint32_t (&word)[TW], uint32_t jmeta, uint32_t js0) {
         uint32_t any = 0;
 #pragma unroll
@@ -372,11 +377,11 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
         const bool is_dep = kind == CK_DEP1 || kind == CK_DEP2;
         const uint32_t dep = __ballot_sync(FM, mine && is_dep);
         if (wm & ~dep) {
-            const uint32_t off = js0 - wsym0 + ((jmeta >> (8 + 4 * i)) & 15u);
+            const uint32_t sym = js0 + ((jmeta >> (8 + 4 * i)) & 15u);
 #pragma unroll
             for (int t = 0; t < TW; t++) {
                 const uint32_t col = transpose32(word[t], lane);
-                if (mine && !is_dep) Bw[off * TW + t] = col;
+                if (mine && !is_dep && col) xor_column<TW>(colOff, colRows, sym, t, col, Rw);
             }
         }
         if (!dep) return;
@@ -385,7 +390,7 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
             uint32_t m = word[t] & dep;
             while (__any_sync(FM, m != 0u)) {
                 if (cnt > FUSED_QCAP - 32u) {
-                    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, wb0, wsym0, shot_base, K, k1, lane, Bw);
+                    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, colOff, colRows, b0, shot_base, K, k1, lane, Rw);
                     cnt = 0;
                 }
                 const int k = m ? (__ffs(m) - 1) >> 2 : 0;
@@ -393,7 +398,7 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
                 const uint32_t bal = __ballot_sync(FM, nib != 0u);
                 if (nib)
                     q[cnt + __popc(bal & lt)] =
-                        ((g + (uint32_t)k - wb0) << 16) | ((uint32_t)t << 9) | ((uint32_t)lane << 4) | nib;
+                        ((g + (uint32_t)k - b0) << 10) | ((uint32_t)t << 9) | ((uint32_t)lane << 4) | nib;
                 cnt += __popc(bal);
                 m &= ~(15u << (4 * k));
             }
@@ -441,42 +446,39 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
         for (int t = 0; t < TW; t++) any |= word[t];
         if (__any_sync(FM, any != 0u)) resolve(g, word, jmeta, js0);
     }
-    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, wb0, wsym0, shot_base, K, k1, lane, Bw);
+    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, colOff, colRows, b0, shot_base, K, k1, lane, Rw);
 }
 
-template <int TW, int U>
+template <int TW>
 __device__ __forceinline__ void draw_scatter(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
-                                             const uint32_t *__restrict__ blkSym0, uint32_t wb0, uint32_t b0,
-                                             uint32_t b1, uint32_t wsym0, const Shots<TW> sc, uint64_t shot_base,
-                                             uint32_t k0, uint32_t k1, int lane, uint32_t *Bw, uint32_t *q)
+                                             const uint32_t *__restrict__ blkSym0, const uint32_t *__restrict__ colOff,
+                                             const uint32_t *__restrict__ colRows, uint32_t b0, uint32_t b1,
+                                             const Shots<TW> sc, uint64_t shot_base, uint32_t k0, uint32_t k1,
+                                             int lane, uint32_t *Rw, uint32_t *q)
 {
     // a tile straddles a multiple of 2^32 shots only if shot0 is unaligned
     if ((shot_base >> 32) == ((shot_base + 32u * TW - 1u) >> 32))
-        draw_group_impl<TW, U, true>(blkT, blkMeta, blkSym0, wb0, b0, b1, wsym0, sc, shot_base, k0, k1, lane, Bw, q);
+        draw_group_impl<TW, true>(blkT, blkMeta, blkSym0, colOff, colRows, b0, b1, sc, shot_base, k0, k1, lane, Rw, q);
     else
-        draw_group_impl<TW, U, false>(blkT, blkMeta, blkSym0, wb0, b0, b1, wsym0, sc, shot_base, k0, k1, lane, Bw, q);
+        draw_group_impl<TW, false>(blkT, blkMeta, blkSym0, colOff, colRows, b0, b1, sc, shot_base, k0, k1, lane, Rw, q);
 }
 
 struct FusedParams {
     const uint4 *blkT;
     const uint32_t *blkMeta;
     const uint32_t *blkSym0;
-    int64_t n_sym, n_rows, n_meas, n_det, n_obs;
-    int nw;                    // symbol windows drawn and consumed one after another
-    const uint32_t *winBlk;    // [nw + 1] first channel block of each window
-    const uint4 *aItem;        // step A: {index-group offset, group count, row, 0}
-    const uint32_t *aOff;      // [nw][threads + 1] items of (window, thread)
+    const uint32_t *colOff;    // [n_sym + 1]: rows of symbol s are colRows[colOff[s] .. colOff[s+1])
+    const uint32_t *colRows;   // measurement rows whose own part holds the symbol
+    int64_t n_blk, n_rows, n_meas, n_det, n_obs;
     const uint8_t *cflag;      // [n_meas] constant bit of each measurement row's own part
     const uint2 *bItem;        // step B: (row, parent), parents first within a thread
     const uint32_t *bOff;      // [threads + 1]
     const uint32_t *cOff;      // step C: detector/observable t = XOR of measurement rows
     const uint32_t *cRefs;
-    const uint4 *idx4;         // groups of 8 x 16-bit window-relative symbol indices
     uint64_t seed, shot0, nshots;
     uint64_t *out[3];
     int64_t rows0[3], nrow[3];
-    uint32_t rec_off_words;    // offset of R_s in shared memory (u32 words)
-    uint32_t q_off_words;      // offset of the warps' fired-event queues (u32 words)
+    uint32_t aux_off_words;    // the warps' event queues (phase 1), the emit stage (phase 3)
 };
 
 template <int TW> struct TileWord;
@@ -485,36 +487,25 @@ template <> struct TileWord<1> {
     __device__ static T zero() { return 0u; }
     __device__ static T ones() { return FM; }
     __device__ static uint32_t get(T v, int) { return v; }
-    __device__ static T make(const Cols<1> c) { return c.v[0]; }
 };
 template <> struct TileWord<2> {
     typedef uint2 T;
     __device__ static T zero() { return make_uint2(0u, 0u); }
     __device__ static T ones() { return make_uint2(FM, FM); }
     __device__ static uint32_t get(T v, int t) { return t ? v.y : v.x; }
-    __device__ static T make(const Cols<2> c) { return make_uint2(c.v[0], c.v[1]); }
 };
 __device__ __forceinline__ uint32_t xorw(uint32_t a, uint32_t b) { return a ^ b; }
 __device__ __forceinline__ uint2 xorw(uint2 a, uint2 b) { return make_uint2(a.x ^ b.x, a.y ^ b.y); }
 
-template <typename W>
-__device__ __forceinline__ W gather8(const W *Bs, uint4 s)
-{
-    const W a = xorw(xorw(Bs[s.x & 0xffffu], Bs[s.x >> 16]), xorw(Bs[s.y & 0xffffu], Bs[s.y >> 16]));
-    const W b = xorw(xorw(Bs[s.z & 0xffffu], Bs[s.z >> 16]), xorw(Bs[s.w & 0xffffu], Bs[s.w >> 16]));
-    return xorw(a, b);
-}
-
 // One tile of 32*TW shots of one program, by the whole CTA.  Ends with a
 // barrier, so the caller may start another tile right away.
-template <int TW, int U>
+template <int TW>
 __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, uint32_t *sm)
 {
     typedef TileWord<TW> TWd;
     typedef typename TWd::T W;
-    W *Bs = reinterpret_cast<W *>(sm);                       // one window of symbols + a zero slot
-    W *Rs = reinterpret_cast<W *>(sm + p.rec_off_words);     // n_rows
-    uint32_t *stage = sm;                                    // aliases Bs in phase 3
+    W *Rs = reinterpret_cast<W *>(sm);                       // [n_rows] records, bit-sliced
+    uint32_t *aux = sm + p.aux_off_words;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const uint64_t trel = tile * (32u * TW);
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
@@ -523,36 +514,15 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
     for (int t = 0; t < TW; t++) sc.s[t] = shot_const(p.shot0 + trel + 32u * t + lane, k1);
     // own parts start from their constants
     for (int64_t j = tid; j < p.n_meas; j += blockDim.x) Rs[j] = p.cflag[j] ? TWd::ones() : TWd::zero();
-    for (int w = 0; w < p.nw; w++) {
-        // ---- phase 1: draw the symbols of window w ------------------------
-        const uint32_t wb0 = p.winBlk[w], wb1 = p.winBlk[w + 1];
-        const uint32_t wsym0 = p.blkSym0[wb0], wsize = p.blkSym0[wb1] - wsym0;
-        const uint32_t nbw = wb1 - wb0;
-        const uint32_t b0 = wb0 + (uint32_t)((uint64_t)warp * nbw / nwarps);
-        const uint32_t b1 = wb0 + (uint32_t)((uint64_t)(warp + 1) * nbw / nwarps);
-        if (tid == 0) Bs[wsize] = TWd::zero();
-        draw_scatter<TW, U>(p.blkT, p.blkMeta, p.blkSym0, wb0, b0, b1, wsym0, sc, p.shot0 + trel, k0, k1, lane,
-                            reinterpret_cast<uint32_t *>(Bs), sm + p.q_off_words + warp * FUSED_QCAP);
-        __syncthreads();
-        // ---- phase 2A: own parts over this window's symbols -------------------
-        {
-            const uint32_t *ao = p.aOff + (size_t)w * (blockDim.x + 1);
-            const uint32_t e = ao[tid + 1];
-            for (uint32_t i = ao[tid]; i < e; i++) {
-                const uint4 m = p.aItem[i];
-                const uint4 *q = p.idx4 + m.x;
-                W acc = TWd::zero();
-                uint32_t k = 0;
-                for (; k + 2 <= m.y; k += 2) {
-                    const uint4 s0 = q[k], s1 = q[k + 1];
-                    acc = xorw(acc, xorw(gather8(Bs, s0), gather8(Bs, s1)));
-                }
-                if (k < m.y) acc = xorw(acc, gather8(Bs, q[k]));
-                Rs[m.z] = xorw(Rs[m.z], acc);
-            }
-        }
-        __syncthreads();
+    __syncthreads();
+    // ---- phase 1 + 2A: draw; fired symbols flip the own parts holding them --
+    {
+        const uint32_t b0 = (uint32_t)((uint64_t)warp * (uint64_t)p.n_blk / (uint64_t)nwarps);
+        const uint32_t b1 = (uint32_t)((uint64_t)(warp + 1) * (uint64_t)p.n_blk / (uint64_t)nwarps);
+        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, p.colOff, p.colRows, b0, b1, sc, p.shot0 + trel, k0, k1, lane,
+                         sm, aux + warp * FUSED_QCAP);
     }
+    __syncthreads();
     // ---- phase 2B: parent chains, m_j = own part ^ m_parent ---------------
     {
         const uint32_t e = p.bOff[tid + 1];
@@ -569,7 +539,8 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
         Rs[p.n_meas + t] = acc;
     }
     __syncthreads();
-    // ---- phase 3: emit shot-major records -----------------------------------
+    // ---- phase 3: emit shot-major records (stage aliases the queues) -------
+    uint32_t *stage = aux;
 #pragma unroll
     for (int sg = 0; sg < 3; sg++) {
         uint64_t *dst = p.out[sg];
@@ -600,15 +571,15 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
     __syncthreads();
 }
 
-// Two CTAs per SM (64 registers) except the 64-shot, two-block variant,
-// which needs more registers than that without spilling.
+// Two CTAs per SM (64 registers); U = 2 marks the 64-shot variant compiled
+// for one CTA per SM with more registers.
 template <int TW, int U>
 __global__ void __launch_bounds__(FUSED_THREADS, (TW == 2 && U == 2) ? 1 : 2) k_fused(FusedParams p)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const uint64_t per_tile = 32u * TW;
     const uint64_t ntiles = (p.nshots + per_tile - 1) / per_tile;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) fused_tile<TW, U>(p, tile, sm);
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) fused_tile<TW>(p, tile, sm);
 }
 
 // Batched form: many programs in one persistent launch.  Work items are
@@ -635,7 +606,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, MINB) k_fused_batch(const Fused
             const int mid = (lo + hi) >> 1;
             if (tileEnd[mid] > item) hi = mid; else lo = mid + 1;
         }
-        fused_tile<1, 2>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
+        fused_tile<1>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
     }
 }
 
@@ -700,6 +671,9 @@ double lpt_assign(const std::vector<int64_t> &items, const std::vector<double> &
 }
 }  // namespace
 
+static uint32_t aux_offset(const sp_program *P, int tw);
+size_t fused_words(const sp_program *P, int tw);
+
 sp_status build_fused_program(sp_program *P, cudaStream_t s)
 {
     // ---- channel-block draw descriptors ---------------------------------
@@ -740,7 +714,7 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     if ((st = upload(&P->d_blkT, bT, s)) || (st = upload(&P->d_blkMeta, bMeta, s)) || (st = upload(&P->d_blkSym0, bSym0, s)))
         return st;
 
-    // ---- product program: host copies of the measurement rows' own parts --
+    // ---- product program: the measurement rows' own parts by symbol -------
     const int64_t R = P->n_rows;
     const int64_t M = P->n_meas;
     std::vector<int32_t> parent((size_t)R);
@@ -752,13 +726,24 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
         SP_CUDA(cudaMemcpyAsync(off.data(), P->d_rowOff, ((size_t)R + 1) * 4, cudaMemcpyDeviceToHost, s));
         SP_CUDA(cudaStreamSynchronize(s));
     }
-    P->h_own_off.assign(off.begin(), off.begin() + (M + 1));
-    P->h_own_idx.assign((size_t)P->h_own_off[M], 0u);
-    if (!P->h_own_idx.empty())
-        SP_CUDA(cudaMemcpy(P->h_own_idx.data(), P->d_idx, P->h_own_idx.size() * 4, cudaMemcpyDeviceToHost));
-    P->h_blkSym0 = bSym0;
+    std::vector<uint32_t> own_idx(R ? (size_t)off[M] : 0u);
+    if (!own_idx.empty())
+        SP_CUDA(cudaMemcpy(own_idx.data(), P->d_idx, own_idx.size() * 4, cudaMemcpyDeviceToHost));
     for (int64_t j = 0; j < M; j++)
         if (parent[j] >= M) return set_error(SP_ERR_CUDA, "measurement row with a non-measurement parent");
+    // transpose row -> symbols (the own parts) into symbol -> rows
+    std::vector<uint32_t> colOff((size_t)P->n_sym + 1, 0), colRows(own_idx.size());
+    for (uint32_t v : own_idx) {
+        if ((int64_t)v >= P->n_sym) return set_error(SP_ERR_CUDA, "own-part symbol out of range");
+        colOff[v + 1]++;
+    }
+    for (int64_t v = 0; v < P->n_sym; v++) colOff[v + 1] += colOff[v];
+    {
+        std::vector<uint32_t> pos(colOff.begin(), colOff.end() - 1);
+        for (int64_t j = 0; j < M; j++)
+            for (uint32_t k = off[j]; k < off[j + 1]; k++) colRows[pos[own_idx[k]]++] = (uint32_t)j;
+    }
+    if ((st = upload(&P->d_colOff, colOff, s)) || (st = upload(&P->d_colRows, colRows, s))) return st;
     // step 0: constants of the own parts
     std::vector<uint8_t> cf(cflag.begin(), cflag.begin() + M);
     // step B: parent chains, whole trees per thread, parents first
@@ -787,7 +772,7 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
         (st = upload(&P->d_fCOff, P->h_xoff, s)) || (st = upload(&P->d_fCRefs, P->h_xrefs, s)))
         return st;
 
-    // ---- window counts that fit each tile width / occupancy ---------------
+    // ---- default variant: the records of a tile must fit in shared memory --
     int dev = 0, smem_max = 0, nsm = 0;
     SP_CUDA(cudaGetDevice(&dev));
     SP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -795,127 +780,28 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     P->num_sms = nsm;
     P->smem_max = smem_max;
     P->fused_tw = 0;
-    P->nw_half = min_windows(P, 1, (size_t)smem_max / 2 - 1024);
-    P->nw_full1 = min_windows(P, 1, (size_t)smem_max);
-    P->nw_full2 = min_windows(P, 2, (size_t)smem_max);
-    P->nw_half2 = min_windows(P, 2, (size_t)smem_max / 2 - 1024);
-    if (R > 0 && nb > 0) {
-        if (P->nw_half > 0) st = fused_select(P, 1, P->nw_half, 2);
-        else if (P->nw_full1 > 0) st = fused_select(P, 1, P->nw_full1, 2);
+    // queued events address blocks relative to a warp's first block
+    const bool events_ok = (uint64_t)nb / (FUSED_THREADS / 32) + 1 < EVENT_MAX_BLOCKS;
+    if (R > 0 && nb > 0 && events_ok) {
+        if (fused_words(P, 2) * 4 <= (size_t)smem_max) st = fused_select(P, 2, 1);
+        else if (fused_words(P, 1) * 4 <= (size_t)smem_max) st = fused_select(P, 1, 1);
         if (st != SP_OK) return st;
     }
     return SP_OK;
 }
 
-// Window boundaries (in channel blocks) for about nw windows of equal size.
-static std::vector<uint32_t> split_windows(const sp_program *P, int nw)
-{
-    const std::vector<uint32_t> &sym0 = P->h_blkSym0;
-    const uint32_t nb = (uint32_t)P->n_blk;
-    const uint64_t target = ((uint64_t)P->n_sym + nw - 1) / (uint64_t)nw;
-    std::vector<uint32_t> wb{0};
-    for (uint32_t b = 0; b < nb; b++) {
-        const uint64_t cur = sym0[b] - sym0[wb.back()];
-        const uint64_t add = sym0[b + 1] - sym0[b];
-        if (cur > 0 && cur + add > target) wb.push_back(b);
-    }
-    wb.push_back(nb);
-    return wb;
-}
+// Shared-memory words of a tile of 32*tw shots: the records R_s (n_rows x tw
+// words), then a region used by the warps' event queues in phase 1 and by
+// the emit stage in phase 3.
+static uint32_t aux_offset(const sp_program *P, int tw) { return (uint32_t)((P->n_rows * tw + 3) / 4 * 4); }
 
-static uint32_t max_window(const sp_program *P, const std::vector<uint32_t> &wb)
-{
-    uint32_t mx = 0;
-    for (size_t w = 0; w + 1 < wb.size(); w++) mx = std::max(mx, P->h_blkSym0[wb[w + 1]] - P->h_blkSym0[wb[w]]);
-    return mx;
-}
-
-static size_t fused_words(const sp_program *P, int tw, uint32_t maxw, uint32_t *rec_off)
+size_t fused_words(const sp_program *P, int tw)
 {
     int64_t max_words32 = 0;
     for (int64_t n : {P->n_meas, P->n_det, P->n_obs}) max_words32 = std::max<int64_t>(max_words32, 2 * ((n + 63) / 64));
-    const int64_t bwords = (((int64_t)maxw + 1) * tw + 3) / 4 * 4;
     const int64_t stage_words = 32 * tw * (max_words32 + 1);
-    if (rec_off) *rec_off = (uint32_t)std::max(bwords, stage_words);
-    return (size_t)(std::max(bwords, stage_words) + P->n_rows * tw) + (FUSED_THREADS / 32) * FUSED_QCAP;
-}
-
-int min_windows(const sp_program *P, int tw, size_t budget_bytes)
-{
-    if (P->n_rows == 0 || P->n_blk == 0) return 0;
-    for (int nw = 1; nw <= 1024; nw = nw < 8 ? nw + 1 : nw * 2) {
-        const std::vector<uint32_t> wb = split_windows(P, nw);
-        const uint32_t mx = max_window(P, wb);
-        if (mx >= 65535u) continue;   // window-relative indices are 16-bit
-        if (fused_words(P, tw, mx, nullptr) * 4 <= budget_bytes) return nw;
-        if (mx <= 16) break;          // windows cannot get smaller than a block
-    }
-    return 0;
-}
-
-// The (window, thread) item lists of one window count, built on demand.
-static sp_status get_layout(sp_program *P, int nw, FusedLayout **out)
-{
-    for (FusedLayout &L : P->layouts)
-        if (L.nw_req == nw) { *out = &L; return SP_OK; }
-    const std::vector<uint32_t> wb = split_windows(P, nw);
-    const int W = (int)wb.size() - 1;
-    const int NT = FUSED_THREADS;
-    const int64_t M = P->n_meas;
-    std::vector<uint32_t> wsym((size_t)W + 1);
-    for (int w = 0; w <= W; w++) wsym[w] = P->h_blkSym0[wb[w]];
-    std::vector<uint4> idx4, aItem;
-    std::vector<uint32_t> aOff((size_t)W * (NT + 1), 0);
-    std::vector<uint32_t> cursor(P->h_own_off.begin(), P->h_own_off.end() - 1);
-    for (int w = 0; w < W; w++) {
-        const uint32_t lo = wsym[w], hi = wsym[w + 1], zero = hi - lo;
-        std::vector<int64_t> items;          // rows with symbols in this window
-        std::vector<uint32_t> g0((size_t)M), ng((size_t)M, 0);
-        std::vector<double> cost((size_t)M, 0.0);
-        for (int64_t j = 0; j < M; j++) {
-            uint32_t a = cursor[j];
-            const uint32_t e = P->h_own_off[j + 1];
-            uint32_t b = a;
-            while (b < e && P->h_own_idx[b] < hi) b++;
-            cursor[j] = b;
-            if (b == a) continue;
-            g0[j] = (uint32_t)idx4.size();
-            for (uint32_t k = a; k < b; k += 8) {
-                uint32_t v[8];
-                for (uint32_t i = 0; i < 8; i++) v[i] = k + i < b ? P->h_own_idx[k + i] - lo : zero;
-                idx4.push_back(make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16)));
-            }
-            ng[j] = (uint32_t)(idx4.size() - g0[j]);
-            cost[j] = 1.0 + ng[j];
-            items.push_back(j);
-        }
-        std::stable_sort(items.begin(), items.end(), [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
-        std::vector<int32_t> owner((size_t)M, 0);
-        lpt_assign(items, cost, NT, owner);
-        uint32_t *ao = aOff.data() + (size_t)w * (NT + 1);
-        std::vector<uint32_t> cnt((size_t)NT, 0);
-        for (int64_t j : items) cnt[owner[j]]++;
-        ao[0] = (uint32_t)aItem.size();
-        for (int t = 0; t < NT; t++) ao[t + 1] = ao[t] + cnt[t];
-        std::vector<uint32_t> pos(ao, ao + NT);
-        aItem.resize(aItem.size() + items.size());
-        for (int64_t j : items) aItem[pos[owner[j]]++] = make_uint4(g0[j], ng[j], (uint32_t)j, 0u);
-    }
-    FusedLayout L;
-    L.nw_req = nw;
-    L.nw = W;
-    L.maxw = max_window(P, wb);
-    L.groups = (int64_t)idx4.size();
-    sp_status st;
-    if ((st = upload(&L.d_winBlk, wb, nullptr)) || (st = upload(&L.d_aItem, aItem, nullptr)) ||
-        (st = upload(&L.d_aOff, aOff, nullptr)) || (st = upload(&L.d_idx4, idx4, nullptr))) {
-        L.release();
-        return st;
-    }
-    SP_CUDA(cudaDeviceSynchronize());
-    P->layouts.push_back(L);
-    *out = &P->layouts.back();
-    return SP_OK;
+    const int64_t queue_words = (FUSED_THREADS / 32) * (int64_t)FUSED_QCAP;
+    return (size_t)aux_offset(P, tw) + (size_t)std::max(stage_words, queue_words);
 }
 
 typedef void (*FusedFn)(FusedParams);
@@ -926,18 +812,16 @@ static FusedFn fused_kernel(int tw, int unroll)
     return unroll == 2 ? k_fused<1, 2> : k_fused<1, 1>;
 }
 
-sp_status fused_select(sp_program *P, int tw, int nw, int unroll)
+sp_status fused_select(sp_program *P, int tw, int unroll)
 {
-    if ((tw != 1 && tw != 2) || (unroll != 1 && unroll != 2) || nw < 1)
-        return set_error(SP_ERR_INVALID_ARG, "tile words must be 1 or 2, blocks per iteration 1 or 2, windows >= 1");
+    if ((tw != 1 && tw != 2) || (unroll != 1 && unroll != 2))
+        return set_error(SP_ERR_INVALID_ARG, "tile words must be 1 or 2, variant 1 or 2");
     if (P->n_rows == 0 || P->n_blk == 0) return set_error(SP_ERR_INVALID_ARG, "nothing to sample on the fused path");
-    FusedLayout *L = nullptr;
-    sp_status st = get_layout(P, nw, &L);
-    if (st != SP_OK) return st;
-    uint32_t rec_off = 0;
-    const size_t bytes = fused_words(P, tw, L->maxw, &rec_off) * 4;
+    if ((uint64_t)P->n_blk / (FUSED_THREADS / 32) + 1 >= EVENT_MAX_BLOCKS)
+        return set_error(SP_ERR_INVALID_ARG, "too many channel blocks for the fused path");
+    const size_t bytes = fused_words(P, tw) * 4;
     if (bytes > (size_t)P->smem_max)
-        return set_error(SP_ERR_INVALID_ARG, "that fused tile does not fit in shared memory; use more windows");
+        return set_error(SP_ERR_INVALID_ARG, "the records of that fused tile do not fit in shared memory");
     FusedFn fn = fused_kernel(tw, unroll);
     // The limit is a property of the kernel, shared by every program: keep it
     // at the device maximum so that no program's choice lowers another's.
@@ -946,39 +830,34 @@ sp_status fused_select(sp_program *P, int tw, int nw, int unroll)
     SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FUSED_THREADS, bytes));
     P->fused_tw = tw;
     P->fused_unroll = unroll;
-    P->fused_layout = (int)(L - P->layouts.data());
     P->fused_smem = bytes;
-    P->fused_rec_off = rec_off;
+    P->fused_aux_off = aux_offset(P, tw);
     P->fused_ctas_per_sm = std::max(occ, 1);
     return SP_OK;
 }
 
-// Autotuner: time the fused variants that fit -- 32-shot tiles with the
-// window count that allows two CTAs per SM or one, 64-shot tiles, one or
-// two channel blocks per draw iteration -- on a few tiles per SM and keep
-// the fastest.  The choice is cached per circuit shape for the process.
+// Autotuner: time the fused variants that fit -- 64-shot tiles at two CTAs
+// per SM, 32-shot tiles, 64-shot tiles at one CTA per SM with more registers
+// -- on a few tiles per SM and keep the fastest.  The choice is cached per
+// circuit shape for the process.
 sp_status autotune(sp_program *P, cudaStream_t s)
 {
     if (!P->fused_tw) return SP_OK;
     typedef std::tuple<int, int64_t, int64_t, int64_t, int64_t, int64_t> Key;
     static std::mutex mu;
-    static std::map<Key, std::tuple<int, int, int>> cache;
+    static std::map<Key, std::pair<int, int>> cache;
     const Key key{P->device, P->n_sym, P->n_rows, P->n_blk, P->nnz_delta, P->n_meas};
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
         if (it != cache.end()) {
             P->tuned = true;
-            return fused_select(P, std::get<0>(it->second), std::get<1>(it->second), std::get<2>(it->second));
+            return fused_select(P, it->second.first, it->second.second);
         }
     }
-    std::vector<std::tuple<int, int, int>> cand;
-    for (int u : {2, 1}) {
-        if (P->nw_half) cand.emplace_back(1, P->nw_half, u);
-        if (P->nw_full1 && P->nw_full1 != P->nw_half) cand.emplace_back(1, P->nw_full1, u);
-        if (P->nw_full2) cand.emplace_back(2, P->nw_full2, u);
-        if (P->nw_half2 && P->nw_half2 != P->nw_full2) cand.emplace_back(2, P->nw_half2, u);
-    }
+    std::vector<std::pair<int, int>> cand;
+    for (auto c : {std::make_pair(2, 1), std::make_pair(1, 1), std::make_pair(2, 2)})
+        if (fused_words(P, c.first) * 4 <= (size_t)P->smem_max) cand.push_back(c);
     const uint64_t shots = (uint64_t)P->num_sms * 2u * 64u * 4u;
     const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
     uint64_t *out = nullptr;
@@ -991,7 +870,7 @@ sp_status autotune(sp_program *P, cudaStream_t s)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    std::tuple<int, int, int> pick(P->fused_tw, P->layouts[P->fused_layout].nw_req, P->fused_unroll);
+    std::pair<int, int> pick(P->fused_tw, P->fused_unroll);
     sp_status st = SP_OK;
     const bool prof = P->profiling;
     P->profiling = false;
@@ -1000,7 +879,7 @@ sp_status autotune(sp_program *P, cudaStream_t s)
     // timing noise does not flip the choice between equivalent variants
     for (size_t ci = 0; ci < cand.size(); ci++) {
         const auto &c = cand[ci];
-        if ((st = fused_select(P, std::get<0>(c), std::get<1>(c), std::get<2>(c))) != SP_OK) break;
+        if ((st = fused_select(P, c.first, c.second)) != SP_OK) break;
         if ((st = fused_chunk(P, 1, 0, shots, om, od, oo, s)) != SP_OK) break;
         P->autotune_launches += 1;
         float ms = 1e30f;
@@ -1027,7 +906,7 @@ sp_status autotune(sp_program *P, cudaStream_t s)
         cache[key] = pick;
     }
     P->tuned = true;
-    return fused_select(P, std::get<0>(pick), std::get<1>(pick), std::get<2>(pick));
+    return fused_select(P, pick.first, pick.second);
 }
 
 sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *B,
@@ -1040,21 +919,20 @@ sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0,
     return SP_OK;
 }
 
-static FusedParams fused_params(const sp_program *P, const FusedLayout &L, int tw, uint32_t rec_off, uint64_t seed,
-                                uint64_t shot0, uint64_t nshots, uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs)
+static FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                                uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs)
 {
     FusedParams fp;
     fp.blkT = P->d_blkT; fp.blkMeta = P->d_blkMeta; fp.blkSym0 = P->d_blkSym0;
-    fp.n_sym = P->n_sym; fp.n_rows = P->n_rows; fp.n_meas = P->n_meas; fp.n_det = P->n_det; fp.n_obs = P->n_obs;
-    fp.nw = L.nw; fp.winBlk = L.d_winBlk; fp.aItem = L.d_aItem; fp.aOff = L.d_aOff; fp.idx4 = L.d_idx4;
+    fp.colOff = P->d_colOff; fp.colRows = P->d_colRows;
+    fp.n_blk = P->n_blk; fp.n_rows = P->n_rows; fp.n_meas = P->n_meas; fp.n_det = P->n_det; fp.n_obs = P->n_obs;
     fp.cflag = P->d_fCflag; fp.bItem = P->d_fChain; fp.bOff = P->d_fBOff;
     fp.cOff = P->d_fCOff; fp.cRefs = P->d_fCRefs;
     fp.seed = seed; fp.shot0 = shot0; fp.nshots = nshots;
     fp.out[0] = d_meas; fp.out[1] = d_det; fp.out[2] = d_obs;
     fp.rows0[0] = 0; fp.rows0[1] = P->n_meas; fp.rows0[2] = P->n_meas + P->n_det;
     fp.nrow[0] = P->n_meas; fp.nrow[1] = P->n_det; fp.nrow[2] = P->n_obs;
-    fp.rec_off_words = rec_off;
-    fp.q_off_words = rec_off + (uint32_t)(P->n_rows * tw);
+    fp.aux_off_words = aux_offset(P, tw);
     return fp;
 }
 
@@ -1063,8 +941,7 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
 {
     if (nshots == 0) return SP_OK;
     if (!P->fused_tw) return set_error(SP_ERR_INVALID_ARG, "fused path unavailable for this program");
-    const FusedParams fp = fused_params(P, P->layouts[P->fused_layout], P->fused_tw, P->fused_rec_off, seed, shot0, nshots,
-                                        d_meas, d_det, d_obs);
+    const FusedParams fp = fused_params(P, P->fused_tw, seed, shot0, nshots, d_meas, d_det, d_obs);
     const uint64_t per_tile = 32u * (uint64_t)P->fused_tw;
     const uint64_t ntiles = (nshots + per_tile - 1) / per_tile;
     const uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)P->num_sms * (uint64_t)P->fused_ctas_per_sm);
@@ -1155,7 +1032,7 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
     int smem_max = 0, nsm = 0;
     SP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     SP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    struct Entry { uint32_t i; double cost; int nw; };
+    struct Entry { uint32_t i; double cost; };
     std::vector<Entry> fused[2];
     std::vector<uint32_t> staged;
     for (uint32_t i = 0; i < n; i++) {
@@ -1163,8 +1040,9 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
         plan->progs.push_back(P);
         if (nshots[i] == 0) continue;
         const bool fused_ok = P->path == SP_PATH_FUSED && P->fused_tw;
-        if (fused_ok && P->nw_half) fused[0].push_back({i, (double)P->n_blk, P->nw_half});
-        else if (fused_ok && P->nw_full1) fused[1].push_back({i, (double)P->n_blk, P->nw_full1});
+        const size_t bytes = fused_ok ? fused_words(P, 1) * 4 : 0;
+        if (fused_ok && bytes <= (size_t)smem_max / 2 - 1024) fused[0].push_back({i, (double)P->n_blk});
+        else if (fused_ok && bytes <= (size_t)smem_max) fused[1].push_back({i, (double)P->n_blk});
         else staged.push_back(i);
     }
     for (uint32_t i : staged) {
@@ -1182,12 +1060,8 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
         size_t smem = 0;
         for (const Entry &e : v) {
             sp_program *P = progs[e.i];
-            FusedLayout *L = nullptr;
-            sp_status st = get_layout(P, e.nw, &L);
-            if (st != SP_OK) return st;
-            uint32_t rec_off = 0;
-            const size_t bytes = fused_words(P, 1, L->maxw, &rec_off) * 4;
-            params.push_back(fused_params(P, *L, 1, rec_off, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
+            const size_t bytes = fused_words(P, 1) * 4;
+            params.push_back(fused_params(P, 1, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
                                           d_det ? d_det[e.i] : nullptr, d_obs ? d_obs[e.i] : nullptr));
             acc += (nshots[e.i] + 31) / 32;
             tileEnd.push_back(acc);

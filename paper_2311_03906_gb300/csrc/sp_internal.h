@@ -53,25 +53,6 @@ struct TraverseCounts {
     uint32_t pad[2];
 };
 
-// Step-A program of the fused kernel for one window count: window
-// boundaries and, per (window, thread), the rows whose own part has symbols
-// in that window, with 16-bit window-relative symbol indices.
-struct FusedLayout {
-    int nw_req = 0;                   // window count asked for
-    int nw = 0;                       // windows produced
-    uint32_t maxw = 0;                // symbols in the largest window
-    int64_t groups = 0;
-    uint32_t *d_winBlk = nullptr;
-    uint4 *d_aItem = nullptr;
-    uint32_t *d_aOff = nullptr;
-    uint4 *d_idx4 = nullptr;
-    void release()
-    {
-        cudaFree(d_winBlk); cudaFree(d_aItem); cudaFree(d_aOff); cudaFree(d_idx4);
-        d_winBlk = nullptr; d_aItem = nullptr; d_aOff = nullptr; d_idx4 = nullptr;
-    }
-};
-
 // ----------------------------------------------------------------------------
 // A built program.
 // ----------------------------------------------------------------------------
@@ -140,15 +121,14 @@ struct sp_program {
     uint32_t *d_fBOff = nullptr;      // [threads+1]
     uint32_t *d_fCOff = nullptr;      // step C: target t = XOR of measurement rows d_fCRefs[off[t]..off[t+1])
     uint32_t *d_fCRefs = nullptr;
-    std::vector<sp::FusedLayout> layouts;   // per window count: windows and step-A items
-    std::vector<uint32_t> h_own_off, h_own_idx, h_blkSym0;  // host copies used to build layouts
-    int nw_half = 0, nw_full1 = 0, nw_full2 = 0, nw_half2 = 0;  // window counts that fit (0 = none)
+    // symbol -> measurement rows whose own part holds it (CSC of the own parts)
+    uint32_t *d_colOff = nullptr;     // [n_sym + 1]
+    uint32_t *d_colRows = nullptr;    // [nnz_delta]
     int smem_max = 0;
     int fused_tw = 0;                 // shots per tile / 32 (0 = fused path off)
-    int fused_unroll = 2;             // channel blocks per draw iteration
-    int fused_layout = 0;             // index into layouts
+    int fused_unroll = 1;             // 2: the 64-shot variant with one CTA per SM
     size_t fused_smem = 0;
-    uint32_t fused_rec_off = 0;
+    uint32_t fused_aux_off = 0;       // shared-memory words before the queue/stage region
     bool tuned = false;
     int autotune_launches = 0;        // fused-kernel launches made by the autotuner
     int fused_ctas_per_sm = 1;
@@ -193,11 +173,10 @@ int64_t default_chunk(const sp_program *P);
 sp_status build_fused_program(sp_program *P, cudaStream_t s);
 sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
                       uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
-int min_windows(const sp_program *P, int tw, size_t budget_bytes);
 sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *seeds, const uint64_t *nshots,
                        uint64_t *const *d_meas, uint64_t *const *d_det, uint64_t *const *d_obs, cudaStream_t s);
 void batch_forget(const sp_program *P);
-sp_status fused_select(sp_program *P, int tw, int nw, int unroll);
+sp_status fused_select(sp_program *P, int tw, int unroll);
 sp_status autotune(sp_program *P, cudaStream_t s);
 sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *B,
                              int64_t pitch, cudaStream_t s);

@@ -22,7 +22,7 @@ def _u64(t):
 
 
 def _suite():
-    # uneven: tiny to d=15 (the last does not fit a fused tile -> staged)
+    # uneven: tiny to d=15; the test sends one of them through the staged kernels
     specs = [(repetition_code(5, 5, 0.01), 1, 1000), (surface_code(3, 3, 2e-3), 2, 4097),
              (surface_code(5, 5, 1e-3), 3, 777), (surface_code(7, 7, 5e-4), 4, 3001),
              (surface_code(9, 9, 2e-3), 5, 2048), (surface_code(15, 15, 1e-3), 6, 1500),
@@ -33,7 +33,7 @@ def _suite():
 def test_batch_matches_separate_calls_and_replay():
     specs = _suite()
     progs = [sp.build(c) for c, _, _ in specs]
-    assert progs[5].info["fused_windows"] > 1, "d=15 needs several symbol windows"
+    assert progs[5].info["path"] == sp.PATH_FUSED
     progs[2].set_path(sp.PATH_SPARSE)   # one circuit through the staged kernels
     seeds = [s for _, s, _ in specs]
     shots = [n for _, _, n in specs]
