@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, (TW == 2 && U == 2) ? 1 : 2) k_
 }
 
 // Batched form: many programs in one persistent launch.  Work items are
-// (program, 32-shot tile) pairs handed out in order by an atomic counter;
+// (program, 64-shot tile) pairs handed out in order by an atomic counter;
 // items of program i are [tileEnd[i-1], tileEnd[i]).  The launcher orders
 // the programs by decreasing cost per tile so the tail is made of the
 // cheapest items.
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, MINB) k_fused_batch(const Fused
             const int mid = (lo + hi) >> 1;
             if (tileEnd[mid] > item) hi = mid; else lo = mid + 1;
         }
-        fused_tile<1>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
+        fused_tile<2>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
     }
 }
 
@@ -1040,7 +1040,7 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
         plan->progs.push_back(P);
         if (nshots[i] == 0) continue;
         const bool fused_ok = P->path == SP_PATH_FUSED && P->fused_tw;
-        const size_t bytes = fused_ok ? fused_words(P, 1) * 4 : 0;
+        const size_t bytes = fused_ok ? fused_words(P, 2) * 4 : 0;
         if (fused_ok && bytes <= (size_t)smem_max / 2 - 1024) fused[0].push_back({i, (double)P->n_blk});
         else if (fused_ok && bytes <= (size_t)smem_max) fused[1].push_back({i, (double)P->n_blk});
         else staged.push_back(i);
@@ -1060,10 +1060,10 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
         size_t smem = 0;
         for (const Entry &e : v) {
             sp_program *P = progs[e.i];
-            const size_t bytes = fused_words(P, 1) * 4;
-            params.push_back(fused_params(P, 1, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
+            const size_t bytes = fused_words(P, 2) * 4;
+            params.push_back(fused_params(P, 2, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
                                           d_det ? d_det[e.i] : nullptr, d_obs ? d_obs[e.i] : nullptr));
-            acc += (nshots[e.i] + 31) / 32;
+            acc += (nshots[e.i] + 63) / 64;
             tileEnd.push_back(acc);
             smem = std::max(smem, bytes);
         }
