@@ -98,8 +98,9 @@ typedef struct {
 enum {
     SP_PATH_AUTO = 0,      /* chosen at build time from the measured density */
     SP_PATH_SPARSE = 1,    /* symbol-index XOR gather over bit-sliced shots */
-    SP_PATH_DENSE = 2,     /* 64-bit AND/popcount parity over shot-major words */
-    SP_PATH_FUSED = 3      /* draw + sparse product + epilogue in one kernel, tile in shared memory */
+    SP_PATH_DENSE = 2,     /* AND/XOR over shot-major words, then popcount parity (CUDA cores) */
+    SP_PATH_FUSED = 3,     /* draw + sparse product + epilogue in one kernel, tile in shared memory */
+    SP_PATH_TENSOR = 4     /* 0/1 FP8 tensor-core contraction (tcgen05), exact FP32 sums, parity */
 };
 
 typedef struct {
@@ -114,7 +115,7 @@ typedef struct {
     uint64_t nnz_delta;            /* after parent-delta encoding */
     uint64_t log_words;            /* length of the traversal's row-operation log */
     double density;                /* nnz_rows / (rows * n_s) */
-    int32_t path;                  /* SP_PATH_SPARSE, SP_PATH_DENSE or SP_PATH_FUSED */
+    int32_t path;                  /* SP_PATH_SPARSE, SP_PATH_DENSE, SP_PATH_FUSED or SP_PATH_TENSOR */
     int32_t fused_tile_shots;      /* shots per fused tile (32 or 64; 0 = fused path unavailable) */
     int32_t fused_variant;         /* 1, or 2 = the 64-shot kernel built for one CTA per SM */
     int32_t fused_ctas_per_sm;     /* resident CTAs per SM of the chosen fused kernel */
@@ -261,12 +262,22 @@ SP_API sp_status sp_set_fused_config(sp_program *prog, int32_t tile_shots, int32
 /* sp_set_chunk -- shots per internal chunk (multiple of 1024, 0 = default). */
 SP_API sp_status sp_set_chunk(sp_program *prog, uint64_t chunk_shots);
 
+/*
+ * sp_device_status -- wait for the device, then report and clear the status
+ * word that the program's tensor-core kernel sets when one of its bounded
+ * waits (on a bulk copy or on its own MMAs) ran out: *status = 0 if every
+ * launch since the last call completed, 1 if some tile gave up (its records
+ * are then not written).  Other kernels have no waits and leave it 0.
+ */
+SP_API sp_status sp_device_status(sp_program *prog, int32_t *status);
+
 /* Kernel classes reported by sp_profile_read. */
 enum {
     SP_KERNEL_DRAW = 0,      /* Philox fault draw */
     SP_KERNEL_PRODUCT = 1,   /* GF(2) product (sparse or dense variant) */
     SP_KERNEL_EMIT = 2,      /* bit-sliced -> shot-major record transpose */
     SP_KERNEL_FUSED = 3,     /* fused draw + product */
+    SP_KERNEL_TENSOR = 4,    /* tensor-core (tcgen05) product */
     SP_KERNEL_CLASSES = 8
 };
 

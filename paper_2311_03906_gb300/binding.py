@@ -22,15 +22,15 @@ STATUS_NAMES = {0: "SP_OK", 1: "SP_ERR_INVALID_ARG", 2: "SP_ERR_UNSUPPORTED_OP",
 OPCODES = {"H": 0, "S": 1, "CX": 2, "X": 3, "Y": 4, "Z": 5, "M": 6, "MR": 7, "R": 8,
            "X_ERROR": 9, "Y_ERROR": 10, "Z_ERROR": 11, "DEPOLARIZE1": 12, "DEPOLARIZE2": 13,
            "DETECTOR": 14, "OBSERVABLE_INCLUDE": 15, "TICK": 16}
-PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED = 0, 1, 2, 3
+PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED, PATH_TENSOR = 0, 1, 2, 3, 4
 
 # every entry point declared in include/symphase.h
 EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",
            "sp_sample_batch", "sp_expect",
            "sp_expect_grad", "sp_export_rows", "sp_export_channels", "sp_set_path", "sp_set_fused_config",
-           "sp_set_chunk",
+           "sp_set_chunk", "sp_device_status",
            "sp_profile_enable", "sp_profile_read", "sp_free", "sp_last_error")
-KERNEL_CLASSES = ("draw", "product", "emit", "fused")
+KERNEL_CLASSES = ("draw", "product", "emit", "fused", "tensor")
 
 
 class SymPhaseError(RuntimeError):
@@ -88,6 +88,7 @@ def load() -> C.CDLL:
     lib.sp_export_channels.argtypes = [vp, vp, vp, vp]
     lib.sp_set_path.argtypes = [vp, i32]
     lib.sp_set_chunk.argtypes = [vp, u64]
+    lib.sp_device_status.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.sp_set_fused_config.argtypes = [vp, i32, i32]
     lib.sp_profile_enable.argtypes = [vp, i32]
     lib.sp_profile_read.argtypes = [vp, vp, vp]
@@ -229,6 +230,13 @@ class Program:
     def set_chunk(self, chunk_shots: int):
         _check(self._lib.sp_set_chunk(self._h, chunk_shots))
         self.refresh_info()
+
+    def device_status(self) -> int:
+        """Waits for the device; 0 if every tensor-core tile since the last
+        call completed, 1 if one gave up on a bounded wait."""
+        v = C.c_int32(0)
+        _check(self._lib.sp_device_status(self._h, C.byref(v)))
+        return int(v.value)
 
     def profile(self, on: bool = True):
         _check(self._lib.sp_profile_enable(self._h, 1 if on else 0))

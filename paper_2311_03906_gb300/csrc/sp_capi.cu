@@ -34,7 +34,8 @@ static void release(sp_program *P)
                     P->d_parent, P->d_cflag, P->d_A64, P->d_const, P->d_inc, P->d_incT, P->d_kappa,
                     P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta,
                     P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs,
-                    P->d_colOff, P->d_colRows};
+                    P->d_colOff, P->d_colRows, P->d_AT, P->d_tc_coef[0], P->d_tc_coef[1], P->d_tc_coef[2],
+                    P->d_tc_status};
     for (void *b : bufs) if (b) cudaFree(b);
     if (P->h_stage) cudaFreeHost(P->h_stage);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -146,8 +147,10 @@ sp_status sp_sample(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshot
     if (P->path == SP_PATH_FUSED && P->fused_tw)
         return fused_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     const int64_t chunk = P->chunk_shots;
-    st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)chunk));
-    if (st != SP_OK) return st;
+    if (uses_staged_scratch(P)) {
+        st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)chunk));
+        if (st != SP_OK) return st;
+    }
     const int64_t wm = words64(P->n_meas), wd = words64(P->n_det), wo = words64(P->n_obs);
     for (uint64_t done = 0; done < nshots;) {
         const uint64_t n = std::min<uint64_t>(nshots - done, (uint64_t)chunk);
@@ -172,7 +175,7 @@ sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t 
     int64_t piece = std::min<int64_t>(P->chunk_shots, std::max<int64_t>(1024, (64 << 20) / std::max<int64_t>(per_shot * 8, 8)));
     piece = std::max<int64_t>(1024, (piece / 1024) * 1024);
     sp_status st = SP_OK;
-    if (!(P->path == SP_PATH_FUSED && P->fused_tw)) {
+    if (uses_staged_scratch(P)) {
         st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)piece));
         if (st != SP_OK) return st;
     }
@@ -288,7 +291,10 @@ sp_status sp_set_path(sp_program *P, int32_t path)
     if (path == SP_PATH_AUTO) { P->path = P->build_path; return SP_OK; }
     if (path == SP_PATH_FUSED && !P->fused_tw)
         return set_error(SP_ERR_INVALID_ARG, "the fused path is unavailable for this program");
-    if (path != SP_PATH_SPARSE && path != SP_PATH_FUSED) return set_error(SP_ERR_INVALID_ARG, "unsupported path");
+    if (path == SP_PATH_TENSOR && !tensor_path_available(P))
+        return set_error(SP_ERR_INVALID_ARG, "the tensor-core path is unavailable for this program or device");
+    if (path != SP_PATH_SPARSE && path != SP_PATH_FUSED && path != SP_PATH_DENSE && path != SP_PATH_TENSOR)
+        return set_error(SP_ERR_INVALID_ARG, "unsupported path");
     P->path = path;
     return SP_OK;
 }
@@ -298,6 +304,19 @@ sp_status sp_set_fused_config(sp_program *P, int32_t tile_shots, int32_t variant
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
     if (tile_shots != 32 && tile_shots != 64) return set_error(SP_ERR_INVALID_ARG, "tile_shots must be 32 or 64");
     return fused_select(P, tile_shots / 32, variant);
+}
+
+sp_status sp_device_status(sp_program *P, int32_t *status)
+{
+    if (!P || !status) return set_error(SP_ERR_INVALID_ARG, "prog and status must not be NULL");
+    *status = 0;
+    if (!P->d_tc_status) return SP_OK;
+    int v = 0;
+    SP_CUDA(cudaDeviceSynchronize());
+    SP_CUDA(cudaMemcpy(&v, P->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) SP_CUDA(cudaMemset(P->d_tc_status, 0, sizeof(int)));
+    *status = v;
+    return SP_OK;
 }
 
 sp_status sp_set_chunk(sp_program *P, uint64_t chunk_shots)

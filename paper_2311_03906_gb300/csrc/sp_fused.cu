@@ -43,17 +43,6 @@ constexpr uint32_t PH_M0 = 0xD2511F53u, PH_M1 = 0xCD9E8D57u;
 constexpr uint32_t PH_W0 = 0x9E3779B9u, PH_W1 = 0xBB67AE85u;
 constexpr int FUSED_THREADS = 512;
 
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
-{
-    const uint32_t m16 = 0x0000FFFFu, m8 = 0x00FF00FFu, m4 = 0x0F0F0F0Fu, m2 = 0x33333333u, m1 = 0x55555555u;
-    uint32_t y;
-    y = __shfl_xor_sync(FM, x, 16); x = (lane & 16) ? ((x & ~m16) | ((y >> 16) & m16)) : ((x & m16) | ((y & m16) << 16));
-    y = __shfl_xor_sync(FM, x, 8);  x = (lane & 8) ? ((x & ~m8) | ((y >> 8) & m8)) : ((x & m8) | ((y & m8) << 8));
-    y = __shfl_xor_sync(FM, x, 4);  x = (lane & 4) ? ((x & ~m4) | ((y >> 4) & m4)) : ((x & m4) | ((y & m4) << 4));
-    y = __shfl_xor_sync(FM, x, 2);  x = (lane & 2) ? ((x & ~m2) | ((y >> 2) & m2)) : ((x & m2) | ((y & m2) << 2));
-    y = __shfl_xor_sync(FM, x, 1);  x = (lane & 1) ? ((x & ~m1) | ((y >> 1) & m1)) : ((x & m1) | ((y & m1) << 1));
-    return x;
-}
 
 // Per-shot quantities of the first two Philox rounds that do not depend on
 // the channel block.
@@ -156,7 +145,11 @@ __device__ __forceinline__ uint32_t chan_bits(uint32_t u, uint32_t T, uint32_t k
 template <int TW> struct Cols { uint32_t v[TW]; };
 template <int TW> struct Shots { ShotConst s[TW]; };
 
-template <int TW, int U, typename Sink>
+// RAW: the lane's own 32-bit words are handed over untransposed (bit k =
+// entry base+k of its shot's vector), and the vector starts with the
+// constant symbol s_0 = 1 at bit 0 (b_0 = 1 of Eq. sampling), so that
+// symbol k of the draw sits at bit k+1.
+template <int TW, int U, bool RAW = false, typename Sink>
 __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
                                             uint32_t b0, uint32_t b1, uint32_t sym_begin, const Shots<TW> sc,
                                             uint32_t k0, uint32_t k1, int lane, Sink sink)
@@ -164,14 +157,14 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
     const Keys K = make_keys(k0, k1);
     uint64_t acc[TW];
 #pragma unroll
-    for (int t = 0; t < TW; t++) acc[t] = 0;
-    uint32_t fill = 0, base = sym_begin;
+    for (int t = 0; t < TW; t++) acc[t] = RAW ? 1u : 0u;
+    uint32_t fill = RAW ? 1u : 0u, base = sym_begin;
     auto flush = [&]() {
         Cols<TW> col;
 #pragma unroll
         for (int t = 0; t < TW; t++) {
             const uint32_t lo = (uint32_t)acc[t];
-            col.v[t] = __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
+            col.v[t] = RAW ? lo : __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
             acc[t] >>= 32;
         }
         sink(base, col);
@@ -263,7 +256,7 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
 #pragma unroll
         for (int t = 0; t < TW; t++) {
             const uint32_t lo = (uint32_t)acc[t];
-            col.v[t] = __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
+            col.v[t] = RAW ? lo : __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
         }
         sink(base, col);
     }
@@ -627,6 +620,37 @@ __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ b
                    [=](uint32_t base, const Cols<1> col) {
                        if ((int64_t)base + lane < n_sym) B[(size_t)(base + lane) * bpitch + w] = col.v[0];
                    });
+}
+
+// Shot-major draw for the dense products: warp = one group of 32 shots, and
+// word w of shot 32g+l (entries 32w..32w+31 of (s_0, s_1, ...)) is stored at
+// Bd[(g * bpitch + w) * 32 + l], so that a warp's stores are contiguous.
+// Words past the last symbol are never written: the coefficient rows are
+// zero there.
+__global__ void __launch_bounds__(256) k_draw_dense(const uint4 *__restrict__ blkT,
+                                                    const uint32_t *__restrict__ blkMeta, int64_t n_blk,
+                                                    uint64_t seed, uint64_t shot0, int64_t ngroups,
+                                                    uint32_t *__restrict__ Bd, int64_t bpitch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (g >= ngroups) return;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    Shots<1> sc;
+    sc.s[0] = shot_const(shot0 + (uint64_t)g * 32u + (uint64_t)lane, k1);
+    uint32_t *dst = Bd + (size_t)g * (size_t)bpitch * 32u + lane;
+    draw_blocks<1, 2, true>(blkT, blkMeta, 0u, (uint32_t)n_blk, 0u, sc, k0, k1, lane,
+                            [=](uint32_t base, const Cols<1> col) { dst[(size_t)(base / 32u) * 32u] = col.v[0]; });
+}
+
+sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t ngroups, uint32_t *Bd,
+                            int64_t bpitch, cudaStream_t s)
+{
+    if (ngroups == 0) return SP_OK;
+    k_draw_dense<<<(unsigned)ceil_div(ngroups, 8), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->n_blk, seed, shot0,
+                                                                 ngroups, Bd, bpitch);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
 }
 
 // ---------------------------------------------------------------------------

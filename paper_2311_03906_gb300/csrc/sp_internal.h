@@ -91,7 +91,14 @@ struct sp_program {
     // scratch (owned, reused across sample calls)
     uint32_t *d_B = nullptr;        // fault bits, bit-sliced: [n_sym][chunk/32]
     uint32_t *d_recT = nullptr;     // records, bit-sliced: [n_rows][chunk/32]
-    uint64_t *d_Bd = nullptr;       // dense path: fault bits shot-major [chunk][a64pitch]
+    uint32_t *d_Bd = nullptr;       // dense paths: fault bits shot-major, [group of 32 shots][apitch][32]
+    size_t dense_shots = 0;         // shots d_Bd holds
+    uint32_t *d_AT = nullptr;       // dense paths: coefficient words transposed, [apitch][rpitch]
+    int64_t rpitch = 0;             // rows of d_AT (n_rows rounded up to 32)
+    uint8_t *d_tc_coef[3] = {nullptr, nullptr, nullptr};  // tensor path: E4M3 stage blocks per record kind
+    int64_t tc_ntiles[3] = {0, 0, 0};                     // 128-row tiles per record kind
+    int64_t tc_nks = 0;                                   // 256-symbol K stages
+    int *d_tc_status = nullptr;                           // tensor kernel status word (0 = ok)
     size_t scratch_shots = 0;
     int64_t chunk_shots = 0;
     int path = SP_PATH_SPARSE;
@@ -164,11 +171,24 @@ struct ProfScope {
     ~ProfScope();
 };
 
+// the staged sparse kernels' scratch (d_B, d_recT) is needed on that path only
+inline bool uses_staged_scratch(const sp_program *P)
+{
+    return !(P->path == SP_PATH_FUSED && P->fused_tw) && P->path != SP_PATH_DENSE && P->path != SP_PATH_TENSOR;
+}
+
 // sampling (sp_sample.cu)
 sp_status ensure_scratch(sp_program *P, size_t shots);
 sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
                        uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
 int64_t default_chunk(const sp_program *P);
+// dense paths (sp_dense.cu)
+sp_status ensure_dense(sp_program *P, size_t shots, cudaStream_t s);
+bool tensor_path_available(const sp_program *P);
+sp_status dense_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
+                      uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
+sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t ngroups, uint32_t *Bd,
+                            int64_t bpitch, cudaStream_t s);
 // fused path (sp_fused.cu)
 sp_status build_fused_program(sp_program *P, cudaStream_t s);
 sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
@@ -189,6 +209,21 @@ sp_status expect_fwd(sp_program *P, const float *d_p, float *d_logE, cudaStream_
 sp_status expect_bwd(sp_program *P, const float *d_p, const float *d_g, float *d_grad, cudaStream_t s);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// 32x32 bit transpose across a warp: lane j receives, as bit l, bit j of
+// lane l's word.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
+{
+    constexpr uint32_t FULL = 0xffffffffu;
+    const uint32_t m16 = 0x0000FFFFu, m8 = 0x00FF00FFu, m4 = 0x0F0F0F0Fu, m2 = 0x33333333u, m1 = 0x55555555u;
+    uint32_t y;
+    y = __shfl_xor_sync(FULL, x, 16); x = (lane & 16) ? ((x & ~m16) | ((y >> 16) & m16)) : ((x & m16) | ((y & m16) << 16));
+    y = __shfl_xor_sync(FULL, x, 8);  x = (lane & 8) ? ((x & ~m8) | ((y >> 8) & m8)) : ((x & m8) | ((y & m8) << 8));
+    y = __shfl_xor_sync(FULL, x, 4);  x = (lane & 4) ? ((x & ~m4) | ((y >> 4) & m4)) : ((x & m4) | ((y & m4) << 4));
+    y = __shfl_xor_sync(FULL, x, 2);  x = (lane & 2) ? ((x & ~m2) | ((y >> 2) & m2)) : ((x & m2) | ((y & m2) << 2));
+    y = __shfl_xor_sync(FULL, x, 1);  x = (lane & 1) ? ((x & ~m1) | ((y >> 1) & m1)) : ((x & m1) | ((y & m1) << 1));
+    return x;
+}
 
 // Raise a kernel's dynamic shared-memory limit to the most the device
 // allows next to its static shared memory.  The limit belongs to the kernel,

@@ -22,19 +22,6 @@ namespace sp {
 
 constexpr uint32_t FULLM = 0xffffffffu;
 
-// 32x32 bit transpose across a warp: in lane l holds row l (bit j = M[l][j]);
-// out lane j holds column j (bit l = M[l][j]).
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
-{
-    const uint32_t m16 = 0x0000FFFFu, m8 = 0x00FF00FFu, m4 = 0x0F0F0F0Fu, m2 = 0x33333333u, m1 = 0x55555555u;
-    uint32_t y;
-    y = __shfl_xor_sync(FULLM, x, 16); x = (lane & 16) ? ((x & ~m16) | ((y >> 16) & m16)) : ((x & m16) | ((y & m16) << 16));
-    y = __shfl_xor_sync(FULLM, x, 8);  x = (lane & 8) ? ((x & ~m8) | ((y >> 8) & m8)) : ((x & m8) | ((y & m8) << 8));
-    y = __shfl_xor_sync(FULLM, x, 4);  x = (lane & 4) ? ((x & ~m4) | ((y >> 4) & m4)) : ((x & m4) | ((y & m4) << 4));
-    y = __shfl_xor_sync(FULLM, x, 2);  x = (lane & 2) ? ((x & ~m2) | ((y >> 2) & m2)) : ((x & m2) | ((y & m2) << 2));
-    y = __shfl_xor_sync(FULLM, x, 1);  x = (lane & 1) ? ((x & ~m1) | ((y >> 1) & m1)) : ((x & m1) | ((y & m1) << 1));
-    return x;
-}
 
 // K5.  Warp = 1024 shots (lane = 32-shot word); rows in order so a parent
 // is always finished (by the same lane) before its children.
@@ -97,7 +84,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ recT,
     for (int q = warp; q < 64; q += 8) {
         const int g = q >> 3, k = q & 7;
         const uint32_t x = in_t[g * 32 + lane][k];
-        out_t[k * 32 + lane][g] = warp_transpose32(x, lane);
+        out_t[k * 32 + lane][g] = transpose32(x, lane);
     }
     __syncthreads();
     const int64_t shot = wb * 32 + t;
@@ -188,6 +175,8 @@ sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t ns
     const int64_t pitch = (int64_t)((P->scratch_shots + 31) / 32);
     if (P->path == SP_PATH_FUSED && P->fused_tw)
         return fused_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
+    if (P->path == SP_PATH_DENSE || P->path == SP_PATH_TENSOR)
+        return dense_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     if (P->n_sym > 0) {
         ProfScope ps(P, SP_KERNEL_DRAW, s);
         sp_status st = launch_draw_staged(P, seed, shot0, nwords, P->d_B, pitch, s);
