@@ -123,6 +123,8 @@ typedef struct {
     int32_t reserved;
     uint64_t chunk_shots;          /* shots per internal sampling chunk */
     double build_ms;               /* wall time of sp_build */
+    double path_probe_ms[5];       /* build-time probe of 32,768 shots per SP_PATH_* (0 = not timed: the
+                                      dense forms are timed only where >= 1 % of the coefficients are set) */
 } sp_info_t;
 
 typedef struct sp_program sp_program;   /* opaque, library-owned */

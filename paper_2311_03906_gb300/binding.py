@@ -56,7 +56,7 @@ class sp_info_t(C.Structure):
                 ("log_words", C.c_uint64), ("density", C.c_double), ("path", C.c_int32),
                 ("fused_tile_shots", C.c_int32), ("fused_variant", C.c_int32),
                 ("fused_ctas_per_sm", C.c_int32), ("autotune_launches", C.c_int32), ("reserved", C.c_int32),
-                ("chunk_shots", C.c_uint64), ("build_ms", C.c_double)]
+                ("chunk_shots", C.c_uint64), ("build_ms", C.c_double), ("path_probe_ms", C.c_double * 5)]
 
 
 _lib = None
@@ -150,7 +150,8 @@ class Program:
         del keep
         info = sp_info_t()
         _check(lib.sp_info(h, C.byref(info)))
-        self.info = {f: getattr(info, f) for f, _ in sp_info_t._fields_}
+        self.info = {f: (list(getattr(info, f)) if f == "path_probe_ms" else getattr(info, f))
+                     for f, _ in sp_info_t._fields_}
         self.num_measurements = info.num_measurements
         self.num_detectors = info.num_detectors
         self.num_observables = info.num_observables
@@ -175,7 +176,8 @@ class Program:
     def refresh_info(self):
         info = sp_info_t()
         _check(self._lib.sp_info(self._h, C.byref(info)))
-        self.info = {f: getattr(info, f) for f, _ in sp_info_t._fields_}
+        self.info = {f: (list(getattr(info, f)) if f == "path_probe_ms" else getattr(info, f))
+                     for f, _ in sp_info_t._fields_}
         return self.info
 
     # -------------------------------------------------------------- records

@@ -928,9 +928,8 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     P->density = (double)P->nnz_rows / cells;
     SP_TRY(build_fused_program(P, stream));
     SP_TRY(autotune(P, stream));
-    P->build_path = P->fused_tw ? SP_PATH_FUSED : SP_PATH_SPARSE;
-    P->path = P->build_path;
     P->chunk_shots = default_chunk(P);
+    SP_TRY(choose_path(P, stream));
     P->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return SP_OK;
 }

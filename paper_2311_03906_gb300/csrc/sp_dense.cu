@@ -409,12 +409,14 @@ bool tensor_path_available(const sp_program *P)
 // device status word of the tensor-core kernel.
 static sp_status ensure_tensor(sp_program *P, cudaStream_t s)
 {
-    if (P->d_tc_status) return SP_OK;
+    if (P->tc_ready) return SP_OK;
     const int64_t rows0[3] = {0, P->n_meas, P->n_meas + P->n_det};
     const int64_t nrow[3] = {P->n_meas, P->n_det, P->n_obs};
     P->tc_nks = ceil_div(P->apitch, TC_KS / 32);
     for (int k = 0; k < 3; k++) {
         P->tc_ntiles[k] = nrow[k] ? ceil_div(2 * ceil_div(nrow[k], 64), TC_N / 32) : 0;
+        cudaFree(P->d_tc_coef[k]);
+        P->d_tc_coef[k] = nullptr;
         if (!P->tc_ntiles[k]) continue;
         const int64_t chunks = P->tc_ntiles[k] * P->tc_nks * (TC_STAGE_BYTES / 16);
         if (cudaMalloc((void **)&P->d_tc_coef[k], (size_t)chunks * 16) != cudaSuccess) {
@@ -427,14 +429,17 @@ static sp_status ensure_tensor(sp_program *P, cudaStream_t s)
                                                                     reinterpret_cast<uint4 *>(P->d_tc_coef[k]));
         SP_CUDA(cudaGetLastError());
     }
-    int *st = nullptr;
-    if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(SP_ERR_OOM, "cudaMalloc of the device status word failed");
+    if (!P->d_tc_status) {
+        int *st = nullptr;
+        if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(SP_ERR_OOM, "cudaMalloc of the device status word failed");
+        }
+        SP_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
+        P->d_tc_status = st;
     }
-    SP_CUDA(cudaMemsetAsync(st, 0, sizeof(int), s));
     SP_CUDA(cudaFuncSetAttribute(k_tc_product, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    P->d_tc_status = st;
+    P->tc_ready = true;
     return SP_OK;
 }
 
@@ -476,6 +481,104 @@ sp_status dense_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
                                             reinterpret_cast<uint32_t *>(g.dst));
         SP_CUDA(cudaGetLastError());
     }
+    return SP_OK;
+}
+
+}  // namespace sp
+
+namespace sp {
+
+namespace {
+
+sp_status run_path(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t shots, uint64_t *om, uint64_t *od,
+                   uint64_t *oo, cudaStream_t s)
+{
+    const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
+    for (uint64_t done = 0; done < shots;) {
+        const uint64_t n = std::min<uint64_t>(shots - done, (uint64_t)P->chunk_shots);
+        sp_status st = sample_chunk(P, seed, shot0 + done, n, om + done * wm, od + done * wd, oo + done * wo, s);
+        if (st != SP_OK) return st;
+        done += n;
+    }
+    return SP_OK;
+}
+
+void drop_dense_buffers(sp_program *P)
+{
+    cudaFree(P->d_Bd);
+    cudaFree(P->d_AT);
+    for (auto &c : P->d_tc_coef) { cudaFree(c); c = nullptr; }
+    P->tc_ready = false;
+    P->d_Bd = nullptr;
+    P->d_AT = nullptr;
+    P->dense_shots = 0;
+}
+
+}  // namespace
+
+// Per-circuit choice of the product form.  The sparse form (the fused kernel
+// when the records of a tile fit in shared memory, else the staged kernels)
+// is the default; where at least 1 % of the coefficients are nonzero the
+// two dense forms (AND/popcount, tensor cores) are also run on a probe of
+// 32,768 shots (best of two timed runs after a warm-up) and the fastest is
+// kept, the default unless another is at least 3 % faster.  Buffers of the
+// forms not kept are released.
+sp_status choose_path(sp_program *P, cudaStream_t s)
+{
+    P->build_path = P->fused_tw ? SP_PATH_FUSED : SP_PATH_SPARSE;
+    P->path = P->build_path;
+    for (double &t : P->path_probe_ms) t = 0.0;
+    if (P->density < 0.01 || P->n_rows == 0 || P->n_sym == 0) return SP_OK;
+    std::vector<int> cand{P->build_path, SP_PATH_DENSE};
+    if (tensor_path_available(P)) cand.push_back(SP_PATH_TENSOR);
+    const uint64_t shots = 32768;
+    const int64_t words = (P->n_meas + 63) / 64 + (P->n_det + 63) / 64 + (P->n_obs + 63) / 64;
+    uint64_t *out = nullptr;
+    if (cudaMalloc((void **)&out, (size_t)shots * (size_t)std::max<int64_t>(words, 1) * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SP_ERR_OOM, "cudaMalloc of the path probe outputs failed");
+    }
+    uint64_t *om = out, *od = om + shots * ((P->n_meas + 63) / 64), *oo = od + shots * ((P->n_det + 63) / 64);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = P->profiling;
+    P->profiling = false;
+    sp_status st = SP_OK;
+    int pick = P->build_path;
+    float best = 1e30f;
+    for (size_t ci = 0; ci < cand.size() && st == SP_OK; ci++) {
+        P->path = cand[ci];
+        if (uses_staged_scratch(P) && (st = ensure_scratch(P, (size_t)std::min<uint64_t>(shots, P->chunk_shots))) != SP_OK)
+            break;
+        if ((st = run_path(P, 1, 0, shots, om, od, oo, s)) != SP_OK) break;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && st == SP_OK; rep++) {
+            cudaEventRecord(e0, s);
+            st = run_path(P, 1, shots * (rep + 1), shots, om, od, oo, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_error(cudaGetLastError(), "path probe"); break; }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        if (st != SP_OK) break;
+        if (cand[ci] == SP_PATH_TENSOR) {
+            int32_t bad = 0;
+            if ((st = sp_device_status(P, &bad)) != SP_OK) break;
+            if (bad) continue;   // a tile gave up on a bounded wait: never pick this form
+        }
+        P->path_probe_ms[cand[ci]] = ms;
+        if (ci == 0 || ms < 0.97f * best) { best = ms; pick = cand[ci]; }
+    }
+    P->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (st != SP_OK) return st;
+    P->build_path = pick;
+    P->path = pick;
+    if (pick != SP_PATH_DENSE && pick != SP_PATH_TENSOR) drop_dense_buffers(P);
     return SP_OK;
 }
 

@@ -145,11 +145,7 @@ __device__ __forceinline__ uint32_t chan_bits(uint32_t u, uint32_t T, uint32_t k
 template <int TW> struct Cols { uint32_t v[TW]; };
 template <int TW> struct Shots { ShotConst s[TW]; };
 
-// RAW: the lane's own 32-bit words are handed over untransposed (bit k =
-// entry base+k of its shot's vector), and the vector starts with the
-// constant symbol s_0 = 1 at bit 0 (b_0 = 1 of Eq. sampling), so that
-// symbol k of the draw sits at bit k+1.
-template <int TW, int U, bool RAW = false, typename Sink>
+template <int TW, int U, typename Sink>
 __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
                                             uint32_t b0, uint32_t b1, uint32_t sym_begin, const Shots<TW> sc,
                                             uint32_t k0, uint32_t k1, int lane, Sink sink)
@@ -157,14 +153,14 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
     const Keys K = make_keys(k0, k1);
     uint64_t acc[TW];
 #pragma unroll
-    for (int t = 0; t < TW; t++) acc[t] = RAW ? 1u : 0u;
-    uint32_t fill = RAW ? 1u : 0u, base = sym_begin;
+    for (int t = 0; t < TW; t++) acc[t] = 0;
+    uint32_t fill = 0, base = sym_begin;
     auto flush = [&]() {
         Cols<TW> col;
 #pragma unroll
         for (int t = 0; t < TW; t++) {
             const uint32_t lo = (uint32_t)acc[t];
-            col.v[t] = RAW ? lo : __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
+            col.v[t] = __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
             acc[t] >>= 32;
         }
         sink(base, col);
@@ -256,7 +252,7 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
 #pragma unroll
         for (int t = 0; t < TW; t++) {
             const uint32_t lo = (uint32_t)acc[t];
-            col.v[t] = RAW ? lo : __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
+            col.v[t] = __any_sync(FM, lo != 0u) ? transpose32(lo, lane) : 0u;
         }
         sink(base, col);
     }
@@ -284,14 +280,13 @@ __device__ __forceinline__ void xor_column(const uint32_t *__restrict__ colOff, 
 }
 
 // Apply the queued events e = lane, lane+32, ... < n: recompute the event's
-// Philox block, turn each fired channel into its symbol bits and flip the
-// shot's bit in the rows of those symbols.
-template <int TW>
+// Philox block, turn each fired channel into its symbol bits and hand each
+// (symbol, tile word, shot bit) to apply.
+template <int TW, typename Apply>
 __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const uint4 *__restrict__ blkT,
                                             const uint32_t *__restrict__ blkMeta, const uint32_t *__restrict__ blkSym0,
-                                            const uint32_t *__restrict__ colOff, const uint32_t *__restrict__ colRows,
                                             uint32_t b0, uint64_t shot_base, const Keys &K, uint32_t k1, int lane,
-                                            uint32_t *Rw)
+                                            const Apply &apply)
 {
     __syncwarp();
     for (uint32_t e = lane; e < n; e += 32) {
@@ -317,7 +312,7 @@ __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const
             while (val) {
                 const int j = __ffs(val) - 1;
                 val &= val - 1;
-                xor_column<TW>(colOff, colRows, off + (uint32_t)j, t, 1u << ln, Rw);
+                apply(off + (uint32_t)j, t, 1u << ln);
             }
         }
     }
@@ -346,13 +341,11 @@ __device__ __forceinline__ uint32_t fired4(uint32_t r0, uint32_t r1, uint32_t r2
 // warp's queue q, drained by all 32 lanes when it fills and at the end.
 // UHI: every shot of the tile has the same high counter word c1u, so round
 // 2's M0 product is the same in all lanes and tile words.
-template <int TW, bool UHI>
+template <int TW, bool UHI, typename Apply>
 __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
-                                                const uint32_t *__restrict__ blkSym0,
-                                                const uint32_t *__restrict__ colOff,
-                                                const uint32_t *__restrict__ colRows, uint32_t b0, uint32_t b1,
+                                                const uint32_t *__restrict__ blkSym0, uint32_t b0, uint32_t b1,
                                                 const Shots<TW> sc, uint64_t shot_base, uint32_t k0, uint32_t k1,
-                                                int lane, uint32_t *Rw, uint32_t *q)
+                                                int lane, uint32_t *q, const Apply &apply)
 {
     static_assert(TW == 1 || TW == 2, "one or two tile words");
     const Keys K = make_keys(k0, k1);
@@ -374,7 +367,7 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
 #pragma unroll
             for (int t = 0; t < TW; t++) {
                 const uint32_t col = transpose32(word[t], lane);
-                if (mine && !is_dep && col) xor_column<TW>(colOff, colRows, sym, t, col, Rw);
+                if (mine && !is_dep && col) apply(sym, t, col);
             }
         }
         if (!dep) return;
@@ -383,7 +376,7 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
             uint32_t m = word[t] & dep;
             while (__any_sync(FM, m != 0u)) {
                 if (cnt > FUSED_QCAP - 32u) {
-                    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, colOff, colRows, b0, shot_base, K, k1, lane, Rw);
+                    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, b0, shot_base, K, k1, lane, apply);
                     cnt = 0;
                 }
                 const int k = m ? (__ffs(m) - 1) >> 2 : 0;
@@ -439,21 +432,20 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
         for (int t = 0; t < TW; t++) any |= word[t];
         if (__any_sync(FM, any != 0u)) resolve(g, word, jmeta, js0);
     }
-    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, colOff, colRows, b0, shot_base, K, k1, lane, Rw);
+    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, b0, shot_base, K, k1, lane, apply);
 }
 
-template <int TW>
+template <int TW, typename Apply>
 __device__ __forceinline__ void draw_scatter(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
-                                             const uint32_t *__restrict__ blkSym0, const uint32_t *__restrict__ colOff,
-                                             const uint32_t *__restrict__ colRows, uint32_t b0, uint32_t b1,
+                                             const uint32_t *__restrict__ blkSym0, uint32_t b0, uint32_t b1,
                                              const Shots<TW> sc, uint64_t shot_base, uint32_t k0, uint32_t k1,
-                                             int lane, uint32_t *Rw, uint32_t *q)
+                                             int lane, uint32_t *q, const Apply &apply)
 {
     // a tile straddles a multiple of 2^32 shots only if shot0 is unaligned
     if ((shot_base >> 32) == ((shot_base + 32u * TW - 1u) >> 32))
-        draw_group_impl<TW, true>(blkT, blkMeta, blkSym0, colOff, colRows, b0, b1, sc, shot_base, k0, k1, lane, Rw, q);
+        draw_group_impl<TW, true>(blkT, blkMeta, blkSym0, b0, b1, sc, shot_base, k0, k1, lane, q, apply);
     else
-        draw_group_impl<TW, false>(blkT, blkMeta, blkSym0, colOff, colRows, b0, b1, sc, shot_base, k0, k1, lane, Rw, q);
+        draw_group_impl<TW, false>(blkT, blkMeta, blkSym0, b0, b1, sc, shot_base, k0, k1, lane, q, apply);
 }
 
 struct FusedParams {
@@ -512,8 +504,10 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
     {
         const uint32_t b0 = (uint32_t)((uint64_t)warp * (uint64_t)p.n_blk / (uint64_t)nwarps);
         const uint32_t b1 = (uint32_t)((uint64_t)(warp + 1) * (uint64_t)p.n_blk / (uint64_t)nwarps);
-        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, p.colOff, p.colRows, b0, b1, sc, p.shot0 + trel, k0, k1, lane,
-                         sm, aux + warp * FUSED_QCAP);
+        const uint32_t *colOff = p.colOff, *colRows = p.colRows;
+        uint32_t *Rw = sm;
+        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, b0, b1, sc, p.shot0 + trel, k0, k1, lane, aux + warp * FUSED_QCAP,
+                         [=](uint32_t sym, int t, uint32_t word) { xor_column<TW>(colOff, colRows, sym, t, word, Rw); });
     }
     __syncthreads();
     // ---- phase 2B: parent chains, m_j = own part ^ m_parent ---------------
@@ -622,33 +616,62 @@ __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ b
                    });
 }
 
-// Shot-major draw for the dense products: warp = one group of 32 shots, and
-// word w of shot 32g+l (entries 32w..32w+31 of (s_0, s_1, ...)) is stored at
-// Bd[(g * bpitch + w) * 32 + l], so that a warp's stores are contiguous.
-// Words past the last symbol are never written: the coefficient rows are
-// zero there.
-__global__ void __launch_bounds__(256) k_draw_dense(const uint4 *__restrict__ blkT,
-                                                    const uint32_t *__restrict__ blkMeta, int64_t n_blk,
-                                                    uint64_t seed, uint64_t shot0, int64_t ngroups,
-                                                    uint32_t *__restrict__ Bd, int64_t bpitch)
+// Shot-major draw for the dense products.  Word w of shot 32g+l (entries
+// 32w..32w+31 of (s_0, s_1, ...), b_0 = 1 of Eq. sampling) is stored at
+// Bd[(g * bpitch + w) * 32 + l].  k_dense_fill writes the constant bit and
+// zeroes the rest; k_draw_dense runs the grouped draw for 64 shots per warp
+// over every channel block and sets the bit of each fired symbol in the
+// shots that drew it (global atomics: faults are rare).
+__global__ void __launch_bounds__(256) k_dense_fill(uint32_t *__restrict__ Bd, int64_t bpitch, int64_t nvec)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (g >= ngroups) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvec) return;
+    const int64_t w = (i / 8) % bpitch;   // 8 uint4 per 32-lane word
+    const uint32_t v = w == 0 ? 1u : 0u;
+    reinterpret_cast<uint4 *>(Bd)[i] = make_uint4(v, v, v, v);
+}
+
+__global__ void __launch_bounds__(256, 4) k_draw_dense(const uint4 *__restrict__ blkT,
+                                                       const uint32_t *__restrict__ blkMeta,
+                                                       const uint32_t *__restrict__ blkSym0, int64_t n_blk,
+                                                       uint64_t seed, uint64_t shot0, int64_t ngroups,
+                                                       uint32_t *__restrict__ Bd, int64_t bpitch)
+{
+    __shared__ uint32_t q[8 * FUSED_QCAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * 8 + warp;      // groups 2gw and 2gw+1
+    if (2 * gw >= ngroups) return;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    Shots<1> sc;
-    sc.s[0] = shot_const(shot0 + (uint64_t)g * 32u + (uint64_t)lane, k1);
-    uint32_t *dst = Bd + (size_t)g * (size_t)bpitch * 32u + lane;
-    draw_blocks<1, 2, true>(blkT, blkMeta, 0u, (uint32_t)n_blk, 0u, sc, k0, k1, lane,
-                            [=](uint32_t base, const Cols<1> col) { dst[(size_t)(base / 32u) * 32u] = col.v[0]; });
+    const uint64_t shot_base = shot0 + 64u * (uint64_t)gw;
+    Shots<2> sc;
+#pragma unroll
+    for (int t = 0; t < 2; t++) sc.s[t] = shot_const(shot_base + 32u * t + lane, k1);
+    uint32_t *base = Bd + (size_t)(2 * gw) * (size_t)bpitch * 32u;
+    const bool has2 = 2 * gw + 1 < ngroups;
+    draw_scatter<2>(blkT, blkMeta, blkSym0, 0u, (uint32_t)n_blk, sc, shot_base, k0, k1, lane, q + warp * FUSED_QCAP,
+                    [=](uint32_t sym, int t, uint32_t word) {
+                        if (t == 1 && !has2) return;
+                        const uint32_t e = sym + 1u;
+                        uint32_t *wp = base + ((size_t)t * (size_t)bpitch + e / 32u) * 32u;
+                        const uint32_t bit = 1u << (e & 31u);
+                        while (word) {
+                            const int l = __ffs(word) - 1;
+                            word &= word - 1;
+                            atomicOr(wp + l, bit);
+                        }
+                    });
 }
 
 sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t ngroups, uint32_t *Bd,
                             int64_t bpitch, cudaStream_t s)
 {
     if (ngroups == 0) return SP_OK;
-    k_draw_dense<<<(unsigned)ceil_div(ngroups, 8), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->n_blk, seed, shot0,
-                                                                 ngroups, Bd, bpitch);
+    const int64_t nvec = ngroups * bpitch * 8;
+    k_dense_fill<<<(unsigned)ceil_div(nvec, 256), 256, 0, s>>>(Bd, bpitch, nvec);
+    SP_CUDA(cudaGetLastError());
+    if (P->n_blk == 0) return SP_OK;
+    k_draw_dense<<<(unsigned)ceil_div(ceil_div(ngroups, 2), 8), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->d_blkSym0,
+                                                                            P->n_blk, seed, shot0, ngroups, Bd, bpitch);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -99,6 +99,8 @@ struct sp_program {
     int64_t tc_ntiles[3] = {0, 0, 0};                     // 128-row tiles per record kind
     int64_t tc_nks = 0;                                   // 256-symbol K stages
     int *d_tc_status = nullptr;                           // tensor kernel status word (0 = ok)
+    bool tc_ready = false;                                // d_tc_coef built for the current program
+    double path_probe_ms[5] = {0, 0, 0, 0, 0};            // build-time probe per path (0 = not timed)
     size_t scratch_shots = 0;
     int64_t chunk_shots = 0;
     int path = SP_PATH_SPARSE;
@@ -184,6 +186,7 @@ sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t ns
 int64_t default_chunk(const sp_program *P);
 // dense paths (sp_dense.cu)
 sp_status ensure_dense(sp_program *P, size_t shots, cudaStream_t s);
+sp_status choose_path(sp_program *P, cudaStream_t s);
 bool tensor_path_available(const sp_program *P);
 sp_status dense_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
                       uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import random_clifford_circuit, random_layered, random_small_circuit, repetition_code, surface_code
+from workloads import (mirror_circuit, random_clifford_circuit, random_layered, random_small_circuit,
+                       repetition_code, surface_code)
 
 pytestmark = pytest.mark.gpu
 
@@ -25,6 +26,8 @@ CIRCUITS = {
     "layered120": lambda: random_layered(120, 60, depolarize=0.01, seed=5),
     "rand5": lambda: random_small_circuit(38, 210, seed=905),
     "cliff4": lambda: random_clifford_circuit(14, 240, seed=704),
+    # dense rows (about 40 % of the coefficients set), 3,072 symbols
+    "mirror48": lambda: mirror_circuit(48, 16, p=0.01, seed=2),
 }
 PATHS = {"dense": sp.PATH_DENSE, "tensor": sp.PATH_TENSOR}
 
@@ -84,3 +87,19 @@ def test_tensor_path_chunked_equals_unchunked():
     torch.cuda.synchronize()
     np.testing.assert_array_equal(_u64(m1), _u64(m2))
     assert prog.device_status() == 0
+
+
+def test_path_choice_is_measured_where_rows_are_dense():
+    """Mirror circuits have dense rows: the build times the sparse and both
+    dense forms and keeps the fastest; the surface code (0.3 % dense) is
+    never probed with the dense forms."""
+    dense = sp.build(mirror_circuit(128, 24, p=0.01, seed=3))
+    probe = dense.info["path_probe_ms"]
+    assert dense.info["density"] > 0.2
+    assert probe[sp.PATH_DENSE] > 0 and probe[sp.PATH_TENSOR] > 0
+    chosen = dense.info["path"]
+    # the default (sparse) form is kept unless another is at least 3 % faster
+    assert probe[chosen] > 0 and probe[chosen] <= min(t for t in probe if t > 0) / 0.97 + 1e-9
+    sparse = sp.build(surface_code(11, 11, 1e-3))
+    assert sparse.info["density"] < 0.01
+    assert sparse.info["path_probe_ms"][sp.PATH_DENSE] == 0 and sparse.info["path"] == sp.PATH_FUSED

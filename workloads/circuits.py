@@ -341,6 +341,47 @@ def random_layered(n: int, layers: Optional[int] = None, cnot_pairs: Optional[in
     return c
 
 
+def mirror_circuit(n: int, layers: int, p: float = 0.01, seed: int = 0) -> Circuit:
+    """``layers`` random Clifford layers (H or S or nothing on every qubit,
+    then floor(n/2) random disjoint CX pairs) followed by their inverse in
+    reverse order, DEPOLARIZE1(p) on every qubit after every layer, then
+    every qubit measured, with one detector per measurement (its noiseless
+    value is 0).  Every outcome is deterministic and, once the light cones
+    have spread, depends on faults all through the circuit: the coefficient
+    rows are dense, the regime where the product is a real contraction."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(n)
+    fwd = []
+    for _ in range(layers):
+        choice = rng.integers(0, 3, size=n)
+        h = [q for q in range(n) if choice[q] == 0]
+        s_ = [q for q in range(n) if choice[q] == 1]
+        pairs = [int(x) for x in rng.permutation(n)[: 2 * (n // 2)]]
+        fwd.append((h, s_, pairs))
+        if h:
+            c.append("H", h)
+        if s_:
+            c.append("S", s_)
+        c.append("CX", pairs)
+        if p > 0:
+            c.append("DEPOLARIZE1", list(range(n)), p)
+    for h, s_, pairs in reversed(fwd):
+        # inverse layer: CX pairs (self-inverse), then S^-1 = S^3, then H
+        rev = [x for k in range(len(pairs) // 2 - 1, -1, -1) for x in pairs[2 * k: 2 * k + 2]]
+        c.append("CX", rev)
+        if s_:
+            for _ in range(3):
+                c.append("S", s_)
+        if h:
+            c.append("H", h)
+        if p > 0:
+            c.append("DEPOLARIZE1", list(range(n)), p)
+    c.append("M", list(range(n)))
+    for q in range(n):
+        c.append("DETECTOR", [n - q])
+    return c
+
+
 # ---------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------
