@@ -38,8 +38,8 @@ def _peaks():
         with open(path) as f:
             d = json.load(f)
         return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "sm_max_mhz": d.get("sm_max_mhz", 2070.0),
-                "source": "measured"}
-    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+                "bf16_tflops": d.get("bf16_tflops", 1900.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
 class ClockSampler:
@@ -191,6 +191,69 @@ def _batched_vs_plain(args):
     return res
 
 
+def _dense_paths(args):
+    """A circuit whose coefficient rows are dense (mirror circuit: 512 qubits,
+    16 random Clifford layers then their inverse, DEPOLARIZE1(p) after
+    every layer, every qubit measured with one detector each; about 33k
+    symbols, 1,024 record rows, ~40 % of the coefficients set): the same
+    shots sampled with the product as the tcgen05 tensor-core contraction,
+    the CUDA-core AND/popcount form and the sparse fused kernel, plus the
+    build's own timed choice. The tensor kernel's roofline is its FP8 rate
+    (measured bf16 peak x 2, the nominal FP8:BF16 ratio)."""
+    import torch
+    import paper_2311_03906_gb300 as sp
+    from workloads import mirror_circuit
+    peaks = _peaks()
+    c = mirror_circuit(512, 16, p=args.dense_p, seed=1)
+    t0 = time.perf_counter()
+    prog = sp.build(c)
+    build_s = time.perf_counter() - t0
+    info = prog.info
+    auto = info["path"]
+    shots = args.dense_shots
+    out = prog.alloc_outputs(shots)
+    rows = info["num_measurements"] + info["num_detectors"] + info["num_observables"]
+    flops = 2.0 * rows * (info["num_symbols"] + 1) * shots
+    stream = torch.cuda.current_stream()
+    names = {sp.PATH_TENSOR: "tensor", sp.PATH_DENSE: "dense", sp.PATH_FUSED: "fused", sp.PATH_SPARSE: "staged-sparse"}
+    sparse_path = sp.PATH_FUSED if info["fused_tile_shots"] else sp.PATH_SPARSE
+    res = {}
+    for path in (sp.PATH_TENSOR, sp.PATH_DENSE, sparse_path):
+        prog.set_path(path)
+        prog.sample(shots, seed=1, out=out)
+        torch.cuda.synchronize()
+        prog.profile(True)
+        prog.profile_read()
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(reps):
+            prog.sample(shots, seed=1, shot0=(r + 1) * shots, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        prof = prog.profile_read()
+        prog.profile(False)
+        kern = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in prof.items() if v[1]}
+        res[names[path]] = {"ms": ms, "shots_per_s": shots / (ms / 1e3), "kernels": kern}
+    status = prog.device_status()
+    t = res["tensor"]["kernels"].get("tensor")
+    roof = None
+    if t:
+        achieved = flops / (t["ms_per_step"] / 1e3) / 1e12
+        peak = 2.0 * peaks["bf16_tflops"]
+        roof = {"kernel": "k_tc_product", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"MEASURED_PEAKS.json bf16_tflops x 2 (nominal FP8:BF16 ratio; {peaks['source']})"}
+    prog.close()
+    return {"config": {"workload": f"mirror_circuit(n=512, layers=16, p={args.dense_p:g}, seed=1)", "shots_per_step": shots,
+                       "symbols": info["num_symbols"], "record_rows": rows, "density": info["density"],
+                       "build_s": build_s, "auto_path": names.get(auto, str(auto)),
+                       "build_probe_ms": {names[k]: v for k, v in enumerate(info["path_probe_ms"]) if v > 0 and k in names}},
+            "paths": res, "tensor_roofline": roof, "device_status": status,
+            "algorithmic_flops_per_shot": flops / shots}
+
+
 def run_profile_case():
     """Small case for ncu: build the d=11 program, then sample 65536 shots
     once. The autotuner's timing launches of the fused kernel come first;
@@ -324,7 +387,7 @@ def run_ours(args):
                    "symbols": info["num_symbols"], "channels": info["num_channels"],
                    "measurements": info["num_measurements"], "detectors": info["num_detectors"],
                    "observables": info["num_observables"], "nnz_delta": info["nnz_delta"],
-                   "path": {1: "staged-sparse", 2: "dense", 3: "fused"}.get(info["path"], "?"),
+                   "path": {1: "staged-sparse", 2: "dense", 3: "fused", 4: "tensor"}.get(info["path"], "?"),
                    "fused_tile_shots": info["fused_tile_shots"],
                    "fused_variant": info["fused_variant"],
                    "chunk_shots": info["chunk_shots"],
@@ -342,6 +405,8 @@ def run_ours(args):
     }
     if world == 1 and not args.no_batch:
         line["batched"] = _batched_vs_plain(args)
+    if world == 1 and not args.no_dense:
+        line["dense_rows"] = _dense_paths(args)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(circuit, budget_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -360,6 +425,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-shots", type=int, default=100_000)
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense-row (mirror circuit) section")
+    ap.add_argument("--dense-shots", type=int, default=262_144)
+    ap.add_argument("--dense-p", type=float, default=0.01, help="noise rate of the dense-row workload")
     ap.add_argument("--profile", action="store_true",
                     help="build, then one 65536-shot sample only (the case captured by ncu)")
     args = ap.parse_args()

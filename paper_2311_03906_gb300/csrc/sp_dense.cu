@@ -96,12 +96,14 @@ __global__ void __launch_bounds__(256) k_popc_product(const uint32_t *__restrict
 // Tensor-core product (tcgen05, kind::f8f6f4, E4M3 operands, FP32 in TMEM)
 // ---------------------------------------------------------------------------
 // Tile: M = 128 shots x N = 128 record rows of one record kind, K in stages of
-// TC_KS = 256 symbols.  Operands are K-major with no swizzle, in 8-row x
-// 16-byte core matrices; in a stage buffer the core matrix (row group rg,
-// K group kg) sits at kg * TC_LBO + rg * TC_SBO (16 x 16 core matrices).
-constexpr int TC_M = 128, TC_N = 128, TC_KS = 256, TC_THREADS = 256;
-constexpr uint32_t TC_STAGE_BYTES = TC_M * TC_KS;                  // 32 KB per operand
+// TC_KS = 192 symbols held in a ring of TC_NS stage buffers.  Operands are
+// K-major with no swizzle, in 8-row x 16-byte core matrices; in a stage
+// buffer the core matrix (row group rg, K group kg) sits at
+// kg * TC_LBO + rg * TC_SBO (16 row groups x 12 K groups).
+constexpr int TC_M = 128, TC_N = 128, TC_KS = 192, TC_NS = 4, TC_THREADS = 256;
+constexpr uint32_t TC_STAGE_BYTES = TC_M * TC_KS;                  // 24 KB per operand
 constexpr uint32_t TC_LBO = 16 * 128, TC_SBO = 128;
+constexpr int TC_KG = TC_KS / 16;                                    // K groups per stage
 constexpr uint32_t TC_TMEM_COLS = 128;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;                      // 2 s bound on every wait
 constexpr uint32_t E4M3_ONE = 0x38u;
@@ -237,32 +239,37 @@ __global__ void k_coef_e4m3(const uint32_t *__restrict__ A, int64_t apitch, int6
 
 // Grid: x = tile of 128 shots, y = tile of 128 rows of one record kind.
 // Warp 0 holds the TMEM accumulator (128 lanes = shots x 128 columns =
-// rows).  Per K stage: thread 0 starts the bulk copy of the coefficient
-// block; all threads expand the shots' fault bits into the other operand;
-// thread 0 issues 8 MMAs of K = 32 and commits them to the stage's barrier,
-// which gates the reuse of that buffer two stages later.  The epilogue reads
-// the exact FP32 counts and keeps their parity.  Every wait is bounded; on a
-// timeout the kernel records status 1, drains its own copies and MMAs (again
-// bounded), frees TMEM and returns.
+// rows).  Thread 0 keeps the coefficient blocks of the next two stages in
+// flight (bulk copies on the stages' full barriers); per stage all threads
+// expand the shots' fault bits (loaded one stage ahead into registers) into
+// the stage's other operand, then thread 0 issues TC_KS/32 MMAs of K = 32,
+// commits them to the stage's done barrier, waits for the MMAs of two
+// stages back and reuses their buffer for the next prefetch, so two stages
+// of MMAs stay queued.  An operand buffer is rewritten only after its MMAs
+// completed: thread 0 saw that at least one CTA barrier earlier.  The
+// epilogue reads the exact FP32 counts and keeps their parity.  Every wait
+// is bounded; on a timeout the kernel records status 1, drains its own
+// copies and MMAs (again bounded), frees TMEM and returns.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_product(const uint32_t *__restrict__ Bd, int64_t bpitch, int64_t ngroups, const uint4 *__restrict__ coef,
                  int64_t nks, int64_t words32, uint64_t nshots, uint32_t *__restrict__ out, int *status)
 {
+    static_assert(TC_NS == 4, "two stages in flight, two being prefetched");
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint8_t *Abuf = sm;                                  // 2 stage buffers
-    uint8_t *Bbuf = sm + 2 * TC_STAGE_BYTES;             // 2 stage buffers
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 4 * TC_STAGE_BYTES);   // full[2], done[2]
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 4);
+    uint8_t *Abuf = sm;                                        // TC_NS stage buffers
+    uint8_t *Bbuf = sm + TC_NS * TC_STAGE_BYTES;               // TC_NS stage buffers
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * TC_NS * TC_STAGE_BYTES);   // full[NS], done[NS]
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * TC_NS);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t m0 = (int64_t)blockIdx.x * TC_M;
     const int64_t nt = blockIdx.y;
-    const uint32_t full = smem_u32(&bars[0]), done = smem_u32(&bars[2]);
+    const uint32_t full = smem_u32(&bars[0]), done = smem_u32(&bars[TC_NS]);
     if (tid == 0) {
-        mbar_init(full, 1);
-        mbar_init(full + 8, 1);
-        mbar_init(done, 1);
-        mbar_init(done + 8, 1);
+        for (int i = 0; i < TC_NS; i++) {
+            mbar_init(full + 8 * i, 1);
+            mbar_init(done + 8 * i, 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -276,9 +283,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
     const uint4 *cblk = coef + (size_t)nt * (size_t)nks * (TC_STAGE_BYTES / 16);
-    // this thread expands shot m of the tile, K groups kgb .. kgb+7 of each stage
+    // this thread expands shot m of the tile, K groups kgb .. kgb+TC_KG/2-1 of each stage
     const int m = tid & (TC_M - 1);
-    const uint32_t kgb = (uint32_t)(tid >> 7) * 8u;
+    const uint32_t kgb = (uint32_t)(tid >> 7) * (TC_KG / 2);
     const int64_t g = (m0 + m) / 32;
     const bool mvalid = g < ngroups;
     const uint32_t *bsrc = Bd + (size_t)(mvalid ? g : 0) * (size_t)bpitch * 32u + (m & 31);
@@ -286,34 +293,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // Every decision to stop or to read TMEM is made CTA-wide by
     // __syncthreads_or, so warp-collective tcgen05 instructions never run in
     // part of a warp.
-    bool failed = false;    // this thread saw a bounded wait run out
-    int64_t issued = 0;     // stages whose MMAs thread 0 committed
-    int64_t copy_ks = -1;   // stage of a bulk copy thread 0 issued and has not seen land
-    for (int64_t ks = 0; ks < nks; ks++) {
-        const int b = (int)(ks & 1);
-        if (ks >= 2 && !mbar_wait(done + 8 * b, (uint32_t)(((ks >> 1) - 1) & 1))) failed = true;
-        if (tid == 0 && !failed) {
-            mbar_expect_tx(full + 8 * b, TC_STAGE_BYTES);
-            bulk_g2s(smem_u32(Bbuf + b * TC_STAGE_BYTES), cblk + (size_t)ks * (TC_STAGE_BYTES / 16), TC_STAGE_BYTES,
-                     full + 8 * b);
-            copy_ks = ks;
-        }
-        uint8_t *Ab = Abuf + b * TC_STAGE_BYTES;
+    bool failed = false;     // this thread saw a bounded wait run out
+    int64_t issued = 0;      // stages whose MMAs thread 0 committed
+    int64_t copied = 0;      // stages whose coefficient copy thread 0 started
+    int64_t landed = 0;      // stages whose coefficient copy thread 0 saw land
+    auto prefetch = [&](int64_t j) {
+        const int jb = (int)(j % TC_NS);
+        mbar_expect_tx(full + 8 * jb, TC_STAGE_BYTES);
+        bulk_g2s(smem_u32(Bbuf + jb * TC_STAGE_BYTES), cblk + (size_t)j * (TC_STAGE_BYTES / 16), TC_STAGE_BYTES,
+                 full + 8 * jb);
+        copied = j + 1;
+    };
+    if (tid == 0)
+        for (int64_t j = 0; j < 2 && j < nks; j++) prefetch(j);
+    constexpr int NW = TC_KG / 4;   // fault-bit words this thread expands per stage
+    uint32_t vn[NW];
+    auto load_words = [&](int64_t ks) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < NW; j++) {
             const int64_t w = ks * (TC_KS / 32) + (kgb >> 1) + j;
-            const uint32_t v = (mvalid && w < bpitch) ? bsrc[(size_t)w * 32u] : 0u;
+            vn[j] = (mvalid && w < bpitch) ? bsrc[(size_t)w * 32u] : 0u;
+        }
+    };
+    load_words(0);
+    for (int64_t ks = 0; ks < nks; ks++) {
+        const int b = (int)(ks % TC_NS);
+        uint8_t *Ab = Abuf + b * TC_STAGE_BYTES;
+        uint32_t v[NW];
+#pragma unroll
+        for (int j = 0; j < NW; j++) v[j] = vn[j];
+        if (ks + 1 < nks) load_words(ks + 1);
+#pragma unroll
+        for (int j = 0; j < NW; j++) {
             const uint32_t kg = kgb + 2u * (uint32_t)j;
-            *reinterpret_cast<uint4 *>(Ab + kg * TC_LBO + a_off) = bits16_to_e4m3(v & 0xFFFFu);
-            *reinterpret_cast<uint4 *>(Ab + (kg + 1u) * TC_LBO + a_off) = bits16_to_e4m3(v >> 16);
+            *reinterpret_cast<uint4 *>(Ab + kg * TC_LBO + a_off) = bits16_to_e4m3(v[j] & 0xFFFFu);
+            *reinterpret_cast<uint4 *>(Ab + (kg + 1u) * TC_LBO + a_off) = bits16_to_e4m3(v[j] >> 16);
         }
         fence_proxy_async_smem();
         if (__syncthreads_or(failed)) break;
         if (tid == 0) {
-            if (!mbar_wait(full + 8 * b, (uint32_t)((ks >> 1) & 1))) {
+            if (!mbar_wait(full + 8 * b, (uint32_t)((ks / TC_NS) & 1))) {
                 failed = true;
             } else {
-                copy_ks = -1;
+                landed = ks + 1;
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(Ab), b0 = smem_u32(Bbuf + b * TC_STAGE_BYTES);
 #pragma unroll
@@ -322,6 +344,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                            smem_desc(b0 + (uint32_t)s * 2u * TC_LBO, TC_LBO, TC_SBO), (ks > 0 || s > 0) ? 1u : 0u);
                 tc_commit(done + 8 * b);
                 issued = ks + 1;
+                // the MMAs of two stages back free their buffers for the next prefetch
+                if (ks >= 2 && !mbar_wait(done + 8 * (int)((ks - 2) % TC_NS), (uint32_t)(((ks - 2) / TC_NS) & 1)))
+                    failed = true;
+                else if (ks + 2 < nks)
+                    prefetch(ks + 2);
             }
         }
     }
@@ -329,9 +356,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // the last committed stage covers every MMA before it
         if (issued > 0) {
             const int64_t last = issued - 1;
-            if (!mbar_wait(done + 8 * (int)(last & 1), (uint32_t)((last >> 1) & 1))) failed = true;
+            if (!mbar_wait(done + 8 * (int)(last % TC_NS), (uint32_t)((last / TC_NS) & 1))) failed = true;
         }
-        if (copy_ks >= 0 && !mbar_wait(full + 8 * (int)(copy_ks & 1), (uint32_t)((copy_ks >> 1) & 1))) failed = true;
+        for (int64_t j = landed; j < copied; j++)
+            if (!mbar_wait(full + 8 * (int)(j % TC_NS), (uint32_t)((j / TC_NS) & 1))) failed = true;
         if (issued != nks) failed = true;
     }
     const bool all_ok = !__syncthreads_or(failed);
@@ -359,9 +387,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
-// 4 stage buffers + barriers + alignment, and 32 KB of slack so that every
-// address an operand descriptor can reach stays inside the allocation.
-constexpr size_t TC_SMEM = 5 * (size_t)TC_STAGE_BYTES + 1024 + 64;
+// TC_NS stage buffers per operand, alignment, barriers and the TMEM address.
+constexpr size_t TC_SMEM = 2 * TC_NS * (size_t)TC_STAGE_BYTES + 1024 + 16 * TC_NS + 16;
 
 }  // namespace
 
