@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) k_popc_product(const uint32_t *__restrict
 // K-major with no swizzle, in 8-row x 16-byte core matrices; in a stage
 // buffer the core matrix (row group rg, K group kg) sits at
 // kg * TC_LBO + rg * TC_SBO (16 row groups x 12 K groups).
-constexpr int TC_M = 128, TC_N = 128, TC_KS = 192, TC_NS = 4, TC_THREADS = 256;
+constexpr int TC_M = 128, TC_N = 128, TC_KS = 192, TC_NS = 4;
+constexpr int TC_EXPANDERS = 256, TC_THREADS = TC_EXPANDERS + 32;   // 8 expander warps + 1 issuer warp
 constexpr uint32_t TC_STAGE_BYTES = TC_M * TC_KS;                  // 24 KB per operand
 constexpr uint32_t TC_LBO = 16 * 128, TC_SBO = 128;
 constexpr int TC_KG = TC_KS / 16;                                    // K groups per stage
@@ -144,6 +145,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     while (!mbar_try_wait(bar, parity))
         if (global_ns() - t0 > TC_WAIT_NS) return false;
     return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
@@ -238,41 +244,45 @@ __global__ void k_coef_e4m3(const uint32_t *__restrict__ A, int64_t apitch, int6
 }
 
 // Grid: x = tile of 128 shots, y = tile of 128 rows of one record kind.
-// Warp 0 holds the TMEM accumulator (128 lanes = shots x 128 columns =
-// rows).  Thread 0 keeps the coefficient blocks of the next two stages in
-// flight (bulk copies on the stages' full barriers); per stage all threads
-// expand the shots' fault bits (loaded one stage ahead into registers) into
-// the stage's other operand, then thread 0 issues TC_KS/32 MMAs of K = 32,
-// commits them to the stage's done barrier, waits for the MMAs of two
-// stages back and reuses their buffer for the next prefetch, so two stages
-// of MMAs stay queued.  An operand buffer is rewritten only after its MMAs
-// completed: thread 0 saw that at least one CTA barrier earlier.  The
-// epilogue reads the exact FP32 counts and keeps their parity.  Every wait
-// is bounded; on a timeout the kernel records status 1, drains its own
-// copies and MMAs (again bounded), frees TMEM and returns.
+// Warp specialised, synchronised by per-stage mbarriers instead of CTA
+// barriers: warps 0-7 (expanders) turn the shots' fault bits, loaded one
+// stage ahead into registers, into the E4M3 operand of each stage and
+// arrive on its afull barrier; lane 0 of warp 8 (issuer) keeps the
+// coefficient blocks of the next TC_NS-1 stages in flight (bulk copies on
+// the full barriers), waits for both operands of a stage, issues TC_KS/32
+// MMAs of K = 32 into the TMEM accumulator (128 lanes = shots x 128
+// columns = rows, held by warp 8) and commits them to the stage's done
+// barrier, which frees the stage's buffers.  The epilogue (warps 0-7) reads
+// the exact FP32 counts and keeps their parity.  Every wait is bounded; a
+// timeout raises the CTA's abort flag, every loop stops at its next check,
+// the issuer drains its own copies and MMAs (again bounded), status 1 is
+// recorded and TMEM is freed.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_product(const uint32_t *__restrict__ Bd, int64_t bpitch, int64_t ngroups, const uint4 *__restrict__ coef,
                  int64_t nks, int64_t words32, uint64_t nshots, uint32_t *__restrict__ out, int *status)
 {
-    static_assert(TC_NS == 4, "two stages in flight, two being prefetched");
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t *Abuf = sm;                                        // TC_NS stage buffers
     uint8_t *Bbuf = sm + TC_NS * TC_STAGE_BYTES;               // TC_NS stage buffers
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * TC_NS * TC_STAGE_BYTES);   // full[NS], done[NS]
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * TC_NS);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * TC_NS * TC_STAGE_BYTES);   // full, afull, done [NS]
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 3 * TC_NS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool issuer_warp = warp == TC_EXPANDERS / 32;
     const int64_t m0 = (int64_t)blockIdx.x * TC_M;
     const int64_t nt = blockIdx.y;
-    const uint32_t full = smem_u32(&bars[0]), done = smem_u32(&bars[TC_NS]);
+    const uint32_t full = smem_u32(&bars[0]), afull = smem_u32(&bars[TC_NS]), done = smem_u32(&bars[2 * TC_NS]);
     if (tid == 0) {
         for (int i = 0; i < TC_NS; i++) {
             mbar_init(full + 8 * i, 1);
+            mbar_init(afull + 8 * i, TC_EXPANDERS);
             mbar_init(done + 8 * i, 1);
         }
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (issuer_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
                      "r"(TC_TMEM_COLS)
                      : "memory");
@@ -282,78 +292,91 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
-    const uint4 *cblk = coef + (size_t)nt * (size_t)nks * (TC_STAGE_BYTES / 16);
-    // this thread expands shot m of the tile, K groups kgb .. kgb+TC_KG/2-1 of each stage
-    const int m = tid & (TC_M - 1);
-    const uint32_t kgb = (uint32_t)(tid >> 7) * (TC_KG / 2);
-    const int64_t g = (m0 + m) / 32;
-    const bool mvalid = g < ngroups;
-    const uint32_t *bsrc = Bd + (size_t)(mvalid ? g : 0) * (size_t)bpitch * 32u + (m & 31);
-    const uint32_t a_off = (uint32_t)(m >> 3) * TC_SBO + (uint32_t)(m & 7) * 16u;
-    // Every decision to stop or to read TMEM is made CTA-wide by
-    // __syncthreads_or, so warp-collective tcgen05 instructions never run in
-    // part of a warp.
-    bool failed = false;     // this thread saw a bounded wait run out
-    int64_t issued = 0;      // stages whose MMAs thread 0 committed
-    int64_t copied = 0;      // stages whose coefficient copy thread 0 started
-    int64_t landed = 0;      // stages whose coefficient copy thread 0 saw land
-    auto prefetch = [&](int64_t j) {
-        const int jb = (int)(j % TC_NS);
-        mbar_expect_tx(full + 8 * jb, TC_STAGE_BYTES);
-        bulk_g2s(smem_u32(Bbuf + jb * TC_STAGE_BYTES), cblk + (size_t)j * (TC_STAGE_BYTES / 16), TC_STAGE_BYTES,
-                 full + 8 * jb);
-        copied = j + 1;
-    };
-    if (tid == 0)
-        for (int64_t j = 0; j < 2 && j < nks; j++) prefetch(j);
-    constexpr int NW = TC_KG / 4;   // fault-bit words this thread expands per stage
-    uint32_t vn[NW];
-    auto load_words = [&](int64_t ks) {
+    bool failed = false;
+    int64_t issued = 0, copied = 0, landed = 0;   // issuer's progress
+    if (!issuer_warp) {
+        // ---- expanders: shot m of the tile, K groups kgb .. kgb+TC_KG/2-1 of each stage
+        const int m = tid & (TC_M - 1);
+        const uint32_t kgb = (uint32_t)(tid >> 7) * (TC_KG / 2);
+        const int64_t g = (m0 + m) / 32;
+        const bool mvalid = g < ngroups;
+        const uint32_t *bsrc = Bd + (size_t)(mvalid ? g : 0) * (size_t)bpitch * 32u + (m & 31);
+        const uint32_t a_off = (uint32_t)(m >> 3) * TC_SBO + (uint32_t)(m & 7) * 16u;
+        constexpr int NW = TC_KG / 4;   // fault-bit words this thread expands per stage
+        uint32_t vn[NW];
+        auto load_words = [&](int64_t ks) {
 #pragma unroll
-        for (int j = 0; j < NW; j++) {
-            const int64_t w = ks * (TC_KS / 32) + (kgb >> 1) + j;
-            vn[j] = (mvalid && w < bpitch) ? bsrc[(size_t)w * 32u] : 0u;
-        }
-    };
-    load_words(0);
-    for (int64_t ks = 0; ks < nks; ks++) {
-        const int b = (int)(ks % TC_NS);
-        uint8_t *Ab = Abuf + b * TC_STAGE_BYTES;
-        uint32_t v[NW];
-#pragma unroll
-        for (int j = 0; j < NW; j++) v[j] = vn[j];
-        if (ks + 1 < nks) load_words(ks + 1);
-#pragma unroll
-        for (int j = 0; j < NW; j++) {
-            const uint32_t kg = kgb + 2u * (uint32_t)j;
-            *reinterpret_cast<uint4 *>(Ab + kg * TC_LBO + a_off) = bits16_to_e4m3(v[j] & 0xFFFFu);
-            *reinterpret_cast<uint4 *>(Ab + (kg + 1u) * TC_LBO + a_off) = bits16_to_e4m3(v[j] >> 16);
-        }
-        fence_proxy_async_smem();
-        if (__syncthreads_or(failed)) break;
-        if (tid == 0) {
-            if (!mbar_wait(full + 8 * b, (uint32_t)((ks / TC_NS) & 1))) {
+            for (int j = 0; j < NW; j++) {
+                const int64_t w = ks * (TC_KS / 32) + (kgb >> 1) + j;
+                vn[j] = (mvalid && w < bpitch) ? bsrc[(size_t)w * 32u] : 0u;
+            }
+        };
+        load_words(0);
+        for (int64_t ks = 0; ks < nks; ks++) {
+            if (*abort_flag) break;
+            const int b = (int)(ks % TC_NS);
+            // the MMAs of stage ks - TC_NS read this buffer last
+            if (ks >= TC_NS && !mbar_wait(done + 8 * b, (uint32_t)(((ks / TC_NS) - 1) & 1))) {
                 failed = true;
-            } else {
-                landed = ks + 1;
-                tc_fence_after();
-                const uint32_t a0 = smem_u32(Ab), b0 = smem_u32(Bbuf + b * TC_STAGE_BYTES);
+                *abort_flag = 1;
+                break;
+            }
+            uint32_t v[NW];
 #pragma unroll
-                for (int s = 0; s < TC_KS / 32; s++)
-                    tc_mma(tmem, smem_desc(a0 + (uint32_t)s * 2u * TC_LBO, TC_LBO, TC_SBO),
-                           smem_desc(b0 + (uint32_t)s * 2u * TC_LBO, TC_LBO, TC_SBO), (ks > 0 || s > 0) ? 1u : 0u);
-                tc_commit(done + 8 * b);
-                issued = ks + 1;
-                // the MMAs of two stages back free their buffers for the next prefetch
-                if (ks >= 2 && !mbar_wait(done + 8 * (int)((ks - 2) % TC_NS), (uint32_t)(((ks - 2) / TC_NS) & 1)))
+            for (int j = 0; j < NW; j++) v[j] = vn[j];
+            if (ks + 1 < nks) load_words(ks + 1);
+            uint8_t *Ab = Abuf + b * TC_STAGE_BYTES;
+#pragma unroll
+            for (int j = 0; j < NW; j++) {
+                const uint32_t kg = kgb + 2u * (uint32_t)j;
+                *reinterpret_cast<uint4 *>(Ab + kg * TC_LBO + a_off) = bits16_to_e4m3(v[j] & 0xFFFFu);
+                *reinterpret_cast<uint4 *>(Ab + (kg + 1u) * TC_LBO + a_off) = bits16_to_e4m3(v[j] >> 16);
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(afull + 8 * b);
+        }
+    } else if (lane == 0) {
+        // ---- issuer
+        const uint4 *cblk = coef + (size_t)nt * (size_t)nks * (TC_STAGE_BYTES / 16);
+        auto prefetch = [&](int64_t j) {
+            const int jb = (int)(j % TC_NS);
+            mbar_expect_tx(full + 8 * jb, TC_STAGE_BYTES);
+            bulk_g2s(smem_u32(Bbuf + jb * TC_STAGE_BYTES), cblk + (size_t)j * (TC_STAGE_BYTES / 16), TC_STAGE_BYTES,
+                     full + 8 * jb);
+            copied = j + 1;
+        };
+        for (int64_t j = 0; j < TC_NS - 1 && j < nks; j++) prefetch(j);
+        for (int64_t ks = 0; ks < nks; ks++) {
+            if (*abort_flag) break;
+            const int b = (int)(ks % TC_NS);
+            const uint32_t par = (uint32_t)((ks / TC_NS) & 1);
+            if (!mbar_wait(afull + 8 * b, par) || !mbar_wait(full + 8 * b, par)) {
+                failed = true;
+                *abort_flag = 1;
+                break;
+            }
+            landed = ks + 1;
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(Abuf + b * TC_STAGE_BYTES), b0 = smem_u32(Bbuf + b * TC_STAGE_BYTES);
+#pragma unroll
+            for (int s = 0; s < TC_KS / 32; s++)
+                tc_mma(tmem, smem_desc(a0 + (uint32_t)s * 2u * TC_LBO, TC_LBO, TC_SBO),
+                       smem_desc(b0 + (uint32_t)s * 2u * TC_LBO, TC_LBO, TC_SBO), (ks > 0 || s > 0) ? 1u : 0u);
+            tc_commit(done + 8 * b);
+            issued = ks + 1;
+            // stage ks + TC_NS - 1 reuses the buffers of stage ks - 1 once its MMAs are done;
+            // the MMAs of stage ks keep the tensor pipe busy meanwhile
+            const int64_t j = ks + TC_NS - 1;
+            if (j < nks) {
+                if (ks >= 1 && !mbar_wait(done + 8 * (int)((ks - 1) % TC_NS), (uint32_t)(((ks - 1) / TC_NS) & 1))) {
                     failed = true;
-                else if (ks + 2 < nks)
-                    prefetch(ks + 2);
+                    *abort_flag = 1;
+                    break;
+                }
+                prefetch(j);
             }
         }
-    }
-    if (tid == 0) {
-        // the last committed stage covers every MMA before it
+        // drain: the last committed stage covers every MMA before it
         if (issued > 0) {
             const int64_t last = issued - 1;
             if (!mbar_wait(done + 8 * (int)(last % TC_NS), (uint32_t)((last / TC_NS) & 1))) failed = true;
@@ -362,8 +385,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!mbar_wait(full + 8 * (int)(j % TC_NS), (uint32_t)((j / TC_NS) & 1))) failed = true;
         if (issued != nks) failed = true;
     }
-    const bool all_ok = !__syncthreads_or(failed);
-    if (all_ok) {
+    const bool all_ok = !__syncthreads_or(failed || *abort_flag);
+    if (all_ok && !issuer_warp) {
         tc_fence_after();
         const int qw = warp & 3, half = warp >> 2;
         const uint32_t taddr = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(64 * half);
@@ -378,17 +401,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int64_t q = nt * (TC_N / 32) + half * 2 + c;
             if (shot < nshots && q < words32) out[shot * (uint64_t)words32 + (uint64_t)q] = word;
         }
-    } else if (tid == 0) {
+    } else if (!all_ok && tid == 0) {
         atomicExch(status, 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    if (issuer_warp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
 }
 
 // TC_NS stage buffers per operand, alignment, barriers and the TMEM address.
-constexpr size_t TC_SMEM = 2 * TC_NS * (size_t)TC_STAGE_BYTES + 1024 + 16 * TC_NS + 16;
+constexpr size_t TC_SMEM = 2 * TC_NS * (size_t)TC_STAGE_BYTES + 1024 + 24 * TC_NS + 16;
 
 }  // namespace
 
