@@ -254,6 +254,35 @@ def _dense_paths(args):
             "algorithmic_flops_per_shot": flops / shots}
 
 
+def _build_times(args):
+    """Time to initialize a sampler (the paper's second measure, Sec. 5): sp_build
+    (GPU traversal, replay, detector rows, sampler program, autotuner) against
+    the oracle's build on the random layered circuits of Fig. 3c (n qubits x n
+    layers, floor(n/2) CX pairs and DEPOLARIZE1(0.01) on every qubit per layer,
+    5% of the qubits measured per layer, all measured at the end). The oracle
+    is timed only up to n = 300 (its cost grows about as n^4)."""
+    import paper_2311_03906_gb300 as sp
+    import oracle
+    from workloads import random_layered
+    out = []
+    for n in args.build_sizes:
+        c = random_layered(n, n, depolarize=0.01, seed=1)
+        t0 = time.perf_counter()
+        prog = sp.build(c)
+        gpu_s = time.perf_counter() - t0
+        row = {"n": n, "ops": len(c.ops), "symbols": prog.info["num_symbols"],
+               "measurements": prog.info["num_measurements"], "gpu_build_s": gpu_s,
+               "gpu_build_ms_library": prog.info["build_ms"]}
+        prog.close()
+        if n <= 300:
+            t0 = time.perf_counter()
+            oracle.Program(c)
+            row["oracle_build_s"] = time.perf_counter() - t0
+            row["oracle_over_gpu"] = row["oracle_build_s"] / gpu_s
+        out.append(row)
+    return {"workload": "random_layered(n, n, depolarize=0.01, seed=1)", "rows": out}
+
+
 def run_profile_case():
     """Small case for ncu: build the d=11 program, then sample 65536 shots
     once. The autotuner's timing launches of the fused kernel come first;
@@ -407,6 +436,8 @@ def run_ours(args):
         line["batched"] = _batched_vs_plain(args)
     if world == 1 and not args.no_dense:
         line["dense_rows"] = _dense_paths(args)
+    if world == 1 and not args.no_build_times:
+        line["build_times"] = _build_times(args)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(circuit, budget_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -428,6 +459,8 @@ def main():
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-row (mirror circuit) section")
     ap.add_argument("--dense-shots", type=int, default=262_144)
     ap.add_argument("--dense-p", type=float, default=0.01, help="noise rate of the dense-row workload")
+    ap.add_argument("--no-build-times", action="store_true", help="skip the sampler-initialization timings")
+    ap.add_argument("--build-sizes", type=int, nargs="*", default=[100, 200, 300, 500])
     ap.add_argument("--profile", action="store_true",
                     help="build, then one 65536-shot sample only (the case captured by ncu)")
     args = ap.parse_args()
