@@ -25,7 +25,8 @@ _lib = None
 # op names -> the oracle's own op codes (the order of its enum)
 _CODES = {"H": 0, "S": 1, "CX": 2, "X": 3, "Y": 4, "Z": 5, "M": 6, "MR": 7, "R": 8,
           "X_ERROR": 9, "Y_ERROR": 10, "Z_ERROR": 11, "DEPOLARIZE1": 12,
-          "DEPOLARIZE2": 13, "DETECTOR": 14, "OBSERVABLE_INCLUDE": 15, "TICK": 16}
+          "DEPOLARIZE2": 13, "DETECTOR": 14, "OBSERVABLE_INCLUDE": 15, "TICK": 16,
+          "X_IF": 17, "Y_IF": 18, "Z_IF": 19}
 CH_TYPES = ("X_ERROR", "Y_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2", "RANDOM")
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported op", 3: "nondeterministic detector",
           4: "out of memory"}

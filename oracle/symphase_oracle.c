@@ -23,6 +23,10 @@
  *   - R / MR: measure, then the conditional Pauli X^e (e = the outcome's
  *     expression) on the measured qubit (the conditional-Pauli idea of the
  *     conclusion), applied to every row like Fact 1 does;
+ *   - feed-forward X_IF / Y_IF / Z_IF (k, q): the Pauli on qubit q applied
+ *     when record rec[-k] is 1, i.e. the conditional Pauli P^e with e that
+ *     record's expression (Sec. 6): every row anticommuting with P gets e
+ *     added to its phase;
  *   - symbols are numbered in op order: a fault's symbols when it is reached
  *     (X/Y/Z_ERROR 1, DEPOLARIZE1 2 = x,z, DEPOLARIZE2 4 = x_a,z_a,x_b,z_b),
  *     a random measurement's symbol at that measurement;
@@ -44,7 +48,8 @@
 
 enum {
     OR_H = 0, OR_S, OR_CX, OR_X, OR_Y, OR_Z, OR_M, OR_MR, OR_R,
-    OR_XERR, OR_YERR, OR_ZERR, OR_DEP1, OR_DEP2, OR_DET, OR_OBS, OR_TICK
+    OR_XERR, OR_YERR, OR_ZERR, OR_DEP1, OR_DEP2, OR_DET, OR_OBS, OR_TICK,
+    OR_XIF, OR_YIF, OR_ZIF   /* feed-forward: targets are (look-back k, qubit) pairs */
 };
 enum { CH_XERR = 0, CH_YERR, CH_ZERR, CH_DEP1, CH_DEP2, CH_RANDOM };
 enum {
@@ -245,11 +250,14 @@ static void measure(orc_prog *P, int64_t a, uint64_t *out)
     }
 }
 
-/* conditional X^e on qubit a (reset) */
-static void cond_x(orc_prog *P, int64_t a, const uint64_t *e)
+/* The Pauli X^xb Z^zb on qubit a applied when the affine form e is 1
+ * (Sec. 6, conditional Paulis): every row that anticommutes with it, i.e.
+ * with xb*z_a + zb*x_a odd, gets e added to its phase.  A reset is the
+ * conditional X^e with e the outcome just measured. */
+static void cond_pauli(orc_prog *P, int64_t a, int xb, int zb, const uint64_t *e)
 {
     for (int64_t r = 0; r < 2 * P->n; r++) {
-        if (Z(P, r)[a]) {
+        if ((xb && Z(P, r)[a]) ^ (zb && X(P, r)[a])) {
             uint64_t *ph = PH(P, r);
             for (int64_t w = 0; w < P->pw; w++) ph[w] ^= e[w];
         }
@@ -323,10 +331,14 @@ orc_prog *or_build(int64_t nq, int64_t nops, const int32_t *code, const int64_t 
         int c = code[i];
         for (int64_t j = 0; j < k; j++) {
             if (c == OR_DET || c == OR_OBS || c == OR_TICK) break;
+            if ((c == OR_XIF || c == OR_YIF || c == OR_ZIF) && !(j & 1)) continue;   /* look-backs */
             if (t[j] < 0 || t[j] >= nq) { P->status = OR_ERR_ARG; break; }
         }
         if (P->status) break;
-        if ((c == OR_CX || c == OR_DEP2) && (k % 2)) { P->status = OR_ERR_ARG; break; }
+        if ((c == OR_CX || c == OR_DEP2 || c == OR_XIF || c == OR_YIF || c == OR_ZIF) && (k % 2)) {
+            P->status = OR_ERR_ARG;
+            break;
+        }
         if (c >= OR_XERR && c <= OR_DEP2 && !(arg[i] >= 0.0 && arg[i] <= 1.0)) { P->status = OR_ERR_ARG; break; }
         switch (c) {
         case OR_H: for (int64_t j = 0; j < k; j++) gate_h(P, t[j]); break;
@@ -375,7 +387,7 @@ orc_prog *or_build(int64_t nq, int64_t nops, const int32_t *code, const int64_t 
                     memcpy(P->meas + P->nmeas * P->pw, e, (size_t)P->pw * 8);
                     P->nmeas++;
                 }
-                if (c != OR_M) cond_x(P, t[j], e);
+                if (c != OR_M) cond_pauli(P, t[j], 1, 0, e);
             }
             break;
         case OR_DET: case OR_OBS: {
@@ -395,6 +407,13 @@ orc_prog *or_build(int64_t nq, int64_t nops, const int32_t *code, const int64_t 
             }
             break;
         }
+        case OR_XIF: case OR_YIF: case OR_ZIF:
+            for (int64_t j = 0; j < k; j += 2) {
+                int64_t lb = t[j];
+                if (lb < 1 || lb > P->nmeas) { P->status = OR_ERR_ARG; break; }
+                cond_pauli(P, t[j + 1], c != OR_ZIF, c != OR_XIF, P->meas + (P->nmeas - lb) * P->pw);
+            }
+            break;
         case OR_TICK: break;
         default: P->status = OR_ERR_OP; break;
         }

@@ -140,6 +140,10 @@ def simulate(circuit, bits) -> tuple:
                     meas.append(m)
                 if name != "M" and m:
                     st.pauli(a, True, False)
+        elif name in ("X_IF", "Y_IF", "Z_IF"):
+            for k, a in zip(t[::2], t[1::2]):
+                if meas[-k]:
+                    st.pauli(a, name[0] in "XY", name[0] in "YZ")
         elif name == "DETECTOR":
             det.append(int(np.bitwise_xor.reduce([meas[-k] for k in t])) if t else 0)
         elif name == "OBSERVABLE_INCLUDE":

@@ -85,6 +85,10 @@ def distribution(circuit, fault_bits) -> dict:
                         branches = each(lambda p, q=q: _apply1(p, n, q, _Z))
                     if vx:
                         branches = each(lambda p, q=q: _apply1(p, n, q, _X))
+        elif name in ("X_IF", "Y_IF", "Z_IF"):
+            U = {"X_IF": _X, "Y_IF": _Y, "Z_IF": _Z}[name]
+            for lb, a in zip(t[::2], t[1::2]):
+                branches = [(_apply1(p, n, a, U) if rec[-lb] else p, pr, rec) for p, pr, rec in branches]
         elif name in ("M", "MR", "R"):
             for a in t:
                 nb = []

@@ -8,7 +8,8 @@ import pytest
 
 import oracle
 from checkers import chp
-from workloads import random_clifford_circuit, random_small_circuit, repetition_code, surface_code
+from workloads import (random_clifford_circuit, random_feedforward_circuit, random_small_circuit, repetition_code,
+                       surface_code)
 
 
 def _check(circuit, nassign, seed, density):
@@ -38,6 +39,16 @@ def test_clifford_heavy_circuits(seed):
     then depend on Y phases and on long products of stabilizer rows."""
     rng = np.random.default_rng(2000 + seed)
     circuit = random_clifford_circuit(int(rng.integers(2, 9)), int(rng.integers(20, 90)), seed=3000 + seed)
+    _check(circuit, 4, seed, density=0.5)
+
+
+@pytest.mark.parametrize("seed", range(32))
+def test_feedforward_circuits(seed):
+    """X_IF / Y_IF / Z_IF conditioned on earlier records (Sec. 6's
+    conditional Paulis): the concrete run applies the Pauli when the record
+    it reads is 1."""
+    rng = np.random.default_rng(4000 + seed)
+    circuit = random_feedforward_circuit(int(rng.integers(2, 12)), int(rng.integers(20, 90)), seed=5000 + seed)
     _check(circuit, 4, seed, density=0.5)
 
 

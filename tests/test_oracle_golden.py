@@ -49,3 +49,31 @@ def test_random_measurement_only_new_row_gets_symbol():
     prog = oracle.Program(circuit)
     m2 = prog.row_bits("meas")[1]
     assert m2[3] == 1 and m2[1] == 1 and m2[2] == 1
+
+
+@pytest.mark.parametrize("basis", ["Z", "X"])
+def test_teleportation_with_feedforward_is_deterministic(basis):
+    """Teleporting |1> (or |->) from qubit 0 to qubit 2 with the textbook
+    corrections X_IF (from qubit 1's outcome) and Z_IF (from qubit 0's) makes
+    the final record the constant 1: no random symbol survives in it,
+    although both Bell-measurement outcomes are random."""
+    from workloads import Circuit
+    c = Circuit(3)
+    c.append("X", [0])
+    if basis == "X":
+        c.append("H", [0])
+    c.append("H", [1]); c.append("CX", [1, 2])        # Bell pair (1, 2)
+    c.append("CX", [0, 1]); c.append("H", [0])        # Bell measurement of (0, 1)
+    c.append("M", [0, 1])
+    c.append("X_IF", [1, 2]); c.append("Z_IF", [2, 2])
+    if basis == "X":
+        c.append("H", [2])
+    c.append("M", [2])
+    prog = oracle.Program(c)
+    rnd = prog.random_symbols()
+    rows = prog.row_bits("meas")
+    assert rnd.sum() == 2 and rows[0][1:].any() and rows[1][1:].any()   # Bell outcomes random
+    assert rows[2][0] == 1 and not rows[2][1:].any()                   # teleported record = 1
+    # without the corrections the record depends on the random outcomes
+    c2 = Circuit(3, [op for op in c.ops if op.name not in ("X_IF", "Z_IF")])
+    assert oracle.Program(c2).row_bits("meas")[2][1:].any()

@@ -31,7 +31,10 @@ MUTANTS = {
     "expect-kappa": ("for (int v = 1; v <= m; v++) odd +=", "for (int v = 1; v < m; v++) odd +="),
     "vjp-sign": ("grad_p[c] += g[j] * (-2.0 * dP / f);", "grad_p[c] += g[j] * (2.0 * dP / f);"),
     "deterministic-row-set": ("            if (X(P, i)[a]) rowsum(P, sc, i + n);", "            if (Z(P, i)[a]) rowsum(P, sc, i + n);"),
-    "reset-row-set": ("        if (Z(P, r)[a]) {\n            uint64_t *ph = PH(P, r);", "        if (X(P, r)[a]) {\n            uint64_t *ph = PH(P, r);"),
+    "reset-row-set": ("if (c != OR_M) cond_pauli(P, t[j], 1, 0, e);", "if (c != OR_M) cond_pauli(P, t[j], 0, 1, e);"),
+    "conditional-pauli-rows": ("if ((xb && Z(P, r)[a]) ^ (zb && X(P, r)[a])) {", "if ((xb && X(P, r)[a]) ^ (zb && Z(P, r)[a])) {"),
+    "feedforward-lookback": ("P->meas + (P->nmeas - lb) * P->pw);", "P->meas + (P->nmeas - lb + 1) * P->pw);"),
+    "feedforward-y-as-x": ("cond_pauli(P, t[j + 1], c != OR_ZIF, c != OR_XIF,", "cond_pauli(P, t[j + 1], c != OR_ZIF, c == OR_ZIF,"),
     "counter-layout": ("uint32_t ctr[4] = {(uint32_t)shot, (uint32_t)(shot >> 32), (uint32_t)(c / 4), 0u};",
                        "uint32_t ctr[4] = {(uint32_t)shot, (uint32_t)(c / 4), (uint32_t)(shot >> 32), 0u};"),
 }

@@ -9,17 +9,19 @@ import pytest
 
 import oracle
 from checkers import statevec
-from workloads import random_clifford_circuit, random_small_circuit
+from workloads import random_clifford_circuit, random_feedforward_circuit, random_small_circuit
 
 
-@pytest.mark.parametrize("seed", range(24))
+@pytest.mark.parametrize("seed", range(36))
 def test_distribution_matches(seed):
     rng = np.random.default_rng(500 + seed)
     n = int(rng.integers(1, 8))
     if seed < 16:
         circuit = random_small_circuit(n, int(rng.integers(8, 40)), seed=100 + seed)
-    else:
+    elif seed < 24:
         circuit = random_clifford_circuit(max(n, 2), int(rng.integers(20, 60)), seed=200 + seed)
+    else:
+        circuit = random_feedforward_circuit(max(n, 2), int(rng.integers(10, 50)), seed=300 + seed)
     prog = oracle.Program(circuit)
     rnd = prog.random_symbols()
     rand_syms = [s for s in range(1, prog.num_symbols + 1) if rnd[s]]

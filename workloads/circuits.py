@@ -13,6 +13,10 @@ Op vocabulary (a small Stim-like grammar written for this project):
     X_ERROR(p) a..  Y_ERROR(p) a..  Z_ERROR(p) a..
     DEPOLARIZE1(p) a..                DEPOLARIZE2(p) a b a b ..
     DETECTOR rec[-k] ..               OBSERVABLE_INCLUDE(i) rec[-k] ..
+    X_IF rec[-k] a ..  Y_IF rec[-k] a ..  Z_IF rec[-k] a ..
+                                      (feed-forward: the Pauli on qubit a when
+                                       record rec[-k] is 1; the conditional
+                                       Paulis of Sec. 6)
     TICK
 
 Generators:
@@ -39,13 +43,15 @@ MEASURES = ("M", "MR", "R")
 NOISE_1Q = ("X_ERROR", "Y_ERROR", "Z_ERROR", "DEPOLARIZE1")
 NOISE_2Q = ("DEPOLARIZE2",)
 ANNOTATIONS = ("DETECTOR", "OBSERVABLE_INCLUDE", "TICK")
-ALL_OPS = GATES_1Q + GATES_2Q + MEASURES + NOISE_1Q + NOISE_2Q + ANNOTATIONS
+FEEDFORWARD = ("X_IF", "Y_IF", "Z_IF")
+ALL_OPS = GATES_1Q + GATES_2Q + MEASURES + NOISE_1Q + NOISE_2Q + ANNOTATIONS + FEEDFORWARD
 
 
 @dataclasses.dataclass(frozen=True)
 class Op:
     """One instruction. ``targets`` are qubit indices, except for DETECTOR and
-    OBSERVABLE_INCLUDE where they are positive look-backs k of ``rec[-k]``.
+    OBSERVABLE_INCLUDE where they are positive look-backs k of ``rec[-k]``,
+    and X_IF/Y_IF/Z_IF where they are (k, qubit) pairs.
     ``arg`` is the probability of a noise op, the observable index of
     OBSERVABLE_INCLUDE, and 0 otherwise."""
 
@@ -66,6 +72,8 @@ class Circuit:
     def _grow(self, op: Op) -> None:
         if op.name in GATES_1Q + GATES_2Q + MEASURES + NOISE_1Q + NOISE_2Q and op.targets:
             self.num_qubits = max(self.num_qubits, max(op.targets) + 1)
+        elif op.name in FEEDFORWARD and len(op.targets) >= 2:
+            self.num_qubits = max(self.num_qubits, max(op.targets[1::2]) + 1)
 
     def append(self, name: str, targets: Sequence[int] = (), arg: float = 0.0) -> "Circuit":
         if name not in ALL_OPS:
@@ -121,6 +129,8 @@ class Circuit:
                 head += f"({int(op.arg)})"
             if op.name in ("DETECTOR", "OBSERVABLE_INCLUDE"):
                 tail = " ".join(f"rec[-{k}]" for k in op.targets)
+            elif op.name in FEEDFORWARD:
+                tail = " ".join(f"rec[-{k}] {q}" for k, q in zip(op.targets[::2], op.targets[1::2]))
             else:
                 tail = " ".join(str(t) for t in op.targets)
             lines.append((head + " " + tail).rstrip())
@@ -149,6 +159,15 @@ class Circuit:
                     if not mm:
                         raise ValueError(f"line {lineno}: bad record target {t!r}")
                     tg.append(int(mm.group(1)))
+            elif name in FEEDFORWARD:
+                if len(rest) % 2:
+                    raise ValueError(f"line {lineno}: {name} takes rec[-k] qubit pairs")
+                tg = []
+                for rt, qt in zip(rest[::2], rest[1::2]):
+                    mm = re.fullmatch(r"rec\[-(\d+)\]", rt)
+                    if not mm:
+                        raise ValueError(f"line {lineno}: bad record target {rt!r}")
+                    tg += [int(mm.group(1)), int(qt)]
             else:
                 tg = [int(t) for t in rest]
             c.append(name, tg, float(arg) if arg not in (None, "") else 0.0)
@@ -447,5 +466,39 @@ def random_small_circuit(num_qubits: int, num_ops: int, seed: int, p_noise: floa
         else:
             q = int(rng.integers(num_qubits))
             c.append(k, [q], p_noise if k in NOISE_1Q else 0.0)
+    c.append("M", list(range(num_qubits)))
+    return c
+
+
+def random_feedforward_circuit(num_qubits: int, num_ops: int, seed: int, p_noise: float = 0.2) -> Circuit:
+    """Small random circuits with feed-forward: the vocabulary of
+    ``random_small_circuit`` plus X_IF / Y_IF / Z_IF on a random qubit,
+    conditioned on a random earlier record (rec[-k], k up to 6), and a
+    teleportation-style correction after some measurements (X_IF rec[-1] on
+    another qubit)."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(num_qubits)
+    kinds = ["H", "S", "CX", "X", "Y", "Z", "M", "MR", "R", "X_ERROR", "Y_ERROR", "Z_ERROR",
+             "DEPOLARIZE1", "DEPOLARIZE2", "X_IF", "Y_IF", "Z_IF"]
+    nrec = 0
+    for _ in range(num_ops):
+        k = kinds[rng.integers(len(kinds))]
+        if k in ("CX", "DEPOLARIZE2"):
+            if num_qubits < 2:
+                continue
+            a, b = rng.choice(num_qubits, size=2, replace=False)
+            c.append(k, [int(a), int(b)], p_noise if k == "DEPOLARIZE2" else 0.0)
+        elif k in FEEDFORWARD:
+            if nrec == 0:
+                continue
+            back = int(rng.integers(1, min(nrec, 6) + 1))
+            c.append(k, [back, int(rng.integers(num_qubits))])
+        else:
+            q = int(rng.integers(num_qubits))
+            c.append(k, [q], p_noise if k in NOISE_1Q else 0.0)
+            if k in ("M", "MR"):
+                nrec += 1
+                if num_qubits > 1 and rng.random() < 0.3:
+                    c.append("X_IF", [1, int((q + 1 + rng.integers(num_qubits - 1)) % num_qubits)])
     c.append("M", list(range(num_qubits)))
     return c
