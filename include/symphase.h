@@ -73,12 +73,17 @@ enum {
     SP_OP_X_ERROR = 9, SP_OP_Y_ERROR = 10, SP_OP_Z_ERROR = 11,
     SP_OP_DEPOLARIZE1 = 12, SP_OP_DEPOLARIZE2 = 13,   /* Pauli faults (Init-P, Sec. 3.1 channels) */
     SP_OP_DETECTOR = 14, SP_OP_OBSERVABLE_INCLUDE = 15,
-    SP_OP_TICK = 16
+    SP_OP_TICK = 16,
+    SP_OP_X_IF = 17, SP_OP_Y_IF = 18, SP_OP_Z_IF = 19  /* feed-forward: conditional Paulis (Sec. 6) */
 };
 
 /* One op.  Gate / noise / measurement ops apply to each target in turn
  * (CX and DEPOLARIZE2 to consecutive pairs).  DETECTOR and
  * OBSERVABLE_INCLUDE targets are look-backs k >= 1 meaning rec[-k].
+ * X_IF / Y_IF / Z_IF targets are pairs (k, q): the Pauli on qubit q is
+ * applied when record rec[-k] is 1, i.e. the conditional Pauli P^e with e
+ * that record's affine form (the conditional Paulis of Sec. 6, of which a
+ * reset's X^e is the special case on the measured qubit).
  * arg: probability for noise ops, observable index for
  * OBSERVABLE_INCLUDE, ignored otherwise. */
 typedef struct {

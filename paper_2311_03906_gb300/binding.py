@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "SP_OK", 1: "SP_ERR_INVALID_ARG", 2: "SP_ERR_UNSUPPORTED_OP",
                 6: "SP_ERR_TIMEOUT", 7: "SP_ERR_TOO_LARGE"}
 OPCODES = {"H": 0, "S": 1, "CX": 2, "X": 3, "Y": 4, "Z": 5, "M": 6, "MR": 7, "R": 8,
            "X_ERROR": 9, "Y_ERROR": 10, "Z_ERROR": 11, "DEPOLARIZE1": 12, "DEPOLARIZE2": 13,
-           "DETECTOR": 14, "OBSERVABLE_INCLUDE": 15, "TICK": 16}
+           "DETECTOR": 14, "OBSERVABLE_INCLUDE": 15, "TICK": 16, "X_IF": 17, "Y_IF": 18, "Z_IF": 19}
 PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED, PATH_TENSOR = 0, 1, 2, 3, 4
 
 # every entry point declared in include/symphase.h

@@ -181,6 +181,33 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             }
             continue;
         }
+        if (code >= I_XIF) {
+            // Feed-forward (the conditional Paulis of Sec. 6): P^e on qubit a
+            // with e the form of record in.b.  A stabilizer row that
+            // anticommutes with P (X: z_a, Z: x_a, Y: x_a ^ z_a) gets e: its
+            // constant bit here, its symbol part in the replay (EV_FF).
+            if (lp + 2 + (uint64_t)n > P.log_cap) { err = 1; break; }
+            const bool useZ = code != I_ZIF, useX = code != I_XIF;
+            __syncthreads();   // the record's constant was written by thread 0
+            const uint32_t e_const = P.rec_const[in.b];
+            int f = 0;
+            if (t < n) {
+                const bool zb = (Z[(size_t)wa * R2 + t] & ma) != 0, xb = (X[(size_t)wa * R2 + t] & ma) != 0;
+                f = ((useZ && zb) != (useX && xb)) ? 1 : 0;
+            }
+            int total;
+            const int off = block_excl_scan(f, s_warp, &total);
+            if (f) {
+                P.log[lp + 2 + off] = (uint32_t)t;
+                if (e_const) r[t] ^= 1;
+            }
+            if (t == 0) {
+                P.log[lp] = (EV_FF << 24) | (uint32_t)total;
+                P.log[lp + 1] = in.b;
+            }
+            lp += 2 + (uint64_t)total;
+            continue;
+        }
         if (code >= I_XERR) {
             // Init-P: record each symbol's injection column over the
             // stabilizer rows (X-type part: z_q, Z-type part: x_q).
@@ -372,7 +399,7 @@ __global__ void __launch_bounds__(32) k_replay(const uint32_t *__restrict__ log,
         const uint32_t ev = h >> 24, cnt = h & 0xffffffu;
         // every event must fit in the log and name rows below n
         const uint64_t len = ev == EV_INJECT ? 2 : ev == EV_MRAND ? 4 + (uint64_t)cnt
-                           : ev == EV_MDET ? 2 + (uint64_t)cnt : 1 + (uint64_t)cnt;
+                           : (ev == EV_MDET || ev == EV_FF) ? 2 + (uint64_t)cnt : 1 + (uint64_t)cnt;
         if (pos + len > log_len) break;
         if (ev == EV_INJECT) {
             const uint32_t s0 = log[pos + 1];
@@ -416,6 +443,17 @@ __global__ void __launch_bounds__(32) k_replay(const uint32_t *__restrict__ log,
             if (j < cnt) acc0 ^= v[min(rows[j], (uint32_t)n - 1u) * 32 + lane];
             e = acc0 ^ acc1;
             if (rec != NO_REC && write) A[(size_t)rec * apitch + g] = e;
+            pos += 2 + cnt;
+        } else if (ev == EV_FF) {
+            // the record's symbol word for this lane: written above by this
+            // same thread, or still zero if the record precedes its symbols
+            const uint32_t rec = log[pos + 1];
+            const uint32_t ef = write ? A[(size_t)rec * apitch + g] : 0u;
+            const uint32_t *rows = log + pos + 2;
+            for (uint32_t j = 0; j < cnt; j++) {
+                const uint32_t i = rows[j];
+                if (i < (uint32_t)n) v[i * 32 + lane] ^= ef;
+            }
             pos += 2 + cnt;
         } else {
             const uint32_t *rows = log + pos + 1;
@@ -618,6 +656,7 @@ struct Flat {
     int64_t nmeas = 0;
     int64_t cap_sym = 0;
     int64_t nmeasfam = 0;
+    int64_t nff = 0;         // feed-forward instructions
 };
 
 uint32_t threshold_of(double p)
@@ -635,7 +674,7 @@ sp_status flatten(const sp_circuit_desc *d, Flat &F)
         const uint32_t k = op.ntargets;
         if (k && !op.targets) return set_error(SP_ERR_INVALID_ARG, "op " + std::to_string(i) + ": NULL targets");
         const uint32_t c = op.opcode;
-        if (c > SP_OP_TICK) return set_error(SP_ERR_UNSUPPORTED_OP, "op " + std::to_string(i) + ": unknown opcode " + std::to_string(c));
+        if (c > SP_OP_Z_IF) return set_error(SP_ERR_UNSUPPORTED_OP, "op " + std::to_string(i) + ": unknown opcode " + std::to_string(c));
         if (c <= SP_OP_DEPOLARIZE2) {
             for (uint32_t j = 0; j < k; j++)
                 if (op.targets[j] >= n)
@@ -699,6 +738,19 @@ sp_status flatten(const sp_circuit_desc *d, Flat &F)
             }
             if (!dst) F.det_off.push_back((uint32_t)F.det_refs.size());
         } break;
+        case SP_OP_X_IF: case SP_OP_Y_IF: case SP_OP_Z_IF: {
+            if (k % 2) return set_error(SP_ERR_INVALID_ARG, "op " + std::to_string(i) + ": feed-forward takes (rec, qubit) pairs");
+            const uint32_t code = c == SP_OP_X_IF ? I_XIF : c == SP_OP_Y_IF ? I_YIF : I_ZIF;
+            for (uint32_t j = 0; j < k; j += 2) {
+                const uint32_t lb = op.targets[j], q = op.targets[j + 1];
+                if (lb < 1 || (int64_t)lb > F.nmeas)
+                    return set_error(SP_ERR_INVALID_ARG, "op " + std::to_string(i) + ": rec[-" + std::to_string(lb) + "] beyond the records so far");
+                if (q >= n)
+                    return set_error(SP_ERR_INVALID_ARG, "op " + std::to_string(i) + ": qubit " + std::to_string(q) + " >= num_qubits");
+                F.insts.push_back({code, q, (uint32_t)(F.nmeas - lb), 0, 0});
+                F.nff++;
+            }
+        } break;
         default: break;
         }
     }
@@ -753,7 +805,8 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     const int Wq = std::max(1, (n + 31) / 32);
     const int R2 = std::max(32, ((2 * n + 31) / 32) * 32);
     const int64_t cap_sym = F.cap_sym;
-    const uint64_t log_cap = 2 * (uint64_t)F.insts.size() + (uint64_t)F.nmeasfam * (2 * (uint64_t)n + 8) + 16;
+    const uint64_t log_cap = 2 * (uint64_t)F.insts.size() + (uint64_t)F.nmeasfam * (2 * (uint64_t)n + 8) +
+                             (uint64_t)F.nff * (2 + (uint64_t)n) + 16;
 
     Inst *d_insts; uint32_t *d_log, *d_inj; uint64_t *d_logpos; uint8_t *d_symrand, *d_recconst;
     TraverseCounts *d_counts; uint32_t *d_gtab = nullptr;

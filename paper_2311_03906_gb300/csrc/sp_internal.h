@@ -19,13 +19,14 @@ namespace sp {
 enum InstCode : uint32_t {
     I_H = 0, I_S, I_CX, I_X, I_Y, I_Z,
     I_M, I_MR, I_R,
-    I_XERR, I_YERR, I_ZERR, I_DEP1, I_DEP2
+    I_XERR, I_YERR, I_ZERR, I_DEP1, I_DEP2,
+    I_XIF, I_YIF, I_ZIF    // feed-forward: a = qubit, b = record index
 };
 
 struct Inst {
     uint32_t code;
     uint32_t a;      // qubit
-    uint32_t b;      // second qubit (CX, DEP2)
+    uint32_t b;      // second qubit (CX, DEP2), record index (feed-forward)
     uint32_t aux;    // threshold T for noise ops
     uint32_t pbits;  // FP32 bits of the probability of noise ops
 };
@@ -39,7 +40,8 @@ enum LogEvent : uint32_t {
     EV_INJECT = 1,   // [hdr|k, s0]            symbols s0..s0+k-1 get their injection columns
     EV_MRAND = 2,    // [hdr|cnt, p, s, rec, rows..]  random measurement with pivot p
     EV_MDET = 3,     // [hdr|cnt, rec, rows..]        deterministic measurement
-    EV_RESET = 4     // [hdr|cnt, rows..]             conditional X^e on the rows
+    EV_RESET = 4,    // [hdr|cnt, rows..]             conditional X^e on the rows
+    EV_FF = 5        // [hdr|cnt, rec, rows..]        rows ^= form of record rec (feed-forward)
 };
 constexpr uint32_t NO_REC = 0xFFFFFFFFu;
 

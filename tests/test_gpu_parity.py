@@ -8,8 +8,8 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import (Circuit, random_clifford_circuit, random_layered, random_small_circuit,
-                       repetition_code, surface_code)
+from workloads import (Circuit, random_clifford_circuit, random_feedforward_circuit, random_layered,
+                       random_small_circuit, repetition_code, surface_code)
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +48,8 @@ for _s in range(8):
     CIRCUITS[f"rand{_s}"] = (lambda s=_s: random_small_circuit(3 + 7 * s, 60 + 30 * s, seed=900 + s))
 for _s in range(6):
     CIRCUITS[f"cliff{_s}"] = (lambda s=_s: random_clifford_circuit(2 + 3 * s, 80 + 40 * s, seed=700 + s))
+for _s in range(6):
+    CIRCUITS[f"ff{_s}"] = (lambda s=_s: random_feedforward_circuit(3 + 6 * s, 60 + 40 * s, seed=800 + s))
 
 
 def _u64(t):
@@ -80,7 +82,7 @@ def test_rows_match_oracle(name):
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
 @pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "wide1000", "rand3", "rand7",
-                                  "cliff2", "cliff5"])
+                                  "cliff2", "cliff5", "ff1", "ff4"])
 @pytest.mark.parametrize("shot0,shots", [(0, 1), (5, 31), (64, 33), (1 << 33, 1061), (7, 4101)])
 def test_records_match_oracle(name, shot0, shots, path):
     c = CIRCUITS[name]()
@@ -127,6 +129,21 @@ def test_every_fused_variant_matches_oracle(name, tile, variant):
     np.testing.assert_array_equal(_u64(m), rm)
     np.testing.assert_array_equal(_u64(d), rd)
     np.testing.assert_array_equal(_u64(o), ro)
+
+
+def test_teleportation_with_feedforward():
+    """Teleporting |1> with X_IF / Z_IF corrections: the last record is 1 in
+    every shot while both Bell-measurement records are uniformly random."""
+    c = Circuit(3)
+    c.append("X", [0]); c.append("H", [1]); c.append("CX", [1, 2]); c.append("CX", [0, 1]); c.append("H", [0])
+    c.append("M", [0, 1]); c.append("X_IF", [1, 2]); c.append("Z_IF", [2, 2]); c.append("M", [2])
+    prog, ref = sp.build(c), oracle.Program(c)
+    m, _, _ = prog.sample(4096, seed=9)
+    torch.cuda.synchronize()
+    rec = oracle.unpack_records(_u64(m), 3)
+    assert rec[:, 2].all()
+    assert 0.45 < rec[:, 0].mean() < 0.55 and 0.45 < rec[:, 1].mean() < 0.55
+    np.testing.assert_array_equal(_u64(m), ref.sample(9, 0, 4096)[0])
 
 
 def test_chunking_and_host_path_give_identical_records():
