@@ -373,11 +373,13 @@ def run_ours(args):
     bytes_B = info["num_symbols"] * shots / 8.0
     bytes_rec = nrec * shots / 8.0
     nblocks = -(-info["num_channels"] // 4)
-    # Philox4x32-10 per (shot, 4-channel block): 17 of its 20 32x32->64-bit
-    # products depend on both the shot and the block (the other three are
-    # computed once per shot or once per block); each product costs two
-    # integer-multiply issues (low and high word).
-    mul_ops = nblocks * 34.0 * shots
+    # Philox4x32-10 per (shot, 4-channel block): 16 of its 20 32x32->64-bit
+    # products depend on both the shot and the block (rounds 3-10); round 1's
+    # two and round 2's M1 product depend on the shot or the block alone, and
+    # round 2's M0 product on the block and the shot's high word (shared by a
+    # whole tile). Each product costs two integer-multiply issues (low and
+    # high word).
+    mul_ops = nblocks * 32.0 * shots
     mul_peak = 152 * 64 * peaks["sm_max_mhz"] * 1e6 / 1e12  # T int32 multiplies/s at max SM clock
     for name, (kms, n) in prof.items():
         if n == 0:

@@ -24,8 +24,10 @@
 // Philox per (shot, channel block b): counter (shot lo, shot hi, b, 0).
 // Round 1's product M1*b is the same for every lane (one per warp), and the
 // products M0*(shot lo) of round 1 and M1*(hi0 ^ k1) of round 2 do not depend
-// on b, so they are computed once per shot: 17 of the 20 wide multiplies of a
-// block remain per (shot, block).
+// on b, so they are computed once per shot; round 2's M0 product depends on b
+// and the shot's high word only, so a tile whose shots share that word
+// computes it once per block: 16 of the 20 wide multiplies of a block remain
+// per (shot, block).
 #include <algorithm>
 #include <map>
 #include <memory>
