@@ -38,3 +38,18 @@ def test_random_layered_rows_are_sparse():
     # most records are a fresh random-measurement symbol
     rnd = prog.random_symbols()
     assert rnd.sum() > 0.5 * prog.num_meas
+
+
+def test_per_channel_probabilities_follow_channel_order():
+    from workloads import channel_probabilities, surface_code, with_channel_probabilities
+    base = surface_code(3, 3, 1e-3)
+    p = channel_probabilities(base.num_fault_channels, seed=4)
+    c = with_channel_probabilities(base, p)
+    assert c.num_fault_channels == base.num_fault_channels
+    prog, ref = oracle.Program(c), oracle.Program(base)
+    ch = prog.channels()
+    fault = ch.type != 5          # random-measurement channels keep 1/2
+    np.testing.assert_allclose(ch.p[fault], p)
+    # same symbols and coefficient rows: only the probabilities changed
+    np.testing.assert_array_equal(prog.rows("det"), ref.rows("det"))
+    np.testing.assert_array_equal(prog.channels().sym0, ref.channels().sym0)

@@ -427,6 +427,29 @@ def channel_probabilities(n_channels: int, lo: float = 5e-4, hi: float = 2e-3, s
     return rng.uniform(lo, hi, size=n_channels)
 
 
+def with_channel_probabilities(circuit: Circuit, p: Sequence[float]) -> Circuit:
+    """The same circuit with fault channel c (in op order: one per target of
+    a one-qubit noise op, one per pair of DEPOLARIZE2) at probability p[c]:
+    each noise op is split into one op per channel."""
+    p = np.asarray(p, dtype=np.float64)
+    if len(p) != circuit.num_fault_channels:
+        raise ValueError(f"{len(p)} probabilities for {circuit.num_fault_channels} fault channels")
+    out = Circuit(circuit.num_qubits)
+    c = 0
+    for op in circuit.ops:
+        if op.name in NOISE_1Q:
+            for t in op.targets:
+                out.append(op.name, [t], float(p[c]))
+                c += 1
+        elif op.name in NOISE_2Q:
+            for a, b in zip(op.targets[::2], op.targets[1::2]):
+                out.append(op.name, [a, b], float(p[c]))
+                c += 1
+        else:
+            out.append(op.name, op.targets, op.arg)
+    return out
+
+
 def random_clifford_circuit(num_qubits: int, num_ops: int, seed: int, p_noise: float = 0.2) -> Circuit:
     """Clifford-heavy random circuits: mostly H, S and CX (building Y
     components and long products of stabilizers), some faults, rare
