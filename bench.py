@@ -31,6 +31,34 @@ SHOTS = 1_000_000
 METRIC = "shots_per_s"
 UNIT = "shots/s"
 
+# DRAM traffic of one launch of the fused sampling kernel on this workload:
+# dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu capture of
+# the first timed 1,000,000-shot launch. The figure belongs to the kernel
+# source it was taken on; when the hash of that source differs, it is dropped
+# (reported as null) until a new capture replaces it.
+FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 588_030 + 300_860_000,
+                 "sources_sha256": "374b8e95d14040c1bf3540e759ca12f4284f301c3048eac8b0c90cd458742c13"}
+FUSED_SOURCES = ("paper_2311_03906_gb300/csrc/sp_fused.cu", "paper_2311_03906_gb300/csrc/sp_internal.h")
+
+
+def _sources_sha256(paths=FUSED_SOURCES):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _fused_traffic(shots_per_launch):
+    """Measured DRAM bytes of one fused launch of shots_per_launch shots (the
+    records written grow in proportion to the shots), or None when no capture
+    matches the current kernel source."""
+    t = FUSED_TRAFFIC
+    if t["bytes"] is None or t["sources_sha256"] != _sources_sha256():
+        return None
+    return t["bytes"] * shots_per_launch / t["shots"]
+
 
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -473,8 +501,12 @@ def run_ours(args):
     roof = None
     if dom:
         k = kern[dom]
+        traffic = None
+        if dom == "fused":
+            traffic = _fused_traffic(shots * args.steps / k["launches"])
         roof = {"kernel": dom, "bound": k.get("bound"), "achieved": k.get("achieved"), "peak": k.get("peak"),
-                "unit": k.get("unit"), "frac": k.get("frac"), "traffic": None,
+                "unit": k.get("unit"), "frac": k.get("frac"), "traffic": traffic,
+                "algorithmic_record_bytes": bytes_rec * args.steps / k["launches"],
                 "peak_source": ("152 SMs x 64 int32 multiplies/clk x max SM clock (derived)" if k.get("bound") == "alu"
                                 else f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})")}
     launches = sum(v[1] for v in prof.values())
@@ -520,7 +552,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots", type=int, default=SHOTS)
