@@ -121,8 +121,8 @@ typedef struct {
     uint64_t log_words;            /* length of the traversal's row-operation log */
     double density;                /* nnz_rows / (rows * n_s) */
     int32_t path;                  /* SP_PATH_SPARSE, SP_PATH_DENSE, SP_PATH_FUSED or SP_PATH_TENSOR */
-    int32_t fused_tile_shots;      /* shots per fused tile (32 or 64; 0 = fused path unavailable) */
-    int32_t fused_variant;         /* 1, or 2 = the 64-shot kernel built for one CTA per SM */
+    int32_t fused_tile_shots;      /* shots per fused tile (32, 64 or 128; 0 = fused path unavailable) */
+    int32_t fused_variant;         /* 1, or 2 = the 64/128-shot kernel built for one CTA per SM */
     int32_t fused_ctas_per_sm;     /* resident CTAs per SM of the chosen fused kernel */
     int32_t autotune_launches;     /* fused-kernel launches the build-time autotuner made */
     int32_t reserved;
@@ -258,11 +258,12 @@ SP_API sp_status sp_set_path(sp_program *prog, int32_t path);
 
 /*
  * sp_set_fused_config -- choose the fused kernel variant by hand instead of
- * the build-time autotuner's choice: tile_shots 32 or 64 (shots per CTA
- * tile); variant 1 (two CTAs per SM) or 2 (64-shot tiles only: the kernel
- * compiled for one CTA per SM with more registers; for 32-shot tiles it is
- * the same kernel as 1).  INVALID_ARG if the tile's records do not fit in
- * shared memory.  Records are identical for every variant.
+ * the build-time autotuner's choice: tile_shots 32, 64 or 128 (shots per
+ * CTA tile; 128 = four Philox streams per thread); variant 1 (two CTAs per
+ * SM: 512 threads for 32- and 64-shot tiles, 256 threads for 128) or 2 (one
+ * CTA of 512 threads per SM compiled with more registers; for 32-shot tiles
+ * it is the same kernel as 1).  INVALID_ARG if the tile's records do not fit
+ * in shared memory.  Records are identical for every variant.
  */
 SP_API sp_status sp_set_fused_config(sp_program *prog, int32_t tile_shots, int32_t variant);
 

@@ -303,7 +303,8 @@ sp_status sp_set_path(sp_program *P, int32_t path)
 sp_status sp_set_fused_config(sp_program *P, int32_t tile_shots, int32_t variant)
 {
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
-    if (tile_shots != 32 && tile_shots != 64) return set_error(SP_ERR_INVALID_ARG, "tile_shots must be 32 or 64");
+    if (tile_shots != 32 && tile_shots != 64 && tile_shots != 128)
+        return set_error(SP_ERR_INVALID_ARG, "tile_shots must be 32, 64 or 128");
     return fused_select(P, tile_shots / 32, variant);
 }
 

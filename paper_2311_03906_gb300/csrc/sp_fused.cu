@@ -262,10 +262,12 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
 
 // Fired-event queue of one warp: FUSED_QCAP 32-bit words in shared memory.
 // An event is one (channel block, shot) in which at least one of the block's
-// depolarizing channels fired: bits 10..31 block - the warp's first block,
-// bit 9 tile word t, bits 4..8 lane, bits 0..3 the fired channels.
+// depolarizing channels fired: bits 0..3 the fired channels, bits 4..8 lane,
+// then the tile word t (one bit for TW <= 2, two for TW = 4), then block -
+// the warp's first block in the remaining bits.
 constexpr uint32_t FUSED_QCAP = 128;
-constexpr uint32_t EVENT_MAX_BLOCKS = 1u << 22;
+__host__ __device__ constexpr int event_tbits(int tw) { return tw == 4 ? 2 : 1; }
+__host__ __device__ constexpr uint32_t event_max_blocks(int tw) { return 1u << (32 - 9 - event_tbits(tw)); }
 // Channel blocks whose compare results are gathered before one vote.
 constexpr uint32_t DRAW_GROUP = 8;
 static_assert(4 * DRAW_GROUP == 32, "a group's channels map one to one onto the lanes");
@@ -291,10 +293,11 @@ __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const
                                             const Apply &apply)
 {
     __syncwarp();
+    constexpr int TB = event_tbits(TW);
     for (uint32_t e = lane; e < n; e += 32) {
         const uint32_t ev = q[e];
-        const uint32_t b = b0 + (ev >> 10);
-        const int t = (ev >> 9) & 1u;
+        const uint32_t b = b0 + (ev >> (9 + TB));
+        const int t = (ev >> 9) & ((1u << TB) - 1u);
         const uint32_t ln = (ev >> 4) & 31u;
         uint32_t fmask = ev & 15u;
         const ShotConst s = shot_const(shot_base + 32u * (uint32_t)t + ln, k1);
@@ -349,7 +352,8 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
                                                 const Shots<TW> sc, uint64_t shot_base, uint32_t k0, uint32_t k1,
                                                 int lane, uint32_t *q, const Apply &apply)
 {
-    static_assert(TW == 1 || TW == 2, "one or two tile words");
+    static_assert(TW == 1 || TW == 2 || TW == 4, "one, two or four tile words");
+    constexpr int TB = event_tbits(TW);
     const Keys K = make_keys(k0, k1);
     const uint32_t c1u = (uint32_t)(shot_base >> 32);
     const uint32_t lt = (1u << lane) - 1u;
@@ -386,7 +390,7 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
                 const uint32_t bal = __ballot_sync(FM, nib != 0u);
                 if (nib)
                     q[cnt + __popc(bal & lt)] =
-                        ((g + (uint32_t)k - b0) << 10) | ((uint32_t)t << 9) | ((uint32_t)lane << 4) | nib;
+                        ((g + (uint32_t)k - b0) << (9 + TB)) | ((uint32_t)t << 9) | ((uint32_t)lane << 4) | nib;
                 cnt += __popc(bal);
                 m &= ~(15u << (4 * k));
             }
@@ -481,12 +485,22 @@ template <> struct TileWord<2> {
     __device__ static T ones() { return make_uint2(FM, FM); }
     __device__ static uint32_t get(T v, int t) { return t ? v.y : v.x; }
 };
+template <> struct TileWord<4> {
+    typedef uint4 T;
+    __device__ static T zero() { return make_uint4(0u, 0u, 0u, 0u); }
+    __device__ static T ones() { return make_uint4(FM, FM, FM, FM); }
+    __device__ static uint32_t get(T v, int t) { return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w; }
+};
 __device__ __forceinline__ uint32_t xorw(uint32_t a, uint32_t b) { return a ^ b; }
 __device__ __forceinline__ uint2 xorw(uint2 a, uint2 b) { return make_uint2(a.x ^ b.x, a.y ^ b.y); }
+__device__ __forceinline__ uint4 xorw(uint4 a, uint4 b)
+{
+    return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
+}
 
-// One tile of 32*TW shots of one program, by the whole CTA.  Ends with a
-// barrier, so the caller may start another tile right away.
-template <int TW>
+// One tile of 32*TW shots of one program, by the whole CTA of NT threads.
+// Ends with a barrier, so the caller may start another tile right away.
+template <int TW, int NT = FUSED_THREADS>
 __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, uint32_t *sm)
 {
     typedef TileWord<TW> TWd;
@@ -513,9 +527,11 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
     }
     __syncthreads();
     // ---- phase 2B: parent chains, m_j = own part ^ m_parent ---------------
-    {
-        const uint32_t e = p.bOff[tid + 1];
-        for (uint32_t i = p.bOff[tid]; i < e; i++) {
+    // (trees are scheduled over FUSED_THREADS lists; a smaller CTA walks
+    // several lists, each independent of the others)
+    for (int th = tid; th < FUSED_THREADS; th += NT) {
+        const uint32_t e = p.bOff[th + 1];
+        for (uint32_t i = p.bOff[th]; i < e; i++) {
             const uint2 rp = p.bItem[i];
             Rs[rp.x] = xorw(Rs[rp.x], Rs[rp.y]);
         }
@@ -560,15 +576,22 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
     __syncthreads();
 }
 
-// Two CTAs per SM (64 registers); U = 2 marks the 64-shot variant compiled
-// for one CTA per SM with more registers.
+// Launch shapes: 32- and 64-shot tiles at 512 threads and two CTAs per SM
+// (64 registers); U = 2 marks the 64-shot variant compiled for one CTA per
+// SM with more registers.  128-shot tiles (four independent Philox streams
+// per thread) run at 256 threads and two CTAs per SM (U = 1) or 512 threads
+// and one CTA per SM (U = 2), 128 registers either way.
+__host__ __device__ constexpr int fused_threads(int tw, int u) { return tw == 4 && u == 1 ? 256 : FUSED_THREADS; }
+__host__ __device__ constexpr int fused_minb(int tw, int u) { return u == 2 && tw != 1 ? 1 : 2; }
+
 template <int TW, int U>
-__global__ void __launch_bounds__(FUSED_THREADS, (TW == 2 && U == 2) ? 1 : 2) k_fused(FusedParams p)
+__global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fused(FusedParams p)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const uint64_t per_tile = 32u * TW;
     const uint64_t ntiles = (p.nshots + per_tile - 1) / per_tile;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) fused_tile<TW>(p, tile, sm);
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        fused_tile<TW, fused_threads(TW, U)>(p, tile, sm);
 }
 
 // Batched form: many programs in one persistent launch.  Work items are
@@ -672,6 +695,9 @@ sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, 
     k_dense_fill<<<(unsigned)ceil_div(nvec, 256), 256, 0, s>>>(Bd, bpitch, nvec);
     SP_CUDA(cudaGetLastError());
     if (P->n_blk == 0) return SP_OK;
+    // one warp covers every channel block: queued events must address them all
+    if ((uint64_t)P->n_blk >= event_max_blocks(2))
+        return set_error(SP_ERR_INVALID_ARG, "too many channel blocks for the dense draw");
     k_draw_dense<<<(unsigned)ceil_div(ceil_div(ngroups, 2), 8), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->d_blkSym0,
                                                                             P->n_blk, seed, shot0, ngroups, Bd, bpitch);
     SP_CUDA(cudaGetLastError());
@@ -830,7 +856,7 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     P->smem_max = smem_max;
     P->fused_tw = 0;
     // queued events address blocks relative to a warp's first block
-    const bool events_ok = (uint64_t)nb / (FUSED_THREADS / 32) + 1 < EVENT_MAX_BLOCKS;
+    const bool events_ok = (uint64_t)nb / (FUSED_THREADS / 32) + 1 < event_max_blocks(2);
     if (R > 0 && nb > 0 && events_ok) {
         if (fused_words(P, 2) * 4 <= (size_t)smem_max) st = fused_select(P, 2, 1);
         else if (fused_words(P, 1) * 4 <= (size_t)smem_max) st = fused_select(P, 1, 1);
@@ -857,16 +883,18 @@ typedef void (*FusedFn)(FusedParams);
 
 static FusedFn fused_kernel(int tw, int unroll)
 {
+    if (tw == 4) return unroll == 2 ? k_fused<4, 2> : k_fused<4, 1>;
     if (tw == 2) return unroll == 2 ? k_fused<2, 2> : k_fused<2, 1>;
     return unroll == 2 ? k_fused<1, 2> : k_fused<1, 1>;
 }
 
 sp_status fused_select(sp_program *P, int tw, int unroll)
 {
-    if ((tw != 1 && tw != 2) || (unroll != 1 && unroll != 2))
-        return set_error(SP_ERR_INVALID_ARG, "tile words must be 1 or 2, variant 1 or 2");
+    if ((tw != 1 && tw != 2 && tw != 4) || (unroll != 1 && unroll != 2))
+        return set_error(SP_ERR_INVALID_ARG, "tile words must be 1, 2 or 4, variant 1 or 2");
     if (P->n_rows == 0 || P->n_blk == 0) return set_error(SP_ERR_INVALID_ARG, "nothing to sample on the fused path");
-    if ((uint64_t)P->n_blk / (FUSED_THREADS / 32) + 1 >= EVENT_MAX_BLOCKS)
+    const int threads = fused_threads(tw, unroll);
+    if ((uint64_t)P->n_blk / (uint64_t)(threads / 32) + 1 >= event_max_blocks(tw))
         return set_error(SP_ERR_INVALID_ARG, "too many channel blocks for the fused path");
     const size_t bytes = fused_words(P, tw) * 4;
     if (bytes > (size_t)P->smem_max)
@@ -876,9 +904,10 @@ sp_status fused_select(sp_program *P, int tw, int unroll)
     // at the device maximum so that no program's choice lowers another's.
     SP_CUDA(max_dynamic_smem(fn));
     int occ = 0;
-    SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FUSED_THREADS, bytes));
+    SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, bytes));
     P->fused_tw = tw;
     P->fused_unroll = unroll;
+    P->fused_threads = threads;
     P->fused_smem = bytes;
     P->fused_aux_off = aux_offset(P, tw);
     P->fused_ctas_per_sm = std::max(occ, 1);
@@ -886,8 +915,9 @@ sp_status fused_select(sp_program *P, int tw, int unroll)
 }
 
 // Autotuner: time the fused variants that fit -- 64-shot tiles at two CTAs
-// per SM, 32-shot tiles, 64-shot tiles at one CTA per SM with more registers
-// -- on a few tiles per SM and keep the fastest.  The choice is cached per
+// per SM, 32-shot tiles, 64-shot tiles at one CTA per SM with more registers,
+// 128-shot tiles at 256 threads x two CTAs or 512 threads x one CTA per SM --
+// on a few tiles per SM and keep the fastest.  The choice is cached per
 // circuit shape for the process.
 sp_status autotune(sp_program *P, cudaStream_t s)
 {
@@ -905,7 +935,8 @@ sp_status autotune(sp_program *P, cudaStream_t s)
         }
     }
     std::vector<std::pair<int, int>> cand;
-    for (auto c : {std::make_pair(2, 1), std::make_pair(1, 1), std::make_pair(2, 2)})
+    for (auto c : {std::make_pair(2, 1), std::make_pair(1, 1), std::make_pair(2, 2), std::make_pair(4, 1),
+                   std::make_pair(4, 2)})
         if (fused_words(P, c.first) * 4 <= (size_t)P->smem_max) cand.push_back(c);
     const uint64_t shots = (uint64_t)P->num_sms * 2u * 64u * 4u;
     const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
@@ -996,7 +1027,7 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
     const uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)P->num_sms * (uint64_t)P->fused_ctas_per_sm);
     ProfScope ps(P, SP_KERNEL_FUSED, s);
     FusedFn fn = fused_kernel(P->fused_tw, P->fused_unroll);
-    fn<<<dim3((unsigned)grid), dim3(FUSED_THREADS), P->fused_smem, s>>>(fp);
+    fn<<<dim3((unsigned)grid), dim3((unsigned)P->fused_threads), P->fused_smem, s>>>(fp);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -137,7 +137,8 @@ struct sp_program {
     uint32_t *d_colRows = nullptr;    // [nnz_delta]
     int smem_max = 0;
     int fused_tw = 0;                 // shots per tile / 32 (0 = fused path off)
-    int fused_unroll = 1;             // 2: the 64-shot variant with one CTA per SM
+    int fused_unroll = 1;             // 2: the 64- or 128-shot variant with one CTA per SM
+    int fused_threads = 512;          // threads per CTA of the selected variant
     size_t fused_smem = 0;
     uint32_t fused_aux_off = 0;       // shared-memory words before the queue/stage region
     bool tuned = false;

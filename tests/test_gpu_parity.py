@@ -43,6 +43,8 @@ CIRCUITS = {
     "surf5": lambda: surface_code(5, 5, 2e-3),
     "layered40": lambda: random_layered(40, 40, depolarize=0.01, seed=3),
     "wide1000": lambda: random_layered(1000, 3, cnot_pairs=500, depolarize=0.001, seed=4),
+    # depolarizing events in most (block, shot) pairs: the warps' event queues fill and drain
+    "noisy5": lambda: surface_code(5, 5, 0.05),
 }
 for _s in range(8):
     CIRCUITS[f"rand{_s}"] = (lambda s=_s: random_small_circuit(3 + 7 * s, 60 + 30 * s, seed=900 + s))
@@ -99,7 +101,7 @@ def test_records_match_oracle(name, shot0, shots, path):
     np.testing.assert_array_equal(_u64(o), ro)
 
 
-@pytest.mark.parametrize("tile", [32, 64])
+@pytest.mark.parametrize("tile", [32, 64, 128])
 @pytest.mark.parametrize("name", ["surf5", "layered40"])
 def test_fused_tiles_straddling_2_pow_32_shots(name, tile):
     """shot0 just below 2^32: some tiles hold shots with two different high
@@ -116,8 +118,8 @@ def test_fused_tiles_straddling_2_pow_32_shots(name, tile):
     np.testing.assert_array_equal(_u64(o), ro)
 
 
-@pytest.mark.parametrize("tile,variant", [(32, 1), (32, 2), (64, 1), (64, 2)])
-@pytest.mark.parametrize("name", ["rep5", "surf5", "layered40", "rand6"])
+@pytest.mark.parametrize("tile,variant", [(32, 1), (32, 2), (64, 1), (64, 2), (128, 1), (128, 2)])
+@pytest.mark.parametrize("name", ["rep5", "surf5", "layered40", "rand6", "noisy5"])
 def test_every_fused_variant_matches_oracle(name, tile, variant):
     c = CIRCUITS[name]()
     prog, ref = sp.build(c), oracle.Program(c)
@@ -200,6 +202,30 @@ def test_full_size_d11_both_paths_agree(d11, path):
         np.testing.assert_array_equal(_u64(o[idx]), ro)
     finally:
         prog.set_path(sp.PATH_AUTO)
+
+
+@pytest.mark.parametrize("tile,variant", [(64, 1), (128, 1), (128, 2)])
+def test_full_size_d11_fused_variants_agree(d11, tile, variant):
+    """Every 64- and 128-shot launch shape gives the records of the
+    autotuner's choice at d=11 (200,000 shots, ragged tail), and a few shots
+    are recomputed by the oracle."""
+    c, prog, ref = d11
+    tuned = (prog.info["fused_tile_shots"], prog.info["fused_variant"])
+    base = prog.sample(200_003, seed=8, shot0=5)
+    prog.set_fused_config(tile, variant)
+    try:
+        assert prog.info["fused_tile_shots"] == tile and prog.info["fused_variant"] == variant
+        out = prog.sample(200_003, seed=8, shot0=5)
+        torch.cuda.synchronize()
+        for a, b in zip(out, base):
+            assert torch.equal(a, b)
+        pick = np.array([0, 127, 128, 200_002])
+        rm, rd, ro = ref.sample_shots(8, pick + 5)
+        idx = torch.as_tensor(pick, device="cuda")
+        np.testing.assert_array_equal(_u64(out[0][idx]), rm)
+        np.testing.assert_array_equal(_u64(out[1][idx]), rd)
+    finally:
+        prog.set_fused_config(*tuned)
 
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
