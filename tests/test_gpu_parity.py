@@ -228,6 +228,55 @@ def test_full_size_d11_fused_variants_agree(d11, tile, variant):
         prog.set_fused_config(*tuned)
 
 
+def _long_repetition(rounds: int, noisy_every: int, p: float):
+    """Distance-3 repetition memory with many rounds (about four record rows
+    per round) and X_ERROR(p) on the data qubits only every noisy_every
+    rounds, so the rows are many and the symbols few."""
+    c = Circuit(5)
+    c.append("R", [0, 1, 2, 3, 4])
+    for r in range(rounds):
+        if r % noisy_every == 0:
+            c.append("X_ERROR", [0, 1, 2], p)
+        c.append("CX", [0, 3, 1, 4])
+        c.append("CX", [1, 3, 2, 4])
+        c.append("MR", [3, 4])
+        for i in range(2):
+            c.append("DETECTOR", [2 - i] if r == 0 else [2 - i, 4 - i])
+    c.append("M", [0, 1, 2])
+    for i in range(2):
+        # data i, data i+1 and ancilla i of the last round
+        c.append("DETECTOR", [3 - i, 2 - i, 5 - i])
+    c.append("OBSERVABLE_INCLUDE", [3], 0)
+    return c
+
+
+@pytest.mark.parametrize("rounds,tile", [(8000, 32), (15000, 0)])
+def test_records_beyond_shared_memory(rounds, tile):
+    """Maximum sizes of the fused tile: at 8,000 rounds (32k record rows) the
+    records fit in shared memory only as 32-shot tiles; at 15,000 (60k rows)
+    not at all, and the fused path is refused. The build's own choice, the
+    staged path, both dense products and (where it fits) the fused path all
+    give the oracle's records."""
+    c = _long_repetition(rounds, 1000, 0.05)
+    prog, ref = sp.build(c), oracle.Program(c)
+    assert prog.num_measurements == 2 * rounds + 3
+    assert prog.info["fused_tile_shots"] == tile
+    if not tile:
+        with pytest.raises(sp.SymPhaseError):
+            prog.set_path(sp.PATH_FUSED)
+    rm, rd, ro = ref.sample(6, 31, 301)
+    assert rd.any()   # faults reach the detectors
+    paths = [sp.PATH_AUTO, sp.PATH_SPARSE, sp.PATH_DENSE, sp.PATH_TENSOR] + ([sp.PATH_FUSED] if tile else [])
+    for path in paths:
+        prog.set_path(path)
+        m, d, o = prog.sample(301, seed=6, shot0=31)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(_u64(m), rm, err_msg=f"path {path}")
+        np.testing.assert_array_equal(_u64(d), rd, err_msg=f"path {path}")
+        np.testing.assert_array_equal(_u64(o), ro, err_msg=f"path {path}")
+    assert prog.device_status() == 0
+
+
 @pytest.mark.parametrize("path", ["fused", "staged"])
 def test_full_size_d17_in_64k_chunks(path):
     """d=17 r=17 p=2e-3 (about 100k symbols), 1e6 shots sampled in
