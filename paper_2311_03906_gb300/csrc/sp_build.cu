@@ -28,6 +28,7 @@ namespace sp {
 constexpr int TRAV_THREADS = 1024;
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int PARENT_LOOKBACK = 512;
+constexpr int REPLAY_SPLIT_MIN_N = 256;   // qubits from which k_replay runs 8 warps per CTA
 
 __device__ __forceinline__ int gcount(uint32_t x1, uint32_t z1, uint32_t x2, uint32_t z2)
 {
@@ -41,55 +42,35 @@ __device__ __forceinline__ int gcount(uint32_t x1, uint32_t z1, uint32_t x2, uin
     return __popc(pos) - __popc(neg);
 }
 
-__device__ __forceinline__ int warp_min(int v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o));
-    return v;
-}
-
 __device__ __forceinline__ int warp_sum(int v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
 
-// Exclusive prefix sum of c over a 1024-thread block; *total gets the sum.
-__device__ __forceinline__ int block_excl_scan(int c, int *s_warp, int *total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int inc = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        int v = s_warp[lane];
-        int vi = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(FULL, vi, o);
-            if (lane >= o) vi += y;
-        }
-        s_warp[lane] = vi - v;
-        if (lane == 31) s_warp[32] = vi;
-    }
-    __syncthreads();
-    int off = s_warp[warp] + inc - c;
-    *total = s_warp[32];
-    __syncthreads();
-    return off;
-}
+// One step of the traversal: a group of ops on disjoint qubits (gates and
+// noise injections, run in parallel) or one barrier op (a measurement, reset
+// or feed-forward, run by the whole CTA).  Ops are sched[begin, end).
+struct TravStep {
+    uint32_t begin, end;
+    uint32_t barrier;
+    uint32_t inj_before;    // noise ops before this step in circuit order
+    uint32_t fsym_before;   // fault symbols before this step
+    uint32_t pad[3];
+};
 
 struct TravParams {
     const Inst *insts;
-    int64_t ninst;
-    int n, Wq, R2;
+    const uint32_t *sched;
+    const TravStep *steps;
+    int64_t nsteps;
+    uint32_t ninj_total, nfsym_total;
+    int n, SW;               // qubits; 32-row words per column
     uint32_t *gtab;          // used when the tableau does not fit in shared memory
     int tab_in_smem;
     uint32_t *log;
     uint64_t log_cap;
-    uint32_t *inj;           // [(cap_sym + 2) * Wq]
+    uint32_t *inj;           // [(cap_sym + 2) * SW]
     uint64_t *sym_logpos;    // [cap_sym + 2]
     uint8_t *sym_random;     // [cap_sym + 2]
     uint32_t *chT;
@@ -100,252 +81,352 @@ struct TravParams {
     TraverseCounts *counts;
 };
 
-// K1: the X/Z pass.  Thread t owns tableau rows t and t + 1024; rows 0..n-1
-// are stabilizers, n..2n-1 destabilizers (stabilizer i pairs with row n+i).
-// Layout: X[w * R2 + row] (32 qubits per word, rows contiguous per word).
+constexpr int TAB_XS = 0, TAB_ZS = 1, TAB_XD = 2, TAB_ZD = 3;
+
+// Bit i of the result = XOR of bits 0..i-1 of x.
+__device__ __forceinline__ uint32_t prefix_xor_excl(uint32_t x)
+{
+    uint32_t y = x << 1;
+    y ^= y << 1;
+    y ^= y << 2;
+    y ^= y << 4;
+    y ^= y << 8;
+    y ^= y << 16;
+    return y;
+}
+
+// One warp writes the rows of the mask words (lane = word; lanes past the
+// last word pass 0) to dst in increasing order and returns their number.
+__device__ __forceinline__ uint32_t write_rows(uint32_t *dst, uint32_t m, int lane)
+{
+    const uint32_t c = __popc(m);
+    uint32_t inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, inc, 31);
+    uint32_t off = inc - c;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        dst[off++] = 32u * (uint32_t)lane + (uint32_t)b;
+    }
+    return total;
+}
+
+// K1: the X/Z pass, qubit-major.  The tableau is kept per qubit q as four
+// bit-vectors over the n stabilizer rows (32 rows per word): XS(q), ZS(q) of
+// the stabilizers and XD(q), ZD(q) of the destabilizers (destabilizer i pairs
+// with stabilizer i), plus the stabilizer phases r as one bit-vector.  A gate
+// (Init-C's column rules, Fact 1 for Paulis) is a few word operations per 32
+// rows, an injection column (Init-P: X^s flips the rows with z_q = 1, Z^s the
+// rows with x_q = 1) is a column read, and a measurement (Init-M) works on
+// whole columns.  Gates and injections arrive in groups on disjoint qubits,
+// one op per warp at a time with lane = row word; a gate's phase flips stay
+// in the lane's register until the next barrier.  Measurements, resets and
+// feed-forward ops are barriers run by the whole CTA.  Requires n <= 1024.
 __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(16) uint32_t tsm[];
+    __shared__ uint32_t s_rs[32], s_m0[32], s_m1[32], s_px[32], s_pz[32];
+    __shared__ uint32_t s_c0[32 * 32], s_c1[32 * 32];
+    __shared__ int s_red[32];
     __shared__ int s_p, s_e, s_err;
+    __shared__ uint32_t s_cnt;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int n = P.n, NR = 2 * n, Wq = P.Wq, R2 = P.R2;
-    int *s_warp = reinterpret_cast<int *>(smem);          // 64 ints
-    int *s_list = s_warp + 64;                            // 2048 ints
-    uint8_t *r = reinterpret_cast<uint8_t *>(s_list + 2048); // R2 bytes (stabilizer phases)
-    uint32_t *X = P.tab_in_smem ? reinterpret_cast<uint32_t *>(r + R2) : P.gtab;
-    uint32_t *Z = X + (size_t)Wq * R2;
-    const int row0 = t, row1 = t + TRAV_THREADS;
+    const int n = P.n, SW = P.SW;
+    uint32_t *tab = P.tab_in_smem ? tsm : P.gtab;
+    auto col = [&](int q) { return tab + (size_t)q * 4 * SW; };
 
-    for (int w = 0; w < Wq; w++) {
-        for (int k = 0; k < 2; k++) {
-            int row = t + k * TRAV_THREADS;
-            if (row >= R2) break;
-            uint32_t xv = 0, zv = 0;
-            if (row < n) {
-                if ((row >> 5) == w) zv = 1u << (row & 31);
-            } else if (row < NR) {
-                int q = row - n;
-                if ((q >> 5) == w) xv = 1u << (q & 31);
-            }
-            X[(size_t)w * R2 + row] = xv;
-            Z[(size_t)w * R2 + row] = zv;
-        }
+    // stabilizer i = Z_i, destabilizer i = X_i, phases 0
+    for (int64_t i = t; i < (int64_t)n * 4 * SW; i += TRAV_THREADS) {
+        const int q = (int)(i / (4 * SW)), k = (int)((i / SW) % 4), w = (int)(i % SW);
+        tab[i] = ((k == TAB_ZS || k == TAB_XD) && w == (q >> 5)) ? 1u << (q & 31) : 0u;
     }
-    if (row0 < R2) r[row0] = 0;
-    if (row1 < R2) r[row1] = 0;
+    if (t < 32) s_rs[t] = 0;
     if (t == 0) s_err = 0;
     __syncthreads();
 
-    uint32_t nsym = 0, nch = 0, nrec = 0, err = 0;
-    uint64_t lp = 0;
-    for (int64_t ii = 0; ii < P.ninst; ii++) {
-        const Inst in = P.insts[ii];
-        const uint32_t code = in.code;
-        const uint32_t a = in.a, wa = a >> 5, ma = 1u << (a & 31);
-        if (code <= I_Z) {
-            // Init-C (H, S, CX: A-G's column updates, phase column 0) and
-            // Pauli gates (Fact 1).  Rows are independent: no barrier.
-            for (int k = 0; k < 2; k++) {
-                const int row = t + k * TRAV_THREADS;
-                if (row >= NR) break;
-                uint32_t *px = X + (size_t)wa * R2 + row;
-                uint32_t *pz = Z + (size_t)wa * R2 + row;
-                const bool stab = row < n;
-                switch (code) {
-                case I_H: {
-                    uint32_t xv = *px, zv = *pz, xb = xv & ma, zb = zv & ma;
-                    if (stab && xb && zb) r[row] ^= 1;
-                    *px = (xv & ~ma) | zb;
-                    *pz = (zv & ~ma) | xb;
-                } break;
-                case I_S: {
-                    uint32_t xv = *px, zv = *pz;
-                    if (stab && (xv & ma) && (zv & ma)) r[row] ^= 1;
-                    *pz = zv ^ (xv & ma);
-                } break;
-                case I_X: if (stab && (*pz & ma)) r[row] ^= 1; break;
-                case I_Z: if (stab && (*px & ma)) r[row] ^= 1; break;
-                case I_Y: if (stab && ((*px ^ *pz) & ma)) r[row] ^= 1; break;
-                case I_CX: {
-                    const uint32_t b = in.b, wb = b >> 5, mb = 1u << (b & 31);
-                    uint32_t *qx = X + (size_t)wb * R2 + row;
-                    uint32_t *qz = Z + (size_t)wb * R2 + row;
-                    const bool xa = (*px & ma) != 0, za = (*pz & ma) != 0;
-                    const bool xb = (*qx & mb) != 0, zb = (*qz & mb) != 0;
-                    if (stab && xa && zb && (xb == za)) r[row] ^= 1;
-                    if (xa) *qx ^= mb;
-                    if (zb) *pz ^= ma;
-                } break;
-                default: break;
+    uint32_t rd = 0;                     // this lane's pending phase flips
+    uint32_t nrand = 0, nrec = 0, inj_mark = 0, err = 0;
+    uint64_t lp = 0;                     // log position after the last barrier's event
+    for (int64_t si = 0; si < P.nsteps; si++) {
+        const TravStep S = P.steps[si];
+        if (!S.barrier) {
+            for (uint32_t k = S.begin + (uint32_t)warp; k < S.end; k += TRAV_THREADS / 32) {
+                const Inst in = P.insts[P.sched[k]];
+                const uint32_t code = in.code;
+                if (code <= I_Z) {
+                    if (lane >= SW) continue;
+                    uint32_t *ca = col((int)in.a);
+                    uint32_t *XS = ca + TAB_XS * SW + lane, *ZS = ca + TAB_ZS * SW + lane;
+                    uint32_t *XD = ca + TAB_XD * SW + lane, *ZD = ca + TAB_ZD * SW + lane;
+                    switch (code) {
+                    case I_H: {
+                        const uint32_t xs = *XS, zs = *ZS, xd = *XD, zd = *ZD;
+                        rd ^= xs & zs;
+                        *XS = zs; *ZS = xs; *XD = zd; *ZD = xd;
+                    } break;
+                    case I_S: {
+                        const uint32_t xs = *XS, zs = *ZS;
+                        rd ^= xs & zs;
+                        *ZS = zs ^ xs;
+                        *ZD ^= *XD;
+                    } break;
+                    case I_X: rd ^= *ZS; break;
+                    case I_Z: rd ^= *XS; break;
+                    case I_Y: rd ^= *XS ^ *ZS; break;
+                    case I_CX: {
+                        uint32_t *cb = col((int)in.b);
+                        const uint32_t xa = *XS, za = *ZS;
+                        const uint32_t xb = cb[TAB_XS * SW + lane], zb = cb[TAB_ZS * SW + lane];
+                        rd ^= xa & zb & ~(xb ^ za);
+                        cb[TAB_XS * SW + lane] = xb ^ xa;
+                        *ZS = za ^ zb;
+                        cb[TAB_XD * SW + lane] ^= *XD;
+                        *ZD ^= cb[TAB_ZD * SW + lane];
+                    } break;
+                    default: break;
+                    }
+                    continue;
+                }
+                // Init-P: the injection column of each symbol over the
+                // stabilizer rows; log slots in circuit order
+                const int kk = code == I_DEP2 ? 4 : (code == I_DEP1 ? 2 : 1);
+                const uint32_t s0 = 1u + in.sym_base + nrand, ch = in.gi + nrand;
+                const uint64_t slot = lp + 2ull * (in.gi - inj_mark);
+                if (slot + 2 > P.log_cap) {
+                    s_err = 1;
+                    continue;
+                }
+                for (int j = 0; j < kk; j++) {
+                    const uint32_t q = (j < 2) ? in.a : in.b;
+                    bool useZ, useX;
+                    if (code == I_XERR) { useZ = true; useX = false; }
+                    else if (code == I_ZERR) { useZ = false; useX = true; }
+                    else if (code == I_YERR) { useZ = true; useX = true; }
+                    else { useZ = !(j & 1); useX = (j & 1) != 0; }
+                    if (lane < SW) {
+                        const uint32_t *cq = col((int)q);
+                        uint32_t v = 0;
+                        if (useZ) v ^= cq[TAB_ZS * SW + lane];
+                        if (useX) v ^= cq[TAB_XS * SW + lane];
+                        P.inj[(size_t)(s0 + j) * SW + lane] = v;
+                    }
+                    if (lane == 0) {
+                        P.sym_logpos[s0 + j] = slot;
+                        P.sym_random[s0 + j] = 0;
+                    }
+                }
+                if (lane == 0) {
+                    P.chT[ch] = in.aux;
+                    P.chP[ch] = __uint_as_float(in.pbits);
+                    P.chKind[ch] = (kk == 1) ? CK_BERN : (kk == 2 ? CK_DEP1 : CK_DEP2);
+                    P.chSym0[ch] = s0;
+                    P.log[slot] = (EV_INJECT << 24) | (uint32_t)kk;
+                    P.log[slot + 1] = s0;
                 }
             }
+            __syncthreads();
             continue;
         }
+        // ---- barrier op ------------------------------------------------------
+        lp += 2ull * (S.inj_before - inj_mark);   // the segment's injection events
+        inj_mark = S.inj_before;
+        if (lane < SW && rd) atomicXor(&s_rs[lane], rd);
+        rd = 0;
+        const Inst in = P.insts[P.sched[S.begin]];
+        const uint32_t code = in.code;
+        const int a = (int)in.a;
+        if (lp + 2 * (uint64_t)n + 8 > P.log_cap) { err = 1; break; }
+        __syncthreads();   // phases flushed, the group's columns written
+        uint32_t *ca = col(a);
         if (code >= I_XIF) {
             // Feed-forward (the conditional Paulis of Sec. 6): P^e on qubit a
-            // with e the form of record in.b.  A stabilizer row that
+            // with e the form of record in.b.  A stabilizer that
             // anticommutes with P (X: z_a, Z: x_a, Y: x_a ^ z_a) gets e: its
             // constant bit here, its symbol part in the replay (EV_FF).
-            if (lp + 2 + (uint64_t)n > P.log_cap) { err = 1; break; }
-            const bool useZ = code != I_ZIF, useX = code != I_XIF;
-            __syncthreads();   // the record's constant was written by thread 0
-            const uint32_t e_const = P.rec_const[in.b];
-            int f = 0;
-            if (t < n) {
-                const bool zb = (Z[(size_t)wa * R2 + t] & ma) != 0, xb = (X[(size_t)wa * R2 + t] & ma) != 0;
-                f = ((useZ && zb) != (useX && xb)) ? 1 : 0;
-            }
-            int total;
-            const int off = block_excl_scan(f, s_warp, &total);
-            if (f) {
-                P.log[lp + 2 + off] = (uint32_t)t;
-                if (e_const) r[t] ^= 1;
-            }
-            if (t == 0) {
-                P.log[lp] = (EV_FF << 24) | (uint32_t)total;
-                P.log[lp + 1] = in.b;
-            }
-            lp += 2 + (uint64_t)total;
-            continue;
-        }
-        if (code >= I_XERR) {
-            // Init-P: record each symbol's injection column over the
-            // stabilizer rows (X-type part: z_q, Z-type part: x_q).
-            const int k = (code == I_DEP2) ? 4 : (code == I_DEP1 ? 2 : 1);
-            if (lp + 2 > P.log_cap) { err = 1; break; }
-            const uint32_t s0 = nsym + 1;
-            for (int j = 0; j < k; j++) {
-                const uint32_t q = (j < 2) ? a : in.b;
-                int useZ, useX;
-                if (code == I_XERR) { useZ = 1; useX = 0; }
-                else if (code == I_ZERR) { useZ = 0; useX = 1; }
-                else if (code == I_YERR) { useZ = 1; useX = 1; }
-                else { useZ = !(j & 1); useX = j & 1; }
-                uint32_t bit = 0;
-                if (t < n) {
-                    const uint32_t w = q >> 5, m = 1u << (q & 31);
-                    const uint32_t xb = (X[(size_t)w * R2 + t] & m) ? 1u : 0u;
-                    const uint32_t zb = (Z[(size_t)w * R2 + t] & m) ? 1u : 0u;
-                    bit = (useZ & zb) ^ (useX & xb);
+            if (warp == 0) {
+                const bool useZ = code != I_ZIF, useX = code != I_XIF;
+                uint32_t m = 0;
+                if (lane < SW) {
+                    if (useZ) m ^= ca[TAB_ZS * SW + lane];
+                    if (useX) m ^= ca[TAB_XS * SW + lane];
                 }
-                const uint32_t bal = __ballot_sync(FULL, bit);
-                if (lane == 0 && warp < Wq) P.inj[(size_t)(s0 + j) * Wq + warp] = bal;
+                const uint32_t total = write_rows(P.log + lp + 2, m, lane);
+                if (P.rec_const[in.b] && lane < SW) s_rs[lane] ^= m;
+                if (lane == 0) {
+                    P.log[lp] = (EV_FF << 24) | total;
+                    P.log[lp + 1] = in.b;
+                    s_cnt = total;
+                }
             }
-            if (t == 0) {
-                P.chT[nch] = in.aux;
-                P.chP[nch] = __uint_as_float(in.pbits);
-                P.chKind[nch] = (k == 1) ? CK_BERN : (k == 2 ? CK_DEP1 : CK_DEP2);
-                P.chSym0[nch] = s0;
-                P.log[lp] = (EV_INJECT << 24) | (uint32_t)k;
-                P.log[lp + 1] = s0;
-                for (int j = 0; j < k; j++) { P.sym_logpos[s0 + j] = lp; P.sym_random[s0 + j] = 0; }
-            }
-            lp += 2;
-            nsym += k;
-            nch++;
+            __syncthreads();
+            lp += 2 + (uint64_t)s_cnt;
             continue;
         }
-        // ---- Init-M (M, MR, R) ------------------------------------------
+        // ---- Init-M (M, MR, R) -----------------------------------------------
         const bool recorded = (code != I_R), reset = (code != I_M);
-        if (lp + 2 * (uint64_t)n + 8 > P.log_cap) { err = 1; break; }
-        __syncthreads();
-        int cand = (t < n && (X[(size_t)wa * R2 + t] & ma)) ? t : 0x7fffffff;
-        cand = warp_min(cand);
-        if (lane == 0) s_warp[warp] = cand;
-        __syncthreads();
+        const uint32_t rec = recorded ? nrec : NO_REC;
         if (warp == 0) {
-            int v = warp_min(s_warp[lane]);
-            if (lane == 0) s_p = v;
+            // the first stabilizer with x_a = 1, if any
+            const uint32_t xw = lane < SW ? ca[TAB_XS * SW + lane] : 0u;
+            const uint32_t bal = __ballot_sync(FULL, xw != 0u);
+            int p = -1;
+            if (bal) {
+                const int L = __ffs(bal) - 1;
+                p = 32 * L + __ffs(__shfl_sync(FULL, xw, L)) - 1;
+            }
+            if (lane == 0) s_p = p;
         }
         __syncthreads();
         const int p = s_p;
-        const uint32_t rec = recorded ? nrec : NO_REC;
         uint32_t e_const;
-        if (p != 0x7fffffff) {
+        if (p >= 0) {
             // random outcome: every other row with x_a = 1 becomes P_p * row
-            const bool f0 = row0 < NR && row0 != p && (X[(size_t)wa * R2 + row0] & ma);
-            const bool f1 = row1 < NR && row1 != p && (X[(size_t)wa * R2 + row1] & ma);
-            const int c = (row0 < n && f0) ? 1 : 0;
-            int total;
-            const int off = block_excl_scan(c, s_warp, &total);
-            if (c) P.log[lp + 4 + off] = (uint32_t)row0;
-            for (int k = 0; k < 2; k++) {
-                const bool f = k ? f1 : f0;
-                if (!f) continue;
-                const int row = k ? row1 : row0;
-                int g = 0;
-                for (int w = 0; w < Wq; w++) {
-                    const uint32_t xp = X[(size_t)w * R2 + p], zp = Z[(size_t)w * R2 + p];
-                    const uint32_t xr = X[(size_t)w * R2 + row], zr = Z[(size_t)w * R2 + row];
-                    if (row < n) g += gcount(xp, zp, xr, zr);
-                    X[(size_t)w * R2 + row] = xr ^ xp;
-                    Z[(size_t)w * R2 + row] = zr ^ zp;
+            const int wp = p >> 5;
+            const uint32_t bp = 1u << (p & 31);
+            if (warp == 0 && lane < SW) {
+                s_m0[lane] = ca[TAB_XS * SW + lane] & (lane == wp ? ~bp : FULL);   // stabilizers
+                s_m1[lane] = ca[TAB_XD * SW + lane];                                // destabilizers
+            }
+            {
+                // the pivot stabilizer, one bit per qubit
+                uint32_t xp = 0, zp = 0;
+                if (t < n) {
+                    const uint32_t *cq = col(t);
+                    xp = (cq[TAB_XS * SW + wp] & bp) ? 1u : 0u;
+                    zp = (cq[TAB_ZS * SW + wp] & bp) ? 1u : 0u;
                 }
-                if (row < n) r[row] = (uint8_t)((((2 * r[row] + 2 * r[p] + g) & 3) == 2) ? 1 : 0);
+                const uint32_t bx = __ballot_sync(FULL, xp), bz = __ballot_sync(FULL, zp);
+                if (lane == 0) {
+                    s_px[warp] = bx;
+                    s_pz[warp] = bz;
+                }
+            }
+            const uint32_t rp = (s_rs[wp] & bp) ? 1u : 0u;
+            __syncthreads();
+            // Rowsum of every masked row with the pivot, one column per warp at
+            // a time.  For the stabilizer rows, A-G's power of i (g summed
+            // over the qubits) is counted mod 4 in bit-sliced form (c1 c0).
+            uint32_t c0 = 0, c1 = 0;
+            if (lane < SW) {
+                const uint32_t ms = s_m0[lane], md = s_m1[lane];
+                for (int q = warp; q < n; q += TRAV_THREADS / 32) {
+                    const uint32_t xq = (s_px[q >> 5] >> (q & 31)) & 1u, zq = (s_pz[q >> 5] >> (q & 31)) & 1u;
+                    if (!(xq | zq)) continue;
+                    uint32_t *cq = col(q);
+                    const uint32_t xs = cq[TAB_XS * SW + lane], zs = cq[TAB_ZS * SW + lane];
+                    const uint32_t X2 = xs & ~zs, Y2 = xs & zs, Z2 = zs & ~xs;
+                    // +1 for the pairs (pivot, row) = XY, YZ, ZX; -1 for YX, ZY, XZ
+                    uint32_t pos, neg;
+                    if (xq && !zq) { pos = Y2; neg = Z2; }
+                    else if (xq) { pos = Z2; neg = X2; }
+                    else { pos = X2; neg = Y2; }
+                    pos &= ms;
+                    neg &= ms;
+                    c1 ^= c0 & pos;
+                    c0 ^= pos;
+                    c1 ^= ~c0 & neg;
+                    c0 ^= neg;
+                    if (xq) cq[TAB_XS * SW + lane] = xs ^ ms;
+                    if (zq) cq[TAB_ZS * SW + lane] = zs ^ ms;
+                    if (md) {
+                        if (xq) cq[TAB_XD * SW + lane] ^= md;
+                        if (zq) cq[TAB_ZD * SW + lane] ^= md;
+                    }
+                }
+            }
+            s_c0[warp * 32 + lane] = c0;
+            s_c1[warp * 32 + lane] = c1;
+            __syncthreads();
+            // destabilizer p := the old stabilizer p; stabilizer p := Z_a
+            if (t < n) {
+                uint32_t *cq = col(t);
+                const bool xp = (s_px[t >> 5] >> (t & 31)) & 1u, zp = (s_pz[t >> 5] >> (t & 31)) & 1u;
+                cq[TAB_XD * SW + wp] = (cq[TAB_XD * SW + wp] & ~bp) | (xp ? bp : 0u);
+                cq[TAB_ZD * SW + wp] = (cq[TAB_ZD * SW + wp] & ~bp) | (zp ? bp : 0u);
+                cq[TAB_XS * SW + wp] &= ~bp;
+                cq[TAB_ZS * SW + wp] = (cq[TAB_ZS * SW + wp] & ~bp) | (t == a ? bp : 0u);
+            }
+            if (warp == 0) {
+                uint32_t a0 = 0, a1 = 0;
+                for (int w = 0; w < TRAV_THREADS / 32; w++) {
+                    const uint32_t b0 = s_c0[w * 32 + lane], b1 = s_c1[w * 32 + lane];
+                    a1 ^= b1 ^ (a0 & b0);
+                    a0 ^= b0;
+                }
+                const uint32_t ms = lane < SW ? s_m0[lane] : 0u;
+                if (a0 & ms) s_err = 2;
+                if (lane < SW) {
+                    // new r = r ^ r_p ^ (power of i) / 2 on the masked rows
+                    uint32_t r = s_rs[lane] ^ (ms & (a1 ^ (rp ? FULL : 0u)));
+                    if (lane == wp) r &= ~bp;
+                    s_rs[lane] = r;
+                }
+                const uint32_t total = write_rows(P.log + lp + 4, ms, lane);
+                if (lane == 0) {
+                    const uint32_t s = 1u + S.fsym_before + nrand, ch = S.inj_before + nrand;
+                    P.log[lp] = (EV_MRAND << 24) | total;
+                    P.log[lp + 1] = (uint32_t)p;
+                    P.log[lp + 2] = s;
+                    P.log[lp + 3] = rec;
+                    P.chT[ch] = 0x80000000u;
+                    P.chP[ch] = 0.5f;
+                    P.chKind[ch] = CK_RANDOM;
+                    P.chSym0[ch] = s;
+                    P.sym_logpos[s] = lp;
+                    P.sym_random[s] = 1;
+                    s_cnt = total;
+                }
             }
             __syncthreads();
-            const uint32_t s = nsym + 1;
-            if (t == 0) {
-                for (int w = 0; w < Wq; w++) {
-                    X[(size_t)w * R2 + n + p] = X[(size_t)w * R2 + p];
-                    Z[(size_t)w * R2 + n + p] = Z[(size_t)w * R2 + p];
-                    X[(size_t)w * R2 + p] = 0;
-                    Z[(size_t)w * R2 + p] = ((uint32_t)w == wa) ? ma : 0u;
-                }
-                r[p] = 0;
-                P.log[lp] = (EV_MRAND << 24) | (uint32_t)total;
-                P.log[lp + 1] = (uint32_t)p;
-                P.log[lp + 2] = s;
-                P.log[lp + 3] = rec;
-                P.chT[nch] = 0x80000000u;
-                P.chP[nch] = 0.5f;
-                P.chKind[nch] = CK_RANDOM;
-                P.chSym0[nch] = s;
-                P.sym_logpos[s] = lp;
-                P.sym_random[s] = 1;
-            }
-            lp += 4 + (uint64_t)total;
-            nsym++;
-            nch++;
+            lp += 4 + (uint64_t)s_cnt;
+            nrand++;
             e_const = 0;
-            __syncthreads();
         } else {
-            // deterministic outcome: product of the stabilizers paired with
-            // destabilizers that have x_a = 1
-            const bool f0 = row0 >= n && row0 < NR && (X[(size_t)wa * R2 + row0] & ma);
-            const bool f1 = row1 < NR && (X[(size_t)wa * R2 + row1] & ma);
-            const int c = (int)f0 + (int)f1;
-            int total;
-            int off = block_excl_scan(c, s_warp, &total);
-            if (f0) { s_list[off] = row0 - n; P.log[lp + 2 + off] = (uint32_t)(row0 - n); off++; }
-            if (f1) { s_list[off] = row1 - n; P.log[lp + 2 + off] = (uint32_t)(row1 - n); }
+            // deterministic outcome: the product of the stabilizers paired with
+            // destabilizers that have x_a = 1.  Its power of i is a sum over
+            // qubits: thread q multiplies the rows' single-qubit Paulis in row
+            // order, 32 rows at a time (exclusive prefix XOR = the product of
+            // the earlier rows), with A-G's g-function per row.
+            if (warp == 0 && lane < SW) s_m1[lane] = ca[TAB_XD * SW + lane];
+            __syncthreads();
+            int G = 0;
+            if (t < n) {
+                const uint32_t *cq = col(t);
+                uint32_t cx = 0, cz = 0;
+                for (int w = 0; w < SW; w++) {
+                    const uint32_t d = s_m1[w];
+                    if (!d) continue;
+                    const uint32_t xs = cq[TAB_XS * SW + w] & d, zs = cq[TAB_ZS * SW + w] & d;
+                    if (!(xs | zs)) continue;
+                    const uint32_t px = prefix_xor_excl(xs) ^ (cx ? FULL : 0u);
+                    const uint32_t pz = prefix_xor_excl(zs) ^ (cz ? FULL : 0u);
+                    G += gcount(xs, zs, px, pz);
+                    cx ^= __popc(xs) & 1u;
+                    cz ^= __popc(zs) & 1u;
+                }
+            }
+            G = warp_sum(G);
+            if (lane == 0) s_red[warp] = G;
             __syncthreads();
             if (warp == 0) {
-                uint32_t ax = 0, az = 0;
-                int g = 0, rs = 0;
-                for (int j = 0; j < total; j++) {
-                    const int i = s_list[j];
-                    if (lane < Wq) {
-                        const uint32_t xi = X[(size_t)lane * R2 + i], zi = Z[(size_t)lane * R2 + i];
-                        g += gcount(xi, zi, ax, az);
-                        ax ^= xi;
-                        az ^= zi;
-                    }
-                    if (lane == 0) rs += r[i];
-                }
-                g = warp_sum(g);
+                const uint32_t d = lane < SW ? s_m1[lane] : 0u;
+                const int g = warp_sum(s_red[lane]) + 2 * warp_sum(__popc(lane < SW ? (s_rs[lane] & d) : 0u));
+                const uint32_t total = write_rows(P.log + lp + 2, d, lane);
                 if (lane == 0) {
-                    const int tot = (2 * rs + g) & 3;
+                    const int tot = g & 3;
                     s_e = (tot == 2) ? 1 : 0;
                     if (tot & 1) s_err = 2;
+                    P.log[lp] = (EV_MDET << 24) | total;
+                    P.log[lp + 1] = rec;
+                    s_cnt = total;
                 }
             }
-            if (t == 0) {
-                P.log[lp] = (EV_MDET << 24) | (uint32_t)total;
-                P.log[lp + 1] = rec;
-            }
-            lp += 2 + (uint64_t)total;
             __syncthreads();
+            lp += 2 + (uint64_t)s_cnt;
             e_const = (uint32_t)s_e;
         }
         if (recorded) {
@@ -354,46 +435,105 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
         }
         if (reset) {
             // conditional X^e on qubit a: flip every stabilizer with z_a = 1
-            const int f = (t < n && (Z[(size_t)wa * R2 + t] & ma)) ? 1 : 0;
-            int total;
-            const int off = block_excl_scan(f, s_warp, &total);
-            if (f) {
-                P.log[lp + 1 + off] = (uint32_t)t;
-                if (e_const) r[t] ^= 1;
+            if (warp == 0) {
+                const uint32_t m = lane < SW ? ca[TAB_ZS * SW + lane] : 0u;
+                const uint32_t total = write_rows(P.log + lp + 1, m, lane);
+                if (e_const && lane < SW) s_rs[lane] ^= m;
+                if (lane == 0) {
+                    P.log[lp] = (EV_RESET << 24) | total;
+                    s_cnt = total;
+                }
             }
-            if (t == 0) P.log[lp] = (EV_RESET << 24) | (uint32_t)total;
-            lp += 1 + (uint64_t)total;
+            __syncthreads();
+            lp += 1 + (uint64_t)s_cnt;
         }
     }
+    if (!err) lp += 2ull * (P.ninj_total - inj_mark);   // the last segment's injections
     __syncthreads();
     if (t == 0) {
         P.counts->log_len = lp;
-        P.counts->nsym = nsym;
-        P.counts->nch = nch;
+        P.counts->nsym = P.nfsym_total + nrand;
+        P.counts->nch = P.ninj_total + nrand;
         P.counts->nrec = nrec;
         P.counts->err = err ? err : (uint32_t)s_err;
     }
 }
 
-// K2: column-parallel replay.  One warp per CTA; lane l owns symbols
-// 32*(32*blockIdx + l) .. +31 as one bit-sliced word per stabilizer row.
-__global__ void __launch_bounds__(32) k_replay(const uint32_t *__restrict__ log, uint64_t log_len,
-                                               const uint32_t *__restrict__ inj, int Wq,
-                                               const uint64_t *__restrict__ sym_logpos, uint32_t nsym,
-                                               int n, uint32_t *__restrict__ A, int64_t apitch)
+// v[i][lane] ^= x for the rows of one logged event.  The rows of an event
+// are distinct (a scan over the tableau's rows), so eight of them are read
+// before any is written: the shared-memory round trips and the loads of the
+// row indices overlap instead of running one after another.  A warp whose
+// lanes all have x = 0 skips the event.
+__device__ __forceinline__ void replay_xor_rows(uint32_t *v, const uint32_t *__restrict__ rows, uint32_t cnt, int n,
+                                                int lane, uint32_t x)
 {
-    extern __shared__ uint32_t v[];  // [n][32]
-    const int lane = threadIdx.x;
+    if (!__any_sync(0xffffffffu, x != 0u)) return;
+    uint32_t j = 0;
+    for (; j + 8 <= cnt; j += 8) {
+        uint32_t i[8], a[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) i[k] = rows[j + k];
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = i[k] < (uint32_t)n ? v[i[k] * 32 + lane] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (i[k] < (uint32_t)n) v[i[k] * 32 + lane] = a[k] ^ x;
+    }
+    for (; j < cnt; j++) {
+        const uint32_t i = rows[j];
+        if (i < (uint32_t)n) v[i * 32 + lane] ^= x;
+    }
+}
+
+// XOR of v[i][lane] over the rows of one logged event (rows past n read row
+// n-1, as a malformed log must not leave the table).
+__device__ __forceinline__ uint32_t replay_xor_of_rows(const uint32_t *v, const uint32_t *__restrict__ rows,
+                                                       uint32_t cnt, int n, int lane)
+{
+    uint32_t acc[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    uint32_t j = 0;
+    for (; j + 8 <= cnt; j += 8) {
+        uint32_t i[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) i[k] = min(rows[j + k], (uint32_t)n - 1u);
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc[k] ^= v[i[k] * 32 + lane];
+    }
+    for (; j < cnt; j++) acc[0] ^= v[min(rows[j], (uint32_t)n - 1u) * 32 + lane];
+    return ((acc[0] ^ acc[1]) ^ (acc[2] ^ acc[3])) ^ ((acc[4] ^ acc[5]) ^ (acc[6] ^ acc[7]));
+}
+
+// K2: column-parallel replay.  A CTA of NW warps owns 1024 symbols: lane l
+// holds symbols 32*(32*blockIdx + l) .. +31 as one bit-sliced word per
+// stabilizer row, in a table v[n][32] shared by the warps.  The warps split
+// each event's row list; an event that changes the table ends with a
+// barrier.  Every skip decision below depends only on values all warps read
+// alike (log words, the table before the event, the event's symbol), so the
+// barriers are uniform across the CTA.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW) k_replay(const uint32_t *__restrict__ log, uint64_t log_len,
+                                                     const uint32_t *__restrict__ inj, int Wq,
+                                                     const uint64_t *__restrict__ sym_logpos, uint32_t nsym,
+                                                     int n, uint32_t *__restrict__ A, int64_t apitch)
+{
+    extern __shared__ uint32_t v[];  // [n][32], then [NW][32] partial XORs
+    uint32_t *s_acc = v + (size_t)n * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * 32 + lane;
-    uint32_t s_first = (uint32_t)blockIdx.x * 1024u;
-    if (s_first == 0) s_first = 1;
+    const uint32_t blo = (uint32_t)blockIdx.x * 1024u, bhi = blo + 1024u;
+    const uint32_t s_first = blo == 0 ? 1u : blo;
     if (s_first > nsym) return;
-    for (int i = 0; i < n; i++) v[i * 32 + lane] = 0;
-    __syncwarp();
+    for (int i = warp; i < n; i += NW) v[i * 32 + lane] = 0;
+    __syncthreads();
     const uint32_t lo = (uint32_t)g * 32u, hi = lo + 32u;
-    const bool write = g < apitch;
+    const bool write = g < apitch && warp == 0;   // warp 0 writes the records
     uint64_t pos = sym_logpos[s_first];
     uint32_t e = 0;
+    // this warp's contiguous share of an event's cnt rows
+    auto share = [&](uint32_t cnt, uint32_t &j0) {
+        j0 = (uint32_t)((uint64_t)warp * cnt / NW);
+        return (uint32_t)((uint64_t)(warp + 1) * cnt / NW) - j0;
+    };
     while (pos < log_len) {
         const uint32_t h = log[pos];
         const uint32_t ev = h >> 24, cnt = h & 0xffffffu;
@@ -401,65 +541,69 @@ __global__ void __launch_bounds__(32) k_replay(const uint32_t *__restrict__ log,
         const uint64_t len = ev == EV_INJECT ? 2 : ev == EV_MRAND ? 4 + (uint64_t)cnt
                            : (ev == EV_MDET || ev == EV_FF) ? 2 + (uint64_t)cnt : 1 + (uint64_t)cnt;
         if (pos + len > log_len) break;
+        uint32_t j0;
         if (ev == EV_INJECT) {
             const uint32_t s0 = log[pos + 1];
-            for (uint32_t s = s0; s < s0 + cnt; s++) {
-                if (s >= lo && s < hi) {
-                    const uint32_t bit = 1u << (s & 31);
-                    const uint32_t *col = inj + (size_t)s * Wq;
-                    for (int w = 0; w < Wq; w++) {
-                        uint32_t m = col[w];
-                        while (m) {
-                            const int b = __ffs(m) - 1;
-                            m &= m - 1;
-                            if (w * 32 + b < n) v[(w * 32 + b) * 32 + lane] ^= bit;
+            if (s0 < bhi && s0 + cnt > blo) {
+                for (uint32_t s = s0; s < s0 + cnt; s++) {
+                    if (s >= lo && s < hi) {
+                        const uint32_t bit = 1u << (s & 31);
+                        const uint32_t *col = inj + (size_t)s * Wq;
+                        for (int w = warp; w < Wq; w += NW) {
+                            uint32_t m = col[w];
+                            while (m) {
+                                const int b = __ffs(m) - 1;
+                                m &= m - 1;
+                                if (w * 32 + b < n) v[(w * 32 + b) * 32 + lane] ^= bit;
+                            }
                         }
                     }
                 }
+                __syncthreads();
             }
             pos += 2;
         } else if (ev == EV_MRAND) {
             const uint32_t p = min(log[pos + 1], (uint32_t)n - 1u), s = log[pos + 2], rec = log[pos + 3];
             const uint32_t vp = v[p * 32 + lane];
-            const uint32_t *rows = log + pos + 4;
-            for (uint32_t j = 0; j < cnt; j++) {
-                const uint32_t i = rows[j];
-                if (i < (uint32_t)n) v[i * 32 + lane] ^= vp;
-            }
             e = (s >= lo && s < hi) ? (1u << (s & 31)) : 0u;
-            v[p * 32 + lane] = e;
-            if (rec != NO_REC && write) A[(size_t)rec * apitch + g] = e;
+            // nothing to do when row p is zero and the new symbol is not ours
+            if (__any_sync(0xffffffffu, vp != 0u) || (s >= blo && s < bhi)) {
+                const uint32_t m = share(cnt, j0);
+                replay_xor_rows(v, log + pos + 4 + j0, m, n, lane, vp);
+                __syncthreads();   // every warp has read row p
+                if (warp == 0) v[p * 32 + lane] = e;
+                if (rec != NO_REC && write) A[(size_t)rec * apitch + g] = e;
+                __syncthreads();
+            }
             pos += 4 + cnt;
         } else if (ev == EV_MDET) {
             const uint32_t rec = log[pos + 1];
-            const uint32_t *rows = log + pos + 2;
-            uint32_t acc0 = 0, acc1 = 0;
-            uint32_t j = 0;
-            for (; j + 1 < cnt; j += 2) {
-                const uint32_t i0 = min(rows[j], (uint32_t)n - 1u), i1 = min(rows[j + 1], (uint32_t)n - 1u);
-                acc0 ^= v[i0 * 32 + lane];
-                acc1 ^= v[i1 * 32 + lane];
-            }
-            if (j < cnt) acc0 ^= v[min(rows[j], (uint32_t)n - 1u) * 32 + lane];
-            e = acc0 ^ acc1;
+            const uint32_t m = share(cnt, j0);
+            s_acc[warp * 32 + lane] = replay_xor_of_rows(v, log + pos + 2 + j0, m, n, lane);
+            __syncthreads();
+            e = 0;
+#pragma unroll
+            for (int w = 0; w < NW; w++) e ^= s_acc[w * 32 + lane];
             if (rec != NO_REC && write) A[(size_t)rec * apitch + g] = e;
+            __syncthreads();   // the partials are reused by the next event
             pos += 2 + cnt;
         } else if (ev == EV_FF) {
-            // the record's symbol word for this lane: written above by this
-            // same thread, or still zero if the record precedes its symbols
+            // the record's symbol word for this lane: written earlier by
+            // warp 0 (a barrier since), or still zero if the record precedes
+            // its symbols
             const uint32_t rec = log[pos + 1];
-            const uint32_t ef = write ? A[(size_t)rec * apitch + g] : 0u;
-            const uint32_t *rows = log + pos + 2;
-            for (uint32_t j = 0; j < cnt; j++) {
-                const uint32_t i = rows[j];
-                if (i < (uint32_t)n) v[i * 32 + lane] ^= ef;
+            const uint32_t ef = g < apitch ? A[(size_t)rec * apitch + g] : 0u;
+            if (__any_sync(0xffffffffu, ef != 0u)) {
+                const uint32_t m = share(cnt, j0);
+                replay_xor_rows(v, log + pos + 2 + j0, m, n, lane, ef);
+                __syncthreads();
             }
             pos += 2 + cnt;
         } else {
-            const uint32_t *rows = log + pos + 1;
-            for (uint32_t j = 0; j < cnt; j++) {
-                const uint32_t i = rows[j];
-                if (i < (uint32_t)n) v[i * 32 + lane] ^= e;
+            if (__any_sync(0xffffffffu, e != 0u)) {
+                const uint32_t m = share(cnt, j0);
+                replay_xor_rows(v, log + pos + 1 + j0, m, n, lane, e);
+                __syncthreads();
             }
             pos += 1 + cnt;
         }
@@ -757,6 +901,67 @@ sp_status flatten(const sp_circuit_desc *d, Flat &F)
     return SP_OK;
 }
 
+// The traversal's schedule.  Between two barrier ops (measurements, resets,
+// feed-forward) gates and noise injections are grouped by level: an op's
+// level is one more than the last level on any of its qubits, so the ops of
+// one level act on disjoint qubits and commute.  Groups run in level order,
+// each op of a group in parallel; barrier ops run alone, in circuit order.
+// Noise ops get their index among noise ops (gi) and the number of fault
+// symbols before them (sym_base): with the random outcomes so far these fix
+// their symbol, channel and log slot in circuit order.
+void schedule(std::vector<Inst> &insts, int n, std::vector<uint32_t> &sched, std::vector<TravStep> &steps,
+              uint32_t &ninj, uint32_t &nfsym)
+{
+    std::vector<uint32_t> last((size_t)std::max(n, 1), 0), epoch((size_t)std::max(n, 1), 0xffffffffu);
+    std::vector<std::pair<uint32_t, uint32_t>> pend;   // (level, op)
+    uint32_t seg = 0;
+    ninj = 0;
+    nfsym = 0;
+    auto flush = [&]() {
+        std::stable_sort(pend.begin(), pend.end(),
+                         [](const std::pair<uint32_t, uint32_t> &x, const std::pair<uint32_t, uint32_t> &y) {
+                             return x.first < y.first;
+                         });
+        for (size_t i = 0; i < pend.size();) {
+            size_t j = i;
+            const uint32_t begin = (uint32_t)sched.size();
+            while (j < pend.size() && pend[j].first == pend[i].first) sched.push_back(pend[j++].second);
+            steps.push_back({begin, (uint32_t)sched.size(), 0u, 0u, 0u, {0u, 0u, 0u}});
+            i = j;
+        }
+        pend.clear();
+        seg++;
+    };
+    for (uint32_t i = 0; i < (uint32_t)insts.size(); i++) {
+        Inst &in = insts[i];
+        const uint32_t c = in.code;
+        if (c == I_M || c == I_MR || c == I_R || c >= I_XIF) {
+            flush();
+            sched.push_back(i);
+            steps.push_back({(uint32_t)sched.size() - 1, (uint32_t)sched.size(), 1u, ninj, nfsym, {0u, 0u, 0u}});
+            continue;
+        }
+        if (c >= I_XERR) {
+            in.gi = ninj++;
+            in.sym_base = nfsym;
+            nfsym += c == I_DEP2 ? 4 : (c == I_DEP1 ? 2 : 1);
+        }
+        const bool two = c == I_CX || c == I_DEP2;
+        uint32_t lvl = 0;
+        if (epoch[in.a] == seg) lvl = last[in.a];
+        if (two && epoch[in.b] == seg) lvl = std::max(lvl, last[in.b]);
+        lvl++;
+        last[in.a] = lvl;
+        epoch[in.a] = seg;
+        if (two) {
+            last[in.b] = lvl;
+            epoch[in.b] = seg;
+        }
+        pend.push_back({lvl, i});
+    }
+    flush();
+}
+
 template <typename T>
 sp_status dalloc(T **p, size_t count)
 {
@@ -803,14 +1008,20 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
 
     Temp tmp;
     const int Wq = std::max(1, (n + 31) / 32);
-    const int R2 = std::max(32, ((2 * n + 31) / 32) * 32);
     const int64_t cap_sym = F.cap_sym;
+    std::vector<uint32_t> sched;
+    std::vector<TravStep> steps;
+    uint32_t ninj = 0, nfsym = 0;
+    schedule(F.insts, n, sched, steps, ninj, nfsym);
     const uint64_t log_cap = 2 * (uint64_t)F.insts.size() + (uint64_t)F.nmeasfam * (2 * (uint64_t)n + 8) +
                              (uint64_t)F.nff * (2 + (uint64_t)n) + 16;
 
-    Inst *d_insts; uint32_t *d_log, *d_inj; uint64_t *d_logpos; uint8_t *d_symrand, *d_recconst;
+    Inst *d_insts; uint32_t *d_log, *d_inj, *d_sched; uint64_t *d_logpos; uint8_t *d_symrand, *d_recconst;
+    TravStep *d_steps;
     TraverseCounts *d_counts; uint32_t *d_gtab = nullptr;
     SP_TRY(tmp.alloc(&d_insts, F.insts.size()));
+    SP_TRY(tmp.alloc(&d_sched, sched.size()));
+    SP_TRY(tmp.alloc(&d_steps, steps.size()));
     SP_TRY(tmp.alloc(&d_log, log_cap));
     SP_TRY(tmp.alloc(&d_inj, (size_t)(cap_sym + 2) * Wq));
     SP_TRY(tmp.alloc(&d_logpos, (size_t)cap_sym + 2));
@@ -821,19 +1032,24 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     SP_TRY(dalloc(&P->d_chKind, (size_t)cap_sym + 1));
     SP_TRY(dalloc(&P->d_chSym0, (size_t)cap_sym + 1));
     SP_TRY(dalloc(&P->d_chP, (size_t)cap_sym + 1));
-    if (!F.insts.empty())
+    if (!F.insts.empty()) {
         SP_CUDA(cudaMemcpyAsync(d_insts, F.insts.data(), F.insts.size() * sizeof(Inst), cudaMemcpyHostToDevice, stream));
+        SP_CUDA(cudaMemcpyAsync(d_sched, sched.data(), sched.size() * 4, cudaMemcpyHostToDevice, stream));
+        SP_CUDA(cudaMemcpyAsync(d_steps, steps.data(), steps.size() * sizeof(TravStep), cudaMemcpyHostToDevice, stream));
+    }
     SP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(TraverseCounts), stream));
     SP_CUDA(cudaMemsetAsync(d_recconst, 0, (size_t)F.nmeas + 1, stream));
 
-    const size_t tab_bytes = 2 * (size_t)Wq * R2 * 4;
-    const size_t head_bytes = 64 * 4 + 2048 * 4 + (size_t)R2;
-    const bool in_smem = head_bytes + tab_bytes <= 200 * 1024;
-    if (!in_smem) SP_TRY(tmp.alloc(&d_gtab, 2 * (size_t)Wq * R2));
-    const size_t smem = head_bytes + (in_smem ? tab_bytes : 0);
+    // the tableau (4 bit-vectors of n rows per qubit) in shared memory when
+    // it fits next to the kernel's 9 KB of static shared memory
+    const size_t tab_words = 4 * (size_t)std::max(n, 1) * Wq;
+    const bool in_smem = tab_words * 4 <= 200 * 1024;
+    if (!in_smem) SP_TRY(tmp.alloc(&d_gtab, tab_words));
+    const size_t smem = in_smem ? tab_words * 4 : 0;
     SP_CUDA(max_dynamic_smem(k_traverse));
     TravParams tp;
-    tp.insts = d_insts; tp.ninst = (int64_t)F.insts.size(); tp.n = n; tp.Wq = Wq; tp.R2 = R2;
+    tp.insts = d_insts; tp.sched = d_sched; tp.steps = d_steps; tp.nsteps = (int64_t)steps.size();
+    tp.ninj_total = ninj; tp.nfsym_total = nfsym; tp.n = n; tp.SW = Wq;
     tp.gtab = d_gtab; tp.tab_in_smem = in_smem ? 1 : 0; tp.log = d_log; tp.log_cap = log_cap;
     tp.inj = d_inj; tp.sym_logpos = d_logpos; tp.sym_random = d_symrand;
     tp.chT = P->d_chT; tp.chKind = P->d_chKind; tp.chSym0 = P->d_chSym0; tp.chP = P->d_chP;
@@ -858,10 +1074,19 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     SP_CUDA(cudaMemsetAsync(P->d_A, 0, arows * P->apitch * 4, stream));
     if (P->n_sym > 0 && n > 0) {
         const int64_t nblk = ceil_div(P->n_sym + 1, 1024);
-        const size_t vsm = (size_t)n * 32 * 4;
-        SP_CUDA(max_dynamic_smem(k_replay));
-        k_replay<<<(unsigned)nblk, 32, vsm, stream>>>(d_log, hc.log_len, d_inj, Wq, d_logpos,
-                                                       hc.nsym, n, P->d_A, P->apitch);
+        // eight warps share a CTA's table where row lists are long enough to
+        // split; one warp otherwise
+        if (n >= REPLAY_SPLIT_MIN_N) {
+            const size_t vsm = ((size_t)n + 8) * 32 * 4;
+            SP_CUDA(max_dynamic_smem(k_replay<8>));
+            k_replay<8><<<(unsigned)nblk, 256, vsm, stream>>>(d_log, hc.log_len, d_inj, Wq, d_logpos,
+                                                               hc.nsym, n, P->d_A, P->apitch);
+        } else {
+            const size_t vsm = ((size_t)n + 1) * 32 * 4;
+            SP_CUDA(max_dynamic_smem(k_replay<1>));
+            k_replay<1><<<(unsigned)nblk, 32, vsm, stream>>>(d_log, hc.log_len, d_inj, Wq, d_logpos,
+                                                              hc.nsym, n, P->d_A, P->apitch);
+        }
         SP_CUDA(cudaGetLastError());
     }
     if (P->n_meas > 0) {

@@ -25,10 +25,13 @@ enum InstCode : uint32_t {
 
 struct Inst {
     uint32_t code;
-    uint32_t a;      // qubit
-    uint32_t b;      // second qubit (CX, DEP2), record index (feed-forward)
-    uint32_t aux;    // threshold T for noise ops
-    uint32_t pbits;  // FP32 bits of the probability of noise ops
+    uint32_t a;         // qubit
+    uint32_t b;         // second qubit (CX, DEP2), record index (feed-forward)
+    uint32_t aux;       // threshold T for noise ops
+    uint32_t pbits;     // FP32 bits of the probability of noise ops
+    uint32_t gi;        // noise ops: index among the circuit's noise ops
+    uint32_t sym_base;  // noise ops: fault symbols before this one
+    uint32_t pad;
 };
 
 // Channel kinds used by the draw kernel.

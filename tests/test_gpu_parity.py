@@ -45,6 +45,9 @@ CIRCUITS = {
     "wide1000": lambda: random_layered(1000, 3, cnot_pairs=500, depolarize=0.001, seed=4),
     # depolarizing events in most (block, shot) pairs: the warps' event queues fill and drain
     "noisy5": lambda: surface_code(5, 5, 0.05),
+    # 256 qubits or more: the replay splits each event's rows over eight warps
+    "layered300": lambda: random_layered(300, 30, depolarize=0.01, seed=6),
+    "ffwide": lambda: random_feedforward_circuit(260, 3000, seed=810),
 }
 for _s in range(8):
     CIRCUITS[f"rand{_s}"] = (lambda s=_s: random_small_circuit(3 + 7 * s, 60 + 30 * s, seed=900 + s))
@@ -84,7 +87,7 @@ def test_rows_match_oracle(name):
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
 @pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "wide1000", "rand3", "rand7",
-                                  "cliff2", "cliff5", "ff1", "ff4"])
+                                  "cliff2", "cliff5", "ff1", "ff4", "layered300", "ffwide"])
 @pytest.mark.parametrize("shot0,shots", [(0, 1), (5, 31), (64, 33), (1 << 33, 1061), (7, 4101)])
 def test_records_match_oracle(name, shot0, shots, path):
     c = CIRCUITS[name]()
