@@ -78,6 +78,8 @@ struct TravParams {
     uint32_t *chSym0;
     float *chP;
     uint8_t *rec_const;
+    uint64_t *ev_pos;        // log positions of the events other than injections
+    uint64_t ev_cap;
     TraverseCounts *counts;
 };
 
@@ -149,7 +151,12 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
     __syncthreads();
 
     uint32_t rd = 0;                     // this lane's pending phase flips
-    uint32_t nrand = 0, nrec = 0, inj_mark = 0, err = 0;
+    uint32_t nrand = 0, nrec = 0, inj_mark = 0, err = 0, nev = 0;
+    // every event other than an injection is also listed by position
+    auto note_event = [&](uint64_t at) {
+        if (t == 0 && nev < P.ev_cap) P.ev_pos[nev] = at;
+        nev++;
+    };
     uint64_t lp = 0;                     // log position after the last barrier's event
     for (int64_t si = 0; si < P.nsteps; si++) {
         const TravStep S = P.steps[si];
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
         const Inst in = P.insts[P.sched[S.begin]];
         const uint32_t code = in.code;
         const int a = (int)in.a;
-        if (lp + 2 * (uint64_t)n + 8 > P.log_cap) { err = 1; break; }
+        if (lp + 2 * (uint64_t)n + 8 > P.log_cap || nev + 2 > P.ev_cap) { err = 1; break; }
         __syncthreads();   // phases flushed, the group's columns written
         uint32_t *ca = col(a);
         if (code >= I_XIF) {
@@ -263,6 +270,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 }
             }
             __syncthreads();
+            note_event(lp);
             lp += 2 + (uint64_t)s_cnt;
             continue;
         }
@@ -382,6 +390,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 }
             }
             __syncthreads();
+            note_event(lp);
             lp += 4 + (uint64_t)s_cnt;
             nrand++;
             e_const = 0;
@@ -426,6 +435,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 }
             }
             __syncthreads();
+            note_event(lp);
             lp += 2 + (uint64_t)s_cnt;
             e_const = (uint32_t)s_e;
         }
@@ -445,6 +455,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 }
             }
             __syncthreads();
+            note_event(lp);
             lp += 1 + (uint64_t)s_cnt;
         }
     }
@@ -455,6 +466,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
         P.counts->nsym = P.nfsym_total + nrand;
         P.counts->nch = P.ninj_total + nrand;
         P.counts->nrec = nrec;
+        P.counts->nev = nev;
         P.counts->err = err ? err : (uint32_t)s_err;
     }
 }
@@ -505,15 +517,20 @@ __device__ __forceinline__ uint32_t replay_xor_of_rows(const uint32_t *v, const 
 
 // K2: column-parallel replay.  A CTA of NW warps owns 1024 symbols: lane l
 // holds symbols 32*(32*blockIdx + l) .. +31 as one bit-sliced word per
-// stabilizer row, in a table v[n][32] shared by the warps.  The warps split
-// each event's row list; an event that changes the table ends with a
-// barrier.  Every skip decision below depends only on values all warps read
-// alike (log words, the table before the event, the event's symbol), so the
-// barriers are uniform across the CTA.
+// stabilizer row, in a table v[n][32] shared by the warps.  The CTA walks the
+// log's events other than injections (ev_pos, from the first one at or after
+// its first symbol); before each it injects its own fault symbols whose
+// injection came earlier (sym_logpos; injections after the last event reach
+// no record).  The warps split each event's row list; an event that changes
+// the table ends with a barrier.  Every skip decision depends only on values
+// all warps read alike (log words, the table before the event, the symbols),
+// so the barriers are uniform across the CTA.
 template <int NW>
-__global__ void __launch_bounds__(32 * NW) k_replay(const uint32_t *__restrict__ log, uint64_t log_len,
+__global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restrict__ log, uint64_t log_len,
+                                                     const uint64_t *__restrict__ ev_pos, uint32_t nev,
                                                      const uint32_t *__restrict__ inj, int Wq,
-                                                     const uint64_t *__restrict__ sym_logpos, uint32_t nsym,
+                                                     const uint64_t *__restrict__ sym_logpos,
+                                                     const uint8_t *__restrict__ sym_random, uint32_t nsym,
                                                      int n, uint32_t *__restrict__ A, int64_t apitch)
 {
     extern __shared__ uint32_t v[];  // [n][32], then [NW][32] partial XORs
@@ -523,46 +540,57 @@ __global__ void __launch_bounds__(32 * NW) k_replay(const uint32_t *__restrict__
     const uint32_t blo = (uint32_t)blockIdx.x * 1024u, bhi = blo + 1024u;
     const uint32_t s_first = blo == 0 ? 1u : blo;
     if (s_first > nsym) return;
+    const uint32_t s_end = min(bhi, nsym + 1u);
     for (int i = warp; i < n; i += NW) v[i * 32 + lane] = 0;
     __syncthreads();
     const uint32_t lo = (uint32_t)g * 32u, hi = lo + 32u;
     const bool write = g < apitch && warp == 0;   // warp 0 writes the records
-    uint64_t pos = sym_logpos[s_first];
+    // the first event at or after this CTA's first symbol
+    const uint64_t p0 = sym_logpos[s_first];
+    uint32_t k = 0, khi = nev;
+    while (k < khi) {
+        const uint32_t mid = (k + khi) >> 1;
+        if (ev_pos[mid] < p0) k = mid + 1; else khi = mid;
+    }
+    uint32_t s_next = s_first;
     uint32_t e = 0;
     // this warp's contiguous share of an event's cnt rows
     auto share = [&](uint32_t cnt, uint32_t &j0) {
         j0 = (uint32_t)((uint64_t)warp * cnt / NW);
         return (uint32_t)((uint64_t)(warp + 1) * cnt / NW) - j0;
     };
-    while (pos < log_len) {
+    for (; k < nev; k++) {
+        const uint64_t pos = ev_pos[k];
+        if (pos >= log_len) break;
+        // Init-P for this CTA's fault symbols injected before the event: lane
+        // l takes its own symbols, warps split the rows of each column
+        const uint32_t s_a = s_next;
+        while (s_next < s_end && sym_logpos[s_next] < pos) s_next++;
+        if (s_next > s_a) {
+            const uint32_t l1 = min(s_next, hi);
+            for (uint32_t s = max(s_a, lo); s < l1; s++) {
+                if (sym_random[s]) continue;
+                const uint32_t bit = 1u << (s & 31);
+                const uint32_t *col = inj + (size_t)s * Wq;
+                for (int w = warp; w < Wq; w += NW) {
+                    uint32_t m = col[w];
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        if (w * 32 + b < n) v[(w * 32 + b) * 32 + lane] ^= bit;
+                    }
+                }
+            }
+            __syncthreads();
+        }
         const uint32_t h = log[pos];
         const uint32_t ev = h >> 24, cnt = h & 0xffffffu;
         // every event must fit in the log and name rows below n
-        const uint64_t len = ev == EV_INJECT ? 2 : ev == EV_MRAND ? 4 + (uint64_t)cnt
+        const uint64_t len = ev == EV_MRAND ? 4 + (uint64_t)cnt
                            : (ev == EV_MDET || ev == EV_FF) ? 2 + (uint64_t)cnt : 1 + (uint64_t)cnt;
         if (pos + len > log_len) break;
         uint32_t j0;
-        if (ev == EV_INJECT) {
-            const uint32_t s0 = log[pos + 1];
-            if (s0 < bhi && s0 + cnt > blo) {
-                for (uint32_t s = s0; s < s0 + cnt; s++) {
-                    if (s >= lo && s < hi) {
-                        const uint32_t bit = 1u << (s & 31);
-                        const uint32_t *col = inj + (size_t)s * Wq;
-                        for (int w = warp; w < Wq; w += NW) {
-                            uint32_t m = col[w];
-                            while (m) {
-                                const int b = __ffs(m) - 1;
-                                m &= m - 1;
-                                if (w * 32 + b < n) v[(w * 32 + b) * 32 + lane] ^= bit;
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            pos += 2;
-        } else if (ev == EV_MRAND) {
+        if (ev == EV_MRAND) {
             const uint32_t p = min(log[pos + 1], (uint32_t)n - 1u), s = log[pos + 2], rec = log[pos + 3];
             const uint32_t vp = v[p * 32 + lane];
             e = (s >= lo && s < hi) ? (1u << (s & 31)) : 0u;
@@ -575,7 +603,6 @@ __global__ void __launch_bounds__(32 * NW) k_replay(const uint32_t *__restrict__
                 if (rec != NO_REC && write) A[(size_t)rec * apitch + g] = e;
                 __syncthreads();
             }
-            pos += 4 + cnt;
         } else if (ev == EV_MDET) {
             const uint32_t rec = log[pos + 1];
             const uint32_t m = share(cnt, j0);
@@ -586,7 +613,6 @@ __global__ void __launch_bounds__(32 * NW) k_replay(const uint32_t *__restrict__
             for (int w = 0; w < NW; w++) e ^= s_acc[w * 32 + lane];
             if (rec != NO_REC && write) A[(size_t)rec * apitch + g] = e;
             __syncthreads();   // the partials are reused by the next event
-            pos += 2 + cnt;
         } else if (ev == EV_FF) {
             // the record's symbol word for this lane: written earlier by
             // warp 0 (a barrier since), or still zero if the record precedes
@@ -598,14 +624,12 @@ __global__ void __launch_bounds__(32 * NW) k_replay(const uint32_t *__restrict__
                 replay_xor_rows(v, log + pos + 2 + j0, m, n, lane, ef);
                 __syncthreads();
             }
-            pos += 2 + cnt;
-        } else {
+        } else if (ev == EV_RESET) {
             if (__any_sync(0xffffffffu, e != 0u)) {
                 const uint32_t m = share(cnt, j0);
                 replay_xor_rows(v, log + pos + 1 + j0, m, n, lane, e);
                 __syncthreads();
             }
-            pos += 1 + cnt;
         }
     }
 }
@@ -1018,10 +1042,14 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
 
     Inst *d_insts; uint32_t *d_log, *d_inj, *d_sched; uint64_t *d_logpos; uint8_t *d_symrand, *d_recconst;
     TravStep *d_steps;
+    uint64_t *d_evpos;
     TraverseCounts *d_counts; uint32_t *d_gtab = nullptr;
     SP_TRY(tmp.alloc(&d_insts, F.insts.size()));
     SP_TRY(tmp.alloc(&d_sched, sched.size()));
     SP_TRY(tmp.alloc(&d_steps, steps.size()));
+    uint64_t ev_cap = 1;   // a barrier op logs at most two events (a measurement and its reset)
+    for (const TravStep &st : steps) ev_cap += st.barrier ? 2 : 0;
+    SP_TRY(tmp.alloc(&d_evpos, ev_cap));
     SP_TRY(tmp.alloc(&d_log, log_cap));
     SP_TRY(tmp.alloc(&d_inj, (size_t)(cap_sym + 2) * Wq));
     SP_TRY(tmp.alloc(&d_logpos, (size_t)cap_sym + 2));
@@ -1053,7 +1081,7 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     tp.gtab = d_gtab; tp.tab_in_smem = in_smem ? 1 : 0; tp.log = d_log; tp.log_cap = log_cap;
     tp.inj = d_inj; tp.sym_logpos = d_logpos; tp.sym_random = d_symrand;
     tp.chT = P->d_chT; tp.chKind = P->d_chKind; tp.chSym0 = P->d_chSym0; tp.chP = P->d_chP;
-    tp.rec_const = d_recconst; tp.counts = d_counts;
+    tp.rec_const = d_recconst; tp.counts = d_counts; tp.ev_pos = d_evpos; tp.ev_cap = ev_cap;
     k_traverse<<<1, TRAV_THREADS, smem, stream>>>(tp);
     SP_CUDA(cudaGetLastError());
     TraverseCounts hc;
@@ -1079,13 +1107,13 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
         if (n >= REPLAY_SPLIT_MIN_N) {
             const size_t vsm = ((size_t)n + 8) * 32 * 4;
             SP_CUDA(max_dynamic_smem(k_replay<8>));
-            k_replay<8><<<(unsigned)nblk, 256, vsm, stream>>>(d_log, hc.log_len, d_inj, Wq, d_logpos,
-                                                               hc.nsym, n, P->d_A, P->apitch);
+            k_replay<8><<<(unsigned)nblk, 256, vsm, stream>>>(d_log, hc.log_len, d_evpos, hc.nev, d_inj, Wq, d_logpos,
+                                                               d_symrand, hc.nsym, n, P->d_A, P->apitch);
         } else {
             const size_t vsm = ((size_t)n + 1) * 32 * 4;
             SP_CUDA(max_dynamic_smem(k_replay<1>));
-            k_replay<1><<<(unsigned)nblk, 32, vsm, stream>>>(d_log, hc.log_len, d_inj, Wq, d_logpos,
-                                                              hc.nsym, n, P->d_A, P->apitch);
+            k_replay<1><<<(unsigned)nblk, 32, vsm, stream>>>(d_log, hc.log_len, d_evpos, hc.nev, d_inj, Wq, d_logpos,
+                                                              d_symrand, hc.nsym, n, P->d_A, P->apitch);
         }
         SP_CUDA(cudaGetLastError());
     }

@@ -55,7 +55,8 @@ struct TraverseCounts {
     uint32_t nch;
     uint32_t nrec;
     uint32_t err;      // 0 ok, 1 log overflow, 2 nondeterministic product phase
-    uint32_t pad[2];
+    uint32_t nev;      // events other than injections (their positions: ev_pos)
+    uint32_t pad;
 };
 
 // ----------------------------------------------------------------------------
