@@ -139,11 +139,14 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int n = P.n, SW = P.SW;
     uint32_t *tab = P.tab_in_smem ? tsm : P.gtab;
-    auto col = [&](int q) { return tab + (size_t)q * 4 * SW; };
+    // a qubit's four bit-vectors plus one pad word: an odd stride, so that
+    // threads reading one word of consecutive qubits hit distinct banks
+    const int QSTR = 4 * SW + 1;
+    auto col = [&](int q) { return tab + (size_t)q * QSTR; };
 
     // stabilizer i = Z_i, destabilizer i = X_i, phases 0
-    for (int64_t i = t; i < (int64_t)n * 4 * SW; i += TRAV_THREADS) {
-        const int q = (int)(i / (4 * SW)), k = (int)((i / SW) % 4), w = (int)(i % SW);
+    for (int64_t i = t; i < (int64_t)n * QSTR; i += TRAV_THREADS) {
+        const int q = (int)(i / QSTR), r = (int)(i % QSTR), k = r / SW, w = r % SW;
         tab[i] = ((k == TAB_ZS || k == TAB_XD) && w == (q >> 5)) ? 1u << (q & 31) : 0u;
     }
     if (t < 32) s_rs[t] = 0;
@@ -321,28 +324,47 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             uint32_t c0 = 0, c1 = 0;
             if (lane < SW) {
                 const uint32_t ms = s_m0[lane], md = s_m1[lane];
-                for (int q = warp; q < n; q += TRAV_THREADS / 32) {
-                    const uint32_t xq = (s_px[q >> 5] >> (q & 31)) & 1u, zq = (s_pz[q >> 5] >> (q & 31)) & 1u;
-                    if (!(xq | zq)) continue;
-                    uint32_t *cq = col(q);
-                    const uint32_t xs = cq[TAB_XS * SW + lane], zs = cq[TAB_ZS * SW + lane];
-                    const uint32_t X2 = xs & ~zs, Y2 = xs & zs, Z2 = zs & ~xs;
-                    // +1 for the pairs (pivot, row) = XY, YZ, ZX; -1 for YX, ZY, XZ
-                    uint32_t pos, neg;
-                    if (xq && !zq) { pos = Y2; neg = Z2; }
-                    else if (xq) { pos = Z2; neg = X2; }
-                    else { pos = X2; neg = Y2; }
-                    pos &= ms;
-                    neg &= ms;
-                    c1 ^= c0 & pos;
-                    c0 ^= pos;
-                    c1 ^= ~c0 & neg;
-                    c0 ^= neg;
-                    if (xq) cq[TAB_XS * SW + lane] = xs ^ ms;
-                    if (zq) cq[TAB_ZS * SW + lane] = zs ^ ms;
-                    if (md) {
-                        if (xq) cq[TAB_XD * SW + lane] ^= md;
-                        if (zq) cq[TAB_ZD * SW + lane] ^= md;
+                // four columns at a time: their words are read before any is
+                // written, so the loads overlap (distinct qubits never alias)
+                constexpr int QB = 4, QS = TRAV_THREADS / 32;
+                for (int q0 = warp; q0 < n; q0 += QB * QS) {
+                    uint32_t xq[QB], zq[QB], xs[QB], zs[QB], xd[QB], zd[QB];
+#pragma unroll
+                    for (int u = 0; u < QB; u++) {
+                        const int q = q0 + u * QS;
+                        xq[u] = q < n ? (s_px[q >> 5] >> (q & 31)) & 1u : 0u;
+                        zq[u] = q < n ? (s_pz[q >> 5] >> (q & 31)) & 1u : 0u;
+                        xs[u] = zs[u] = xd[u] = zd[u] = 0u;
+                        if (xq[u] | zq[u]) {
+                            const uint32_t *cq = col(q);
+                            xs[u] = cq[TAB_XS * SW + lane];
+                            zs[u] = cq[TAB_ZS * SW + lane];
+                            if (md && xq[u]) xd[u] = cq[TAB_XD * SW + lane];
+                            if (md && zq[u]) zd[u] = cq[TAB_ZD * SW + lane];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < QB; u++) {
+                        if (!(xq[u] | zq[u])) continue;
+                        const uint32_t X2 = xs[u] & ~zs[u], Y2 = xs[u] & zs[u], Z2 = zs[u] & ~xs[u];
+                        // +1 for the pairs (pivot, row) = XY, YZ, ZX; -1 for YX, ZY, XZ
+                        uint32_t pos, neg;
+                        if (xq[u] && !zq[u]) { pos = Y2; neg = Z2; }
+                        else if (xq[u]) { pos = Z2; neg = X2; }
+                        else { pos = X2; neg = Y2; }
+                        pos &= ms;
+                        neg &= ms;
+                        c1 ^= c0 & pos;
+                        c0 ^= pos;
+                        c1 ^= ~c0 & neg;
+                        c0 ^= neg;
+                        uint32_t *cq = col(q0 + u * QS);
+                        if (xq[u]) cq[TAB_XS * SW + lane] = xs[u] ^ ms;
+                        if (zq[u]) cq[TAB_ZS * SW + lane] = zs[u] ^ ms;
+                        if (md) {
+                            if (xq[u]) cq[TAB_XD * SW + lane] = xd[u] ^ md;
+                            if (zq[u]) cq[TAB_ZD * SW + lane] = zd[u] ^ md;
+                        }
                     }
                 }
             }
@@ -1068,9 +1090,10 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     SP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(TraverseCounts), stream));
     SP_CUDA(cudaMemsetAsync(d_recconst, 0, (size_t)F.nmeas + 1, stream));
 
-    // the tableau (4 bit-vectors of n rows per qubit) in shared memory when
-    // it fits next to the kernel's 9 KB of static shared memory
-    const size_t tab_words = 4 * (size_t)std::max(n, 1) * Wq;
+    // the tableau (4 bit-vectors of n rows per qubit, plus a pad word) in
+    // shared memory when it fits next to the kernel's 9 KB of static shared
+    // memory
+    const size_t tab_words = (size_t)std::max(n, 1) * (4 * (size_t)Wq + 1);
     const bool in_smem = tab_words * 4 <= 200 * 1024;
     if (!in_smem) SP_TRY(tmp.alloc(&d_gtab, tab_words));
     const size_t smem = in_smem ? tab_words * 4 : 0;
