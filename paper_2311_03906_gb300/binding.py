@@ -125,13 +125,15 @@ def _circuit_struct(circuit):
         circuit = Circuit.from_text(circuit)
     keep = []
     ops = (sp_op * max(1, len(circuit.ops)))()
+    p32 = C.POINTER(C.c_uint32)
     for i, op in enumerate(circuit.ops):
-        arr = (C.c_uint32 * max(1, len(op.targets)))(*op.targets)
+        arr = np.asarray(op.targets, dtype=np.uint32) if len(op.targets) else np.zeros(1, np.uint32)
         keep.append(arr)
-        ops[i].opcode = OPCODES[op.name]
-        ops[i].ntargets = len(op.targets)
-        ops[i].targets = C.cast(arr, C.POINTER(C.c_uint32))
-        ops[i].arg = float(op.arg)
+        o = ops[i]
+        o.opcode = OPCODES[op.name]
+        o.ntargets = len(op.targets)
+        o.targets = arr.ctypes.data_as(p32)
+        o.arg = float(op.arg)
     desc = sp_circuit_desc(circuit.num_qubits, len(circuit.ops), C.cast(ops, C.POINTER(sp_op)))
     return desc, (ops, keep)
 
