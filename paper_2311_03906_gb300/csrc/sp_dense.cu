@@ -95,17 +95,18 @@ __global__ void __launch_bounds__(256) k_popc_product(const uint32_t *__restrict
 // ---------------------------------------------------------------------------
 // Tensor-core product (tcgen05, kind::f8f6f4, E4M3 operands, FP32 in TMEM)
 // ---------------------------------------------------------------------------
-// Tile: M = 128 shots x N = 128 record rows of one record kind, K in stages of
-// TC_KS = 192 symbols held in a ring of TC_NS stage buffers.  Operands are
+// Tile: M = 128 shots x N = 256 record rows of one record kind, K in stages of
+// TC_KS = 128 symbols held in a ring of TC_NS stage buffers.  Operands are
 // K-major with no swizzle, in 8-row x 16-byte core matrices; in a stage
 // buffer the core matrix (row group rg, K group kg) sits at
-// kg * TC_LBO + rg * TC_SBO (16 row groups x 12 K groups).
-constexpr int TC_M = 128, TC_N = 128, TC_KS = 192, TC_NS = 4;
+// kg * LBO + rg * TC_SBO, LBO = (rows / 8) * 128 bytes.
+constexpr int TC_M = 128, TC_N = 256, TC_KS = 128, TC_NS = 4;
 constexpr int TC_EXPANDERS = 256, TC_THREADS = TC_EXPANDERS + 32;   // 8 expander warps + 1 issuer warp
-constexpr uint32_t TC_STAGE_BYTES = TC_M * TC_KS;                  // 24 KB per operand
-constexpr uint32_t TC_LBO = 16 * 128, TC_SBO = 128;
+constexpr uint32_t TC_ABYTES = TC_M * TC_KS;                       // 16 KB: shots x symbols
+constexpr uint32_t TC_BBYTES = TC_N * TC_KS;                       // 32 KB: rows x symbols
+constexpr uint32_t TC_SBO = 128, TC_ALBO = (TC_M / 8) * 128, TC_BLBO = (TC_N / 8) * 128;
 constexpr int TC_KG = TC_KS / 16;                                    // K groups per stage
-constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr uint32_t TC_TMEM_COLS = TC_N;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;                      // 2 s bound on every wait
 constexpr uint32_t E4M3_ONE = 0x38u;
 
@@ -230,12 +231,12 @@ __global__ void k_coef_e4m3(const uint32_t *__restrict__ A, int64_t apitch, int6
                             int64_t ntiles, int64_t nks, uint4 *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t per_block = TC_STAGE_BYTES / 16;
+    const int64_t per_block = TC_BBYTES / 16;
     if (i >= ntiles * nks * per_block) return;
     const int64_t blk = i / per_block;
     const uint32_t c = (uint32_t)(i % per_block);   // byte offset c*16 = kg*LBO + rg*SBO + r8*16
     const int64_t tile = blk / nks, ks = blk % nks;
-    const uint32_t kg = c >> 7, rg = (c >> 3) & 15u, r8 = c & 7u;
+    const uint32_t kg = c / TC_N, rg = (c >> 3) % (TC_N / 8), r8 = c & 7u;
     const int64_t r = tile * TC_N + rg * 8 + r8;
     const int64_t w = ks * (TC_KS / 32) + (kg >> 1);
     uint32_t h = 0;
@@ -264,8 +265,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t *Abuf = sm;                                        // TC_NS stage buffers
-    uint8_t *Bbuf = sm + TC_NS * TC_STAGE_BYTES;               // TC_NS stage buffers
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * TC_NS * TC_STAGE_BYTES);   // full, afull, done [NS]
+    uint8_t *Bbuf = sm + TC_NS * TC_ABYTES;                    // TC_NS stage buffers
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + TC_NS * (TC_ABYTES + TC_BBYTES));   // full, afull, done [NS]
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 3 * TC_NS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -325,24 +326,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int j = 0; j < NW; j++) v[j] = vn[j];
             if (ks + 1 < nks) load_words(ks + 1);
-            uint8_t *Ab = Abuf + b * TC_STAGE_BYTES;
+            uint8_t *Ab = Abuf + b * TC_ABYTES;
 #pragma unroll
             for (int j = 0; j < NW; j++) {
                 const uint32_t kg = kgb + 2u * (uint32_t)j;
-                *reinterpret_cast<uint4 *>(Ab + kg * TC_LBO + a_off) = bits16_to_e4m3(v[j] & 0xFFFFu);
-                *reinterpret_cast<uint4 *>(Ab + (kg + 1u) * TC_LBO + a_off) = bits16_to_e4m3(v[j] >> 16);
+                *reinterpret_cast<uint4 *>(Ab + kg * TC_ALBO + a_off) = bits16_to_e4m3(v[j] & 0xFFFFu);
+                *reinterpret_cast<uint4 *>(Ab + (kg + 1u) * TC_ALBO + a_off) = bits16_to_e4m3(v[j] >> 16);
             }
             fence_proxy_async_smem();
             mbar_arrive(afull + 8 * b);
         }
     } else if (lane == 0) {
         // ---- issuer
-        const uint4 *cblk = coef + (size_t)nt * (size_t)nks * (TC_STAGE_BYTES / 16);
+        const uint4 *cblk = coef + (size_t)nt * (size_t)nks * (TC_BBYTES / 16);
         auto prefetch = [&](int64_t j) {
             const int jb = (int)(j % TC_NS);
-            mbar_expect_tx(full + 8 * jb, TC_STAGE_BYTES);
-            bulk_g2s(smem_u32(Bbuf + jb * TC_STAGE_BYTES), cblk + (size_t)j * (TC_STAGE_BYTES / 16), TC_STAGE_BYTES,
-                     full + 8 * jb);
+            mbar_expect_tx(full + 8 * jb, TC_BBYTES);
+            bulk_g2s(smem_u32(Bbuf + jb * TC_BBYTES), cblk + (size_t)j * (TC_BBYTES / 16), TC_BBYTES, full + 8 * jb);
             copied = j + 1;
         };
         for (int64_t j = 0; j < TC_NS - 1 && j < nks; j++) prefetch(j);
@@ -357,11 +357,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             landed = ks + 1;
             tc_fence_after();
-            const uint32_t a0 = smem_u32(Abuf + b * TC_STAGE_BYTES), b0 = smem_u32(Bbuf + b * TC_STAGE_BYTES);
+            const uint32_t a0 = smem_u32(Abuf + b * TC_ABYTES), b0 = smem_u32(Bbuf + b * TC_BBYTES);
 #pragma unroll
             for (int s = 0; s < TC_KS / 32; s++)
-                tc_mma(tmem, smem_desc(a0 + (uint32_t)s * 2u * TC_LBO, TC_LBO, TC_SBO),
-                       smem_desc(b0 + (uint32_t)s * 2u * TC_LBO, TC_LBO, TC_SBO), (ks > 0 || s > 0) ? 1u : 0u);
+                tc_mma(tmem, smem_desc(a0 + (uint32_t)s * 2u * TC_ALBO, TC_ALBO, TC_SBO),
+                       smem_desc(b0 + (uint32_t)s * 2u * TC_BLBO, TC_BLBO, TC_SBO), (ks > 0 || s > 0) ? 1u : 0u);
             tc_commit(done + 8 * b);
             issued = ks + 1;
             // stage ks + TC_NS - 1 reuses the buffers of stage ks - 1 once its MMAs are done;
@@ -388,17 +388,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool all_ok = !__syncthreads_or(failed || *abort_flag);
     if (all_ok && !issuer_warp) {
         tc_fence_after();
+        // warp: TMEM lanes 32*qw.. (its shots), columns (rows) half*TC_N/2..
         const int qw = warp & 3, half = warp >> 2;
-        const uint32_t taddr = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(64 * half);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(half * (TC_N / 2));
         const uint64_t shot = (uint64_t)m0 + (uint64_t)(32 * qw + lane);
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
+        for (int c = 0; c < TC_N / 64; c++) {
             uint32_t v[32];
             tc_ld32(taddr + 32u * (uint32_t)c, v);
             uint32_t word = 0;
 #pragma unroll
             for (int k = 0; k < 32; k++) word |= (__float2uint_rz(__uint_as_float(v[k])) & 1u) << k;
-            const int64_t q = nt * (TC_N / 32) + half * 2 + c;
+            const int64_t q = nt * (TC_N / 32) + half * (TC_N / 64) + c;
             if (shot < nshots && q < words32) out[shot * (uint64_t)words32 + (uint64_t)q] = word;
         }
     } else if (!all_ok && tid == 0) {
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // TC_NS stage buffers per operand, alignment, barriers and the TMEM address.
-constexpr size_t TC_SMEM = 2 * TC_NS * (size_t)TC_STAGE_BYTES + 1024 + 24 * TC_NS + 16;
+constexpr size_t TC_SMEM = TC_NS * (size_t)(TC_ABYTES + TC_BBYTES) + 1024 + 24 * TC_NS + 16;
 
 }  // namespace
 
@@ -468,7 +469,7 @@ static sp_status ensure_tensor(sp_program *P, cudaStream_t s)
         cudaFree(P->d_tc_coef[k]);
         P->d_tc_coef[k] = nullptr;
         if (!P->tc_ntiles[k]) continue;
-        const int64_t chunks = P->tc_ntiles[k] * P->tc_nks * (TC_STAGE_BYTES / 16);
+        const int64_t chunks = P->tc_ntiles[k] * P->tc_nks * (TC_BBYTES / 16);
         if (cudaMalloc((void **)&P->d_tc_coef[k], (size_t)chunks * 16) != cudaSuccess) {
             cudaGetLastError();
             P->d_tc_coef[k] = nullptr;
