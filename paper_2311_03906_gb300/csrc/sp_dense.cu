@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_popc_product(const uint32_t *__restrict
 // K-major with no swizzle, in 8-row x 16-byte core matrices; in a stage
 // buffer the core matrix (row group rg, K group kg) sits at
 // kg * LBO + rg * TC_SBO, LBO = (rows / 8) * 128 bytes.
-constexpr int TC_M = 128, TC_N = 256, TC_KS = 128, TC_NS = 4;
+constexpr int TC_M = 128, TC_N = 256, TC_KS = 192, TC_NS = 3;
 constexpr int TC_EXPANDERS = 256, TC_THREADS = TC_EXPANDERS + 32;   // 8 expander warps + 1 issuer warp
 constexpr uint32_t TC_ABYTES = TC_M * TC_KS;                       // 16 KB: shots x symbols
 constexpr uint32_t TC_BBYTES = TC_N * TC_KS;                       // 32 KB: rows x symbols
