@@ -21,6 +21,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "sp_internal.h"
 
 namespace sp {
@@ -81,6 +83,7 @@ struct TravParams {
     uint64_t *ev_pos;        // log positions of the events other than injections
     uint64_t ev_cap;
     TraverseCounts *counts;
+    int qp;                  // qubits per CTA of a cluster
 };
 
 constexpr int TAB_XS = 0, TAB_ZS = 1, TAB_XD = 2, TAB_ZD = 3;
@@ -127,37 +130,76 @@ __device__ __forceinline__ uint32_t write_rows(uint32_t *dst, uint32_t m, int la
 // whole columns.  Gates and injections arrive in groups on disjoint qubits,
 // one op per warp at a time with lane = row word; a gate's phase flips stay
 // in the lane's register until the next barrier.  Measurements, resets and
-// feed-forward ops are barriers run by the whole CTA.  Requires n <= 1024.
+// feed-forward ops are barriers.
+//
+// CL > 1: a cluster of CL CTAs, CTA r holding the columns of qubits
+// [r*QP, (r+1)*QP) in its shared memory (other CTAs' columns through
+// distributed shared memory).  Each CTA applies the ops on its own qubits and
+// the row operations of a measurement to its own columns; rank 0 keeps the
+// phases (changed only by atomic XORs), combines the CTAs' partial phase
+// counts and writes the log.  Values every CTA needs (the pivot, the row
+// masks and their counts) are computed by each from the measured column, so
+// all CTAs keep the same log position.  Requires n <= 1024.
+template <int CL>
 __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
 {
     extern __shared__ __align__(16) uint32_t tsm[];
     __shared__ uint32_t s_rs[32], s_m0[32], s_m1[32], s_px[32], s_pz[32];
     __shared__ uint32_t s_c0[32 * 32], s_c1[32 * 32];
+    __shared__ uint32_t s_gc0[CL * 32], s_gc1[CL * 32];   // rank 0: the CTAs' phase counts
+    __shared__ int s_gG[CL];                              // rank 0: the CTAs' power-of-i sums
     __shared__ int s_red[32];
     __shared__ int s_p, s_e, s_err;
     __shared__ uint32_t s_cnt;
+    namespace cg = cooperative_groups;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int n = P.n, SW = P.SW;
-    uint32_t *tab = P.tab_in_smem ? tsm : P.gtab;
     // a qubit's four bit-vectors plus one pad word: an odd stride, so that
     // threads reading one word of consecutive qubits hit distinct banks
     const int QSTR = 4 * SW + 1;
-    auto col = [&](int q) { return tab + (size_t)q * QSTR; };
+    int rank = 0, q0 = 0, nq = n;
+    uint32_t *tab = P.tab_in_smem ? tsm : P.gtab;
+    if constexpr (CL > 1) {
+        rank = (int)cg::this_cluster().block_rank();
+        q0 = rank * P.qp;
+        nq = max(0, min(P.qp, n - q0));
+        tab = tsm;
+    }
+    // rank 0's copy of a shared array (this CTA's own for CL = 1)
+    auto at0 = [&](auto *x) {
+        if constexpr (CL > 1) return cg::this_cluster().map_shared_rank(x, 0);
+        else return x;
+    };
+    auto csync = [&]() {
+        if constexpr (CL > 1) cg::this_cluster().sync();
+        else __syncthreads();
+    };
+    // column of qubit q (in another CTA's shared memory for CL > 1)
+    auto col = [&](int q) -> uint32_t * {
+        if constexpr (CL > 1) {
+            const int o = q / P.qp;
+            uint32_t *base = o == rank ? tsm : cg::this_cluster().map_shared_rank(tsm, o);
+            return base + (size_t)(q - o * P.qp) * QSTR;
+        } else {
+            return tab + (size_t)q * QSTR;
+        }
+    };
+    auto own = [&](int q) { return CL == 1 || q / P.qp == rank; };
 
     // stabilizer i = Z_i, destabilizer i = X_i, phases 0
-    for (int64_t i = t; i < (int64_t)n * QSTR; i += TRAV_THREADS) {
-        const int q = (int)(i / QSTR), r = (int)(i % QSTR), k = r / SW, w = r % SW;
+    for (int64_t i = t; i < (int64_t)nq * QSTR; i += TRAV_THREADS) {
+        const int q = q0 + (int)(i / QSTR), r = (int)(i % QSTR), k = r / SW, w = r % SW;
         tab[i] = ((k == TAB_ZS || k == TAB_XD) && w == (q >> 5)) ? 1u << (q & 31) : 0u;
     }
     if (t < 32) s_rs[t] = 0;
     if (t == 0) s_err = 0;
-    __syncthreads();
+    csync();
 
     uint32_t rd = 0;                     // this lane's pending phase flips
     uint32_t nrand = 0, nrec = 0, inj_mark = 0, err = 0, nev = 0;
     // every event other than an injection is also listed by position
     auto note_event = [&](uint64_t at) {
-        if (t == 0 && nev < P.ev_cap) P.ev_pos[nev] = at;
+        if (t == 0 && rank == 0 && nev < P.ev_cap) P.ev_pos[nev] = at;
         nev++;
     };
     uint64_t lp = 0;                     // log position after the last barrier's event
@@ -167,6 +209,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             for (uint32_t k = S.begin + (uint32_t)warp; k < S.end; k += TRAV_THREADS / 32) {
                 const Inst in = P.insts[P.sched[k]];
                 const uint32_t code = in.code;
+                if (!own((int)in.a)) continue;
                 if (code <= I_Z) {
                     if (lane >= SW) continue;
                     uint32_t *ca = col((int)in.a);
@@ -238,20 +281,20 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                     P.log[slot + 1] = s0;
                 }
             }
-            __syncthreads();
+            csync();
             continue;
         }
         // ---- barrier op ------------------------------------------------------
         lp += 2ull * (S.inj_before - inj_mark);   // the segment's injection events
         inj_mark = S.inj_before;
-        if (lane < SW && rd) atomicXor(&s_rs[lane], rd);
+        if (lane < SW && rd) atomicXor(at0(s_rs) + lane, rd);
         rd = 0;
         const Inst in = P.insts[P.sched[S.begin]];
         const uint32_t code = in.code;
         const int a = (int)in.a;
         if (lp + 2 * (uint64_t)n + 8 > P.log_cap || nev + 2 > P.ev_cap) { err = 1; break; }
-        __syncthreads();   // phases flushed, the group's columns written
-        uint32_t *ca = col(a);
+        csync();   // phases flushed, the groups' columns written
+        const uint32_t *ca = col(a);
         if (code >= I_XIF) {
             // Feed-forward (the conditional Paulis of Sec. 6): P^e on qubit a
             // with e the form of record in.b.  A stabilizer that
@@ -264,17 +307,21 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                     if (useZ) m ^= ca[TAB_ZS * SW + lane];
                     if (useX) m ^= ca[TAB_XS * SW + lane];
                 }
-                const uint32_t total = write_rows(P.log + lp + 2, m, lane);
-                if (P.rec_const[in.b] && lane < SW) s_rs[lane] ^= m;
-                if (lane == 0) {
-                    P.log[lp] = (EV_FF << 24) | total;
-                    P.log[lp + 1] = in.b;
-                    s_cnt = total;
+                const uint32_t total = (uint32_t)warp_sum(__popc(m));
+                if (rank == 0) {
+                    write_rows(P.log + lp + 2, m, lane);
+                    if (P.rec_const[in.b] && m) atomicXor(&s_rs[lane], m);
+                    if (lane == 0) {
+                        P.log[lp] = (EV_FF << 24) | total;
+                        P.log[lp + 1] = in.b;
+                    }
                 }
+                if (lane == 0) s_cnt = total;
             }
             __syncthreads();
             note_event(lp);
             lp += 2 + (uint64_t)s_cnt;
+            csync();   // rank 0 has read the column before the next step changes it
             continue;
         }
         // ---- Init-M (M, MR, R) -----------------------------------------------
@@ -293,7 +340,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
         }
         __syncthreads();
         const int p = s_p;
-        uint32_t e_const;
+        uint32_t e_const = 0;
         if (p >= 0) {
             // random outcome: every other row with x_a = 1 becomes P_p * row
             const int wp = p >> 5;
@@ -303,10 +350,10 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 s_m1[lane] = ca[TAB_XD * SW + lane];                                // destabilizers
             }
             {
-                // the pivot stabilizer, one bit per qubit
+                // the pivot stabilizer on this CTA's qubits, one bit per qubit
                 uint32_t xp = 0, zp = 0;
-                if (t < n) {
-                    const uint32_t *cq = col(t);
+                if (t < nq) {
+                    const uint32_t *cq = tab + (size_t)t * QSTR;
                     xp = (cq[TAB_XS * SW + wp] & bp) ? 1u : 0u;
                     zp = (cq[TAB_ZS * SW + wp] & bp) ? 1u : 0u;
                 }
@@ -316,27 +363,28 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                     s_pz[warp] = bz;
                 }
             }
-            const uint32_t rp = (s_rs[wp] & bp) ? 1u : 0u;
-            __syncthreads();
-            // Rowsum of every masked row with the pivot, one column per warp at
-            // a time.  For the stabilizer rows, A-G's power of i (g summed
-            // over the qubits) is counted mod 4 in bit-sliced form (c1 c0).
+            const uint32_t rp = (rank == 0 && (s_rs[wp] & bp)) ? 1u : 0u;
+            csync();   // every CTA has read the measured column
+            // Rowsum of every masked row with the pivot on this CTA's columns,
+            // one column per warp at a time.  For the stabilizer rows, A-G's
+            // power of i (g summed over the qubits) is counted mod 4 in
+            // bit-sliced form (c1 c0).
             uint32_t c0 = 0, c1 = 0;
             if (lane < SW) {
                 const uint32_t ms = s_m0[lane], md = s_m1[lane];
-                // four columns at a time: their words are read before any is
+                // two columns at a time: their words are read before any is
                 // written, so the loads overlap (distinct qubits never alias)
-                constexpr int QB = 4, QS = TRAV_THREADS / 32;
-                for (int q0 = warp; q0 < n; q0 += QB * QS) {
+                constexpr int QB = 2, QS = TRAV_THREADS / 32;
+                for (int l0 = warp; l0 < nq; l0 += QB * QS) {
                     uint32_t xq[QB], zq[QB], xs[QB], zs[QB], xd[QB], zd[QB];
 #pragma unroll
                     for (int u = 0; u < QB; u++) {
-                        const int q = q0 + u * QS;
-                        xq[u] = q < n ? (s_px[q >> 5] >> (q & 31)) & 1u : 0u;
-                        zq[u] = q < n ? (s_pz[q >> 5] >> (q & 31)) & 1u : 0u;
+                        const int l = l0 + u * QS;
+                        xq[u] = l < nq ? (s_px[l >> 5] >> (l & 31)) & 1u : 0u;
+                        zq[u] = l < nq ? (s_pz[l >> 5] >> (l & 31)) & 1u : 0u;
                         xs[u] = zs[u] = xd[u] = zd[u] = 0u;
                         if (xq[u] | zq[u]) {
-                            const uint32_t *cq = col(q);
+                            const uint32_t *cq = tab + (size_t)l * QSTR;
                             xs[u] = cq[TAB_XS * SW + lane];
                             zs[u] = cq[TAB_ZS * SW + lane];
                             if (md && xq[u]) xd[u] = cq[TAB_XD * SW + lane];
@@ -358,7 +406,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                         c0 ^= pos;
                         c1 ^= ~c0 & neg;
                         c0 ^= neg;
-                        uint32_t *cq = col(q0 + u * QS);
+                        uint32_t *cq = tab + (size_t)(l0 + u * QS) * QSTR;
                         if (xq[u]) cq[TAB_XS * SW + lane] = xs[u] ^ ms;
                         if (zq[u]) cq[TAB_ZS * SW + lane] = zs[u] ^ ms;
                         if (md) {
@@ -372,29 +420,42 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             s_c1[warp * 32 + lane] = c1;
             __syncthreads();
             // destabilizer p := the old stabilizer p; stabilizer p := Z_a
-            if (t < n) {
-                uint32_t *cq = col(t);
+            if (t < nq) {
+                uint32_t *cq = tab + (size_t)t * QSTR;
                 const bool xp = (s_px[t >> 5] >> (t & 31)) & 1u, zp = (s_pz[t >> 5] >> (t & 31)) & 1u;
                 cq[TAB_XD * SW + wp] = (cq[TAB_XD * SW + wp] & ~bp) | (xp ? bp : 0u);
                 cq[TAB_ZD * SW + wp] = (cq[TAB_ZD * SW + wp] & ~bp) | (zp ? bp : 0u);
                 cq[TAB_XS * SW + wp] &= ~bp;
-                cq[TAB_ZS * SW + wp] = (cq[TAB_ZS * SW + wp] & ~bp) | (t == a ? bp : 0u);
+                cq[TAB_ZS * SW + wp] = (cq[TAB_ZS * SW + wp] & ~bp) | (q0 + t == a ? bp : 0u);
             }
             if (warp == 0) {
+                // this CTA's mod-4 counts, to rank 0
                 uint32_t a0 = 0, a1 = 0;
                 for (int w = 0; w < TRAV_THREADS / 32; w++) {
                     const uint32_t b0 = s_c0[w * 32 + lane], b1 = s_c1[w * 32 + lane];
                     a1 ^= b1 ^ (a0 & b0);
                     a0 ^= b0;
                 }
+                at0(s_gc0)[rank * 32 + lane] = a0;
+                at0(s_gc1)[rank * 32 + lane] = a1;
+                const uint32_t ms = lane < SW ? s_m0[lane] : 0u;
+                const uint32_t total = (uint32_t)warp_sum(__popc(ms));
+                if (lane == 0) s_cnt = total;
+            }
+            csync();   // the counts gathered, every column written
+            if (rank == 0 && warp == 0) {
+                uint32_t a0 = 0, a1 = 0;
+                for (int r = 0; r < CL; r++) {
+                    const uint32_t b0 = s_gc0[r * 32 + lane], b1 = s_gc1[r * 32 + lane];
+                    a1 ^= b1 ^ (a0 & b0);
+                    a0 ^= b0;
+                }
                 const uint32_t ms = lane < SW ? s_m0[lane] : 0u;
                 if (a0 & ms) s_err = 2;
-                if (lane < SW) {
-                    // new r = r ^ r_p ^ (power of i) / 2 on the masked rows
-                    uint32_t r = s_rs[lane] ^ (ms & (a1 ^ (rp ? FULL : 0u)));
-                    if (lane == wp) r &= ~bp;
-                    s_rs[lane] = r;
-                }
+                // new r = r ^ r_p ^ (power of i) / 2 on the masked rows; r_p := 0
+                uint32_t flip = ms & (a1 ^ (rp ? FULL : 0u));
+                if (lane == wp && rp) flip ^= bp;
+                if (lane < SW && flip) atomicXor(&s_rs[lane], flip);
                 const uint32_t total = write_rows(P.log + lp + 4, ms, lane);
                 if (lane == 0) {
                     const uint32_t s = 1u + S.fsym_before + nrand, ch = S.inj_before + nrand;
@@ -408,14 +469,11 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                     P.chSym0[ch] = s;
                     P.sym_logpos[s] = lp;
                     P.sym_random[s] = 1;
-                    s_cnt = total;
                 }
             }
-            __syncthreads();
             note_event(lp);
             lp += 4 + (uint64_t)s_cnt;
             nrand++;
-            e_const = 0;
         } else {
             // deterministic outcome: the product of the stabilizers paired with
             // destabilizers that have x_a = 1.  Its power of i is a sum over
@@ -425,8 +483,8 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             if (warp == 0 && lane < SW) s_m1[lane] = ca[TAB_XD * SW + lane];
             __syncthreads();
             int G = 0;
-            if (t < n) {
-                const uint32_t *cq = col(t);
+            if (t < nq) {
+                const uint32_t *cq = tab + (size_t)t * QSTR;
                 uint32_t cx = 0, cz = 0;
                 for (int w = 0; w < SW; w++) {
                     const uint32_t d = s_m1[w];
@@ -444,53 +502,69 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             if (lane == 0) s_red[warp] = G;
             __syncthreads();
             if (warp == 0) {
+                const int g = warp_sum(s_red[lane]);
                 const uint32_t d = lane < SW ? s_m1[lane] : 0u;
-                const int g = warp_sum(s_red[lane]) + 2 * warp_sum(__popc(lane < SW ? (s_rs[lane] & d) : 0u));
-                const uint32_t total = write_rows(P.log + lp + 2, d, lane);
+                const uint32_t total = (uint32_t)warp_sum(__popc(d));
+                if (lane == 0) {
+                    at0(s_gG)[rank] = g;
+                    s_cnt = total;
+                }
+            }
+            csync();   // the sums gathered
+            if (rank == 0 && warp == 0) {
+                const uint32_t d = lane < SW ? s_m1[lane] : 0u;
+                const int g = warp_sum(lane < CL ? s_gG[lane] : 0) +
+                              2 * warp_sum(__popc(lane < SW ? (s_rs[lane] & d) : 0u));
+                write_rows(P.log + lp + 2, d, lane);
                 if (lane == 0) {
                     const int tot = g & 3;
                     s_e = (tot == 2) ? 1 : 0;
                     if (tot & 1) s_err = 2;
-                    P.log[lp] = (EV_MDET << 24) | total;
+                    P.log[lp] = (EV_MDET << 24) | s_cnt;
                     P.log[lp + 1] = rec;
-                    s_cnt = total;
                 }
             }
             __syncthreads();
             note_event(lp);
             lp += 2 + (uint64_t)s_cnt;
-            e_const = (uint32_t)s_e;
+            e_const = rank == 0 ? (uint32_t)s_e : 0u;
         }
         if (recorded) {
-            if (t == 0) P.rec_const[nrec] = (uint8_t)e_const;
+            if (t == 0 && rank == 0) P.rec_const[nrec] = (uint8_t)e_const;
             nrec++;
         }
         if (reset) {
             // conditional X^e on qubit a: flip every stabilizer with z_a = 1
             if (warp == 0) {
                 const uint32_t m = lane < SW ? ca[TAB_ZS * SW + lane] : 0u;
-                const uint32_t total = write_rows(P.log + lp + 1, m, lane);
-                if (e_const && lane < SW) s_rs[lane] ^= m;
-                if (lane == 0) {
-                    P.log[lp] = (EV_RESET << 24) | total;
-                    s_cnt = total;
+                const uint32_t total = (uint32_t)warp_sum(__popc(m));
+                if (rank == 0) {
+                    write_rows(P.log + lp + 1, m, lane);
+                    if (e_const && m) atomicXor(&s_rs[lane], m);
+                    if (lane == 0) P.log[lp] = (EV_RESET << 24) | total;
                 }
+                if (lane == 0) s_cnt = total;
             }
             __syncthreads();
             note_event(lp);
             lp += 1 + (uint64_t)s_cnt;
         }
+        csync();   // the next step starts when every CTA is done with this one
     }
     if (!err) lp += 2ull * (P.ninj_total - inj_mark);   // the last segment's injections
-    __syncthreads();
-    if (t == 0) {
+    csync();
+    if (t == 0 && rank == 0) {
+        uint32_t e2 = (uint32_t)s_err;
+        if constexpr (CL > 1)
+            for (int r = 1; r < CL; r++) e2 = max(e2, (uint32_t)*cg::this_cluster().map_shared_rank(&s_err, r));
         P.counts->log_len = lp;
         P.counts->nsym = P.nfsym_total + nrand;
         P.counts->nch = P.ninj_total + nrand;
         P.counts->nrec = nrec;
         P.counts->nev = nev;
-        P.counts->err = err ? err : (uint32_t)s_err;
+        P.counts->err = err ? err : e2;
     }
+    csync();   // no CTA leaves while another may still read its shared memory
 }
 
 // v[i][lane] ^= x for the rows of one logged event.  The rows of an event
@@ -1090,22 +1164,59 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     SP_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(TraverseCounts), stream));
     SP_CUDA(cudaMemsetAsync(d_recconst, 0, (size_t)F.nmeas + 1, stream));
 
-    // the tableau (4 bit-vectors of n rows per qubit, plus a pad word) in
-    // shared memory when it fits next to the kernel's 9 KB of static shared
-    // memory
-    const size_t tab_words = (size_t)std::max(n, 1) * (4 * (size_t)Wq + 1);
-    const bool in_smem = tab_words * 4 <= 200 * 1024;
-    if (!in_smem) SP_TRY(tmp.alloc(&d_gtab, tab_words));
-    const size_t smem = in_smem ? tab_words * 4 : 0;
-    SP_CUDA(max_dynamic_smem(k_traverse));
+    // The tableau (4 bit-vectors of n rows per qubit, plus a pad word) lives
+    // in shared memory: one CTA's when it fits next to the kernel's static
+    // shared memory, else spread over a cluster of 2, 4 or 8 CTAs; global
+    // memory with one CTA if no cluster can be launched.
+    const size_t qbytes = (4 * (size_t)Wq + 1) * 4;
+    const size_t smem_cap = 192 * 1024;
+    int CL = 1, qp = std::max(n, 1);
+    if ((size_t)qp * qbytes > smem_cap) {
+        CL = 0;
+        for (int c : {2, 4, 8}) {
+            const int q = (n + c - 1) / c;
+            if ((size_t)q * qbytes <= smem_cap) { CL = c; qp = q; break; }
+        }
+    }
     TravParams tp;
     tp.insts = d_insts; tp.sched = d_sched; tp.steps = d_steps; tp.nsteps = (int64_t)steps.size();
     tp.ninj_total = ninj; tp.nfsym_total = nfsym; tp.n = n; tp.SW = Wq;
-    tp.gtab = d_gtab; tp.tab_in_smem = in_smem ? 1 : 0; tp.log = d_log; tp.log_cap = log_cap;
+    tp.gtab = nullptr; tp.tab_in_smem = 1; tp.log = d_log; tp.log_cap = log_cap;
     tp.inj = d_inj; tp.sym_logpos = d_logpos; tp.sym_random = d_symrand;
     tp.chT = P->d_chT; tp.chKind = P->d_chKind; tp.chSym0 = P->d_chSym0; tp.chP = P->d_chP;
     tp.rec_const = d_recconst; tp.counts = d_counts; tp.ev_pos = d_evpos; tp.ev_cap = ev_cap;
-    k_traverse<<<1, TRAV_THREADS, smem, stream>>>(tp);
+    tp.qp = qp;
+    bool launched = false;
+    if (CL > 1) {
+        const size_t smem = (size_t)qp * qbytes;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)CL);
+        cfg.blockDim = dim3(TRAV_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaSuccess;
+        if (CL == 2) { SP_CUDA(max_dynamic_smem(k_traverse<2>)); e = cudaLaunchKernelEx(&cfg, k_traverse<2>, tp); }
+        else if (CL == 4) { SP_CUDA(max_dynamic_smem(k_traverse<4>)); e = cudaLaunchKernelEx(&cfg, k_traverse<4>, tp); }
+        else { SP_CUDA(max_dynamic_smem(k_traverse<8>)); e = cudaLaunchKernelEx(&cfg, k_traverse<8>, tp); }
+        if (e == cudaSuccess) launched = true;
+        else cudaGetLastError();
+    }
+    if (!launched) {
+        const bool in_smem = CL == 1;
+        if (!in_smem) SP_TRY(tmp.alloc(&d_gtab, (size_t)std::max(n, 1) * (4 * (size_t)Wq + 1)));
+        tp.gtab = d_gtab;
+        tp.tab_in_smem = in_smem ? 1 : 0;
+        tp.qp = std::max(n, 1);
+        SP_CUDA(max_dynamic_smem(k_traverse<1>));
+        k_traverse<1><<<1, TRAV_THREADS, in_smem ? (size_t)std::max(n, 1) * qbytes : 0, stream>>>(tp);
+    }
     SP_CUDA(cudaGetLastError());
     TraverseCounts hc;
     SP_CUDA(cudaMemcpyAsync(&hc, d_counts, sizeof hc, cudaMemcpyDeviceToHost, stream));
