@@ -631,6 +631,9 @@ __global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restric
 {
     extern __shared__ uint32_t v[];  // [n][32], then [NW][32] partial XORs
     uint32_t *s_acc = v + (size_t)n * 32;
+    // the next 32 events: position and first four log words, loaded together
+    __shared__ uint64_t s_epos[32];
+    __shared__ uint4 s_ew[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * 32 + lane;
     const uint32_t blo = (uint32_t)blockIdx.x * 1024u, bhi = blo + 1024u;
@@ -648,6 +651,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restric
         const uint32_t mid = (k + khi) >> 1;
         if (ev_pos[mid] < p0) k = mid + 1; else khi = mid;
     }
+    const uint32_t khi0 = k;   // batches of 32 events start here
     uint32_t s_next = s_first;
     uint32_t e = 0;
     // this warp's contiguous share of an event's cnt rows
@@ -656,7 +660,26 @@ __global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restric
         return (uint32_t)((uint64_t)(warp + 1) * cnt / NW) - j0;
     };
     for (; k < nev; k++) {
-        const uint64_t pos = ev_pos[k];
+        const uint32_t kb = (k - khi0) & 31u;
+        if (kb == 0) {
+            __syncthreads();   // every warp is done with the previous batch
+            if (warp == 0) {
+                uint64_t ep = log_len;
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                if (k + lane < nev) {
+                    ep = ev_pos[k + lane];
+                    if (ep < log_len) w.x = log[ep];
+                    if (ep + 1 < log_len) w.y = log[ep + 1];
+                    if (ep + 2 < log_len) w.z = log[ep + 2];
+                    if (ep + 3 < log_len) w.w = log[ep + 3];
+                }
+                s_epos[lane] = ep;
+                s_ew[lane] = w;
+            }
+            __syncthreads();
+        }
+        const uint64_t pos = s_epos[kb];
+        const uint4 ew = s_ew[kb];
         if (pos >= log_len) break;
         // Init-P for this CTA's fault symbols injected before the event: lane
         // l takes its own symbols, warps split the rows of each column
@@ -679,7 +702,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restric
             }
             __syncthreads();
         }
-        const uint32_t h = log[pos];
+        const uint32_t h = ew.x;
         const uint32_t ev = h >> 24, cnt = h & 0xffffffu;
         // every event must fit in the log and name rows below n
         const uint64_t len = ev == EV_MRAND ? 4 + (uint64_t)cnt
@@ -687,7 +710,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restric
         if (pos + len > log_len) break;
         uint32_t j0;
         if (ev == EV_MRAND) {
-            const uint32_t p = min(log[pos + 1], (uint32_t)n - 1u), s = log[pos + 2], rec = log[pos + 3];
+            const uint32_t p = min(ew.y, (uint32_t)n - 1u), s = ew.z, rec = ew.w;
             const uint32_t vp = v[p * 32 + lane];
             e = (s >= lo && s < hi) ? (1u << (s & 31)) : 0u;
             // nothing to do when row p is zero and the new symbol is not ours
@@ -700,7 +723,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restric
                 __syncthreads();
             }
         } else if (ev == EV_MDET) {
-            const uint32_t rec = log[pos + 1];
+            const uint32_t rec = ew.y;
             const uint32_t m = share(cnt, j0);
             s_acc[warp * 32 + lane] = replay_xor_of_rows(v, log + pos + 2 + j0, m, n, lane);
             __syncthreads();
@@ -713,7 +736,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_replay(const uint32_t *__restric
             // the record's symbol word for this lane: written earlier by
             // warp 0 (a barrier since), or still zero if the record precedes
             // its symbols
-            const uint32_t rec = log[pos + 1];
+            const uint32_t rec = ew.y;
             const uint32_t ef = g < apitch ? A[(size_t)rec * apitch + g] : 0u;
             if (__any_sync(0xffffffffu, ef != 0u)) {
                 const uint32_t m = share(cnt, j0);
