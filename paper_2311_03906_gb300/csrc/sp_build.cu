@@ -854,14 +854,20 @@ __global__ void k_parent(const uint32_t *__restrict__ A, int64_t apitch, int64_t
     const uint32_t nj = nnz[j];
     int best = (int)nj, arg = -1;
     const int64_t i0 = j - lookback > 0 ? j - lookback : 0;
+    const uint32_t *rj = A + (size_t)j * apitch;
     for (int64_t i = i0 + threadIdx.x; i < j; i += blockDim.x) {
-        const uint32_t *ri = A + (size_t)i * apitch;
+        // overlap of the two supports, counted from the shorter one (reading
+        // the other row's bits)
+        const uint32_t ni = nnz[i];
+        const bool from_i = ni < nj;
+        const uint32_t *ro = from_i ? rj : A + (size_t)i * apitch;
+        const uint32_t kb = from_i ? off[i] : off[j], ke = from_i ? off[i + 1] : off[j + 1];
         int ov = 0;
-        for (uint32_t k = off[j]; k < off[j + 1]; k++) {
+        for (uint32_t k = kb; k < ke; k++) {
             const uint32_t s = idx[k] + 1u;
-            ov += (ri[s >> 5] >> (s & 31)) & 1u;
+            ov += (ro[s >> 5] >> (s & 31)) & 1u;
         }
-        const int d = (int)nnz[i] + (int)nj - 2 * ov;
+        const int d = (int)ni + (int)nj - 2 * ov;
         if (d < best || (d == best && arg >= 0 && i > arg)) { best = d; arg = (int)i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
