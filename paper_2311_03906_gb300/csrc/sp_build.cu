@@ -144,7 +144,7 @@ template <int CL>
 __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
 {
     extern __shared__ __align__(16) uint32_t tsm[];
-    __shared__ uint32_t s_rs[32], s_m0[32], s_m1[32], s_px[32], s_pz[32];
+    __shared__ uint32_t s_rs[32], s_m0[32], s_m1[32], s_za[32], s_px[32], s_pz[32];
     __shared__ uint32_t s_c0[32 * 32], s_c1[32 * 32];
     __shared__ uint32_t s_gc0[CL * 32], s_gc1[CL * 32];   // rank 0: the CTAs' phase counts
     __shared__ int s_gG[CL];                              // rank 0: the CTAs' power-of-i sums
@@ -285,6 +285,9 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             continue;
         }
         // ---- barrier op ------------------------------------------------------
+        // Every column is final here (the last group or barrier step ended
+        // with a cluster barrier).  Pending phase flips go to rank 0 now; rank
+        // 0 reads its phases only after the next cluster barrier.
         lp += 2ull * (S.inj_before - inj_mark);   // the segment's injection events
         inj_mark = S.inj_before;
         if (lane < SW && rd) atomicXor(at0(s_rs) + lane, rd);
@@ -293,8 +296,8 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
         const uint32_t code = in.code;
         const int a = (int)in.a;
         if (lp + 2 * (uint64_t)n + 8 > P.log_cap || nev + 2 > P.ev_cap) { err = 1; break; }
-        csync();   // phases flushed, the groups' columns written
-        const uint32_t *ca = col(a);
+        uint32_t *ca = col(a);
+        const bool own_a = own(a);
         if (code >= I_XIF) {
             // Feed-forward (the conditional Paulis of Sec. 6): P^e on qubit a
             // with e the form of record in.b.  A stabilizer that
@@ -321,14 +324,15 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             __syncthreads();
             note_event(lp);
             lp += 2 + (uint64_t)s_cnt;
-            csync();   // rank 0 has read the column before the next step changes it
+            csync();   // every CTA has read the column before the next step changes it
             continue;
         }
         // ---- Init-M (M, MR, R) -----------------------------------------------
         const bool recorded = (code != I_R), reset = (code != I_M);
         const uint32_t rec = recorded ? nrec : NO_REC;
         if (warp == 0) {
-            // the first stabilizer with x_a = 1, if any
+            // the measured column, read by every CTA before anyone changes it:
+            // the first stabilizer with x_a = 1 (if any), the row masks, z_a
             const uint32_t xw = lane < SW ? ca[TAB_XS * SW + lane] : 0u;
             const uint32_t bal = __ballot_sync(FULL, xw != 0u);
             int p = -1;
@@ -336,19 +340,21 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 const int L = __ffs(bal) - 1;
                 p = 32 * L + __ffs(__shfl_sync(FULL, xw, L)) - 1;
             }
+            s_m0[lane] = p >= 0 && lane == (p >> 5) ? xw & ~(1u << (p & 31)) : xw;   // stabilizers (random case)
+            s_m1[lane] = lane < SW ? ca[TAB_XD * SW + lane] : 0u;                     // destabilizers
+            s_za[lane] = lane < SW ? ca[TAB_ZS * SW + lane] : 0u;
             if (lane == 0) s_p = p;
         }
         __syncthreads();
         const int p = s_p;
         uint32_t e_const = 0;
+        uint32_t zpa = 0;   // z_a of the pivot (random outcomes)
         if (p >= 0) {
             // random outcome: every other row with x_a = 1 becomes P_p * row
             const int wp = p >> 5;
             const uint32_t bp = 1u << (p & 31);
-            if (warp == 0 && lane < SW) {
-                s_m0[lane] = ca[TAB_XS * SW + lane] & (lane == wp ? ~bp : FULL);   // stabilizers
-                s_m1[lane] = ca[TAB_XD * SW + lane];                                // destabilizers
-            }
+            zpa = (s_za[wp] & bp) ? 1u : 0u;
+            const int la = own_a ? a - q0 : -1;   // the measured column, if this CTA holds it
             {
                 // the pivot stabilizer on this CTA's qubits, one bit per qubit
                 uint32_t xp = 0, zp = 0;
@@ -363,12 +369,13 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                     s_pz[warp] = bz;
                 }
             }
-            const uint32_t rp = (rank == 0 && (s_rs[wp] & bp)) ? 1u : 0u;
-            csync();   // every CTA has read the measured column
+            __syncthreads();
             // Rowsum of every masked row with the pivot on this CTA's columns,
             // one column per warp at a time.  For the stabilizer rows, A-G's
             // power of i (g summed over the qubits) is counted mod 4 in
-            // bit-sliced form (c1 c0).
+            // bit-sliced form (c1 c0).  The measured column is counted here
+            // but written only after the next cluster barrier, when every CTA
+            // is done reading it.
             uint32_t c0 = 0, c1 = 0;
             if (lane < SW) {
                 const uint32_t ms = s_m0[lane], md = s_m1[lane];
@@ -406,6 +413,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                         c0 ^= pos;
                         c1 ^= ~c0 & neg;
                         c0 ^= neg;
+                        if (l0 + u * QS == la) continue;   // the measured column: later
                         uint32_t *cq = tab + (size_t)(l0 + u * QS) * QSTR;
                         if (xq[u]) cq[TAB_XS * SW + lane] = xs[u] ^ ms;
                         if (zq[u]) cq[TAB_ZS * SW + lane] = zs[u] ^ ms;
@@ -419,14 +427,15 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             s_c0[warp * 32 + lane] = c0;
             s_c1[warp * 32 + lane] = c1;
             __syncthreads();
-            // destabilizer p := the old stabilizer p; stabilizer p := Z_a
-            if (t < nq) {
+            // destabilizer p := the old stabilizer p; stabilizer p := Z_a (the
+            // measured column later)
+            if (t < nq && t != la) {
                 uint32_t *cq = tab + (size_t)t * QSTR;
                 const bool xp = (s_px[t >> 5] >> (t & 31)) & 1u, zp = (s_pz[t >> 5] >> (t & 31)) & 1u;
                 cq[TAB_XD * SW + wp] = (cq[TAB_XD * SW + wp] & ~bp) | (xp ? bp : 0u);
                 cq[TAB_ZD * SW + wp] = (cq[TAB_ZD * SW + wp] & ~bp) | (zp ? bp : 0u);
                 cq[TAB_XS * SW + wp] &= ~bp;
-                cq[TAB_ZS * SW + wp] = (cq[TAB_ZS * SW + wp] & ~bp) | (q0 + t == a ? bp : 0u);
+                cq[TAB_ZS * SW + wp] &= ~bp;
             }
             if (warp == 0) {
                 // this CTA's mod-4 counts, to rank 0
@@ -442,7 +451,25 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 const uint32_t total = (uint32_t)warp_sum(__popc(ms));
                 if (lane == 0) s_cnt = total;
             }
-            csync();   // the counts gathered, every column written
+            csync();   // counts and phase flips gathered; nobody reads the measured column any more
+            if (la >= 0 && warp == 0 && lane < SW) {
+                // the measured column: rowsum (the pivot has x_a = 1), then
+                // row p := the old stabilizer p (destabilizer) and Z_a (stabilizer)
+                uint32_t *cq = tab + (size_t)la * QSTR;
+                const uint32_t ms = s_m0[lane], md = s_m1[lane];
+                uint32_t xs = cq[TAB_XS * SW + lane] ^ ms, zs = cq[TAB_ZS * SW + lane] ^ (zpa ? ms : 0u);
+                uint32_t xd = cq[TAB_XD * SW + lane] ^ md, zd = cq[TAB_ZD * SW + lane] ^ (zpa ? md : 0u);
+                if (lane == wp) {
+                    xd |= bp;
+                    zd = zpa ? (zd | bp) : (zd & ~bp);
+                    xs &= ~bp;
+                    zs |= bp;
+                }
+                cq[TAB_XS * SW + lane] = xs;
+                cq[TAB_ZS * SW + lane] = zs;
+                cq[TAB_XD * SW + lane] = xd;
+                cq[TAB_ZD * SW + lane] = zd;
+            }
             if (rank == 0 && warp == 0) {
                 uint32_t a0 = 0, a1 = 0;
                 for (int r = 0; r < CL; r++) {
@@ -453,6 +480,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                 const uint32_t ms = lane < SW ? s_m0[lane] : 0u;
                 if (a0 & ms) s_err = 2;
                 // new r = r ^ r_p ^ (power of i) / 2 on the masked rows; r_p := 0
+                const uint32_t rp = __shfl_sync(FULL, lane < SW ? s_rs[lane] : 0u, wp) & bp ? 1u : 0u;
                 uint32_t flip = ms & (a1 ^ (rp ? FULL : 0u));
                 if (lane == wp && rp) flip ^= bp;
                 if (lane < SW && flip) atomicXor(&s_rs[lane], flip);
@@ -480,8 +508,6 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             // qubits: thread q multiplies the rows' single-qubit Paulis in row
             // order, 32 rows at a time (exclusive prefix XOR = the product of
             // the earlier rows), with A-G's g-function per row.
-            if (warp == 0 && lane < SW) s_m1[lane] = ca[TAB_XD * SW + lane];
-            __syncthreads();
             int G = 0;
             if (t < nq) {
                 const uint32_t *cq = tab + (size_t)t * QSTR;
@@ -510,7 +536,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
                     s_cnt = total;
                 }
             }
-            csync();   // the sums gathered
+            csync();   // the sums and phase flips gathered
             if (rank == 0 && warp == 0) {
                 const uint32_t d = lane < SW ? s_m1[lane] : 0u;
                 const int g = warp_sum(lane < CL ? s_gG[lane] : 0) +
@@ -535,8 +561,14 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
         }
         if (reset) {
             // conditional X^e on qubit a: flip every stabilizer with z_a = 1
+            // after the measurement (a random outcome changed z_a on the
+            // masked rows by the pivot's z_a, and row p is Z_a)
             if (warp == 0) {
-                const uint32_t m = lane < SW ? ca[TAB_ZS * SW + lane] : 0u;
+                uint32_t m = lane < SW ? s_za[lane] : 0u;
+                if (p >= 0 && lane < SW) {
+                    if (zpa) m ^= s_m0[lane];
+                    if (lane == (p >> 5)) m |= 1u << (p & 31);
+                }
                 const uint32_t total = (uint32_t)warp_sum(__popc(m));
                 if (rank == 0) {
                     write_rows(P.log + lp + 1, m, lane);
@@ -549,7 +581,7 @@ __global__ void __launch_bounds__(TRAV_THREADS, 1) k_traverse(TravParams P)
             note_event(lp);
             lp += 1 + (uint64_t)s_cnt;
         }
-        csync();   // the next step starts when every CTA is done with this one
+        csync();   // the measured column written; the next step may read it
     }
     if (!err) lp += 2ull * (P.ninj_total - inj_mark);   // the last segment's injections
     csync();
