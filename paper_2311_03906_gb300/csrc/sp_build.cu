@@ -3,12 +3,14 @@
 // The symbolic tableau of Eq. stabilizer3 is 2n x (2n + n_s + 1) bits.  By
 // Fact 2 every branch of A-G's algorithm depends only on the X/Z part, so the
 // traversal runs in two passes:
-//   K1 k_traverse   one CTA walks the ops in order over the X/Z tableau plus
-//                   the constant phase column (Init-C, Fact 1, Init-M on
-//                   column 0) and writes a log of the row operations that
-//                   touch symbol columns, plus each fault symbol's injection
-//                   column (Init-P: X^{s} flips rows with z_a = 1, Z^{s} rows
-//                   with x_a = 1);
+//   K1 k_traverse   walks the ops over the X/Z tableau plus the constant
+//                   phase column (Init-C, Fact 1, Init-M on column 0), kept
+//                   qubit-major and bit-parallel over rows, in one CTA's
+//                   shared memory or spread over a thread-block cluster.  It
+//                   writes a log of the row operations that touch symbol
+//                   columns, and each fault symbol's injection column
+//                   (Init-P: X^{s} flips rows with z_a = 1, Z^{s} rows with
+//                   x_a = 1);
 //   K2 k_replay     every symbol column is replayed through that log from
 //                   the moment its symbol appears, 32 columns per thread as
 //                   bit-sliced words in shared memory.  The outcome vector of
