@@ -48,6 +48,11 @@ CIRCUITS = {
     # 256 qubits or more: the replay splits each event's rows over eight warps
     "layered300": lambda: random_layered(300, 30, depolarize=0.01, seed=6),
     "ffwide": lambda: random_feedforward_circuit(260, 3000, seed=810),
+    # more than 577 qubits: the traversal's tableau spreads over a cluster of
+    # CTAs (2 for 640 and 700 qubits, 4 for 1000), with resets and feed-forward
+    "rand640": lambda: random_small_circuit(640, 5000, seed=930),
+    "ff700": lambda: random_feedforward_circuit(700, 6000, seed=820),
+    "rand1000": lambda: random_small_circuit(1000, 6000, seed=931),
 }
 for _s in range(8):
     CIRCUITS[f"rand{_s}"] = (lambda s=_s: random_small_circuit(3 + 7 * s, 60 + 30 * s, seed=900 + s))
@@ -87,7 +92,8 @@ def test_rows_match_oracle(name):
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
 @pytest.mark.parametrize("name", ["fig1", "rep5", "surf3", "surf5", "layered40", "wide1000", "rand3", "rand7",
-                                  "cliff2", "cliff5", "ff1", "ff4", "layered300", "ffwide"])
+                                  "cliff2", "cliff5", "ff1", "ff4", "layered300", "ffwide", "rand640", "ff700",
+                                  "rand1000"])
 @pytest.mark.parametrize("shot0,shots", [(0, 1), (5, 31), (64, 33), (1 << 33, 1061), (7, 4101)])
 def test_records_match_oracle(name, shot0, shots, path):
     c = CIRCUITS[name]()
