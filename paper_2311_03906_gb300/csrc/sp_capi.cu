@@ -175,6 +175,12 @@ sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t 
     // pipeline granularity: at most the sampling chunk, at most 64 MiB of records
     int64_t piece = std::min<int64_t>(P->chunk_shots, std::max<int64_t>(1024, (64 << 20) / std::max<int64_t>(per_shot * 8, 8)));
     piece = std::max<int64_t>(1024, (piece / 1024) * 1024);
+    if (P->path == SP_PATH_FUSED && P->fused_tw) {
+        // whole waves of the fused kernel's tiles, so that no piece ends in a
+        // partly filled wave
+        const int64_t wave = (int64_t)P->num_sms * P->fused_ctas_per_sm * 32 * P->fused_tw;
+        if (wave > 0 && piece > wave) piece = (piece / wave) * wave;
+    }
     sp_status st = SP_OK;
     if (uses_staged_scratch(P)) {
         st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)piece));
