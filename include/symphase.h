@@ -260,10 +260,11 @@ SP_API sp_status sp_set_path(sp_program *prog, int32_t path);
  * sp_set_fused_config -- choose the fused kernel variant by hand instead of
  * the build-time autotuner's choice: tile_shots 32, 64 or 128 (shots per
  * CTA tile; 128 = four Philox streams per thread); variant 1 (two CTAs per
- * SM: 512 threads for 32- and 64-shot tiles, 256 threads for 128) or 2 (one
+ * SM: 512 threads for 32- and 64-shot tiles, 256 threads for 128), 2 (one
  * CTA of 512 threads per SM compiled with more registers; for 32-shot tiles
- * it is the same kernel as 1).  INVALID_ARG if the tile's records do not fit
- * in shared memory.  Records are identical for every variant.
+ * it is the same kernel as 1) or 3 (64-shot tiles only: four CTAs of 256
+ * threads per SM).  INVALID_ARG if the tile's records do not fit in shared
+ * memory.  Records are identical for every variant.
  */
 SP_API sp_status sp_set_fused_config(sp_program *prog, int32_t tile_shots, int32_t variant);
 

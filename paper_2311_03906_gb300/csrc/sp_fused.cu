@@ -578,11 +578,12 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
 
 // Launch shapes: 32- and 64-shot tiles at 512 threads and two CTAs per SM
 // (64 registers); U = 2 marks the 64-shot variant compiled for one CTA per
-// SM with more registers.  128-shot tiles (four independent Philox streams
+// SM with more registers, U = 3 the 64-shot variant at 256 threads and four
+// CTAs per SM.  128-shot tiles (four independent Philox streams
 // per thread) run at 256 threads and two CTAs per SM (U = 1) or 512 threads
 // and one CTA per SM (U = 2), 128 registers either way.
-__host__ __device__ constexpr int fused_threads(int tw, int u) { return tw == 4 && u == 1 ? 256 : FUSED_THREADS; }
-__host__ __device__ constexpr int fused_minb(int tw, int u) { return u == 2 && tw != 1 ? 1 : 2; }
+__host__ __device__ constexpr int fused_threads(int tw, int u) { return (tw == 4 && u == 1) || u == 3 ? 256 : FUSED_THREADS; }
+__host__ __device__ constexpr int fused_minb(int tw, int u) { return u == 3 ? 4 : (u == 2 && tw != 1 ? 1 : 2); }
 
 template <int TW, int U>
 __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fused(FusedParams p)
@@ -884,14 +885,14 @@ typedef void (*FusedFn)(FusedParams);
 static FusedFn fused_kernel(int tw, int unroll)
 {
     if (tw == 4) return unroll == 2 ? k_fused<4, 2> : k_fused<4, 1>;
-    if (tw == 2) return unroll == 2 ? k_fused<2, 2> : k_fused<2, 1>;
+    if (tw == 2) return unroll == 3 ? k_fused<2, 3> : unroll == 2 ? k_fused<2, 2> : k_fused<2, 1>;
     return unroll == 2 ? k_fused<1, 2> : k_fused<1, 1>;
 }
 
 sp_status fused_select(sp_program *P, int tw, int unroll)
 {
-    if ((tw != 1 && tw != 2 && tw != 4) || (unroll != 1 && unroll != 2))
-        return set_error(SP_ERR_INVALID_ARG, "tile words must be 1, 2 or 4, variant 1 or 2");
+    if ((tw != 1 && tw != 2 && tw != 4) || unroll < 1 || unroll > 3 || (unroll == 3 && tw != 2))
+        return set_error(SP_ERR_INVALID_ARG, "tile words must be 1, 2 or 4, variant 1 or 2 (3: 64-shot tiles only)");
     if (P->n_rows == 0 || P->n_blk == 0) return set_error(SP_ERR_INVALID_ARG, "nothing to sample on the fused path");
     const int threads = fused_threads(tw, unroll);
     if ((uint64_t)P->n_blk / (uint64_t)(threads / 32) + 1 >= event_max_blocks(tw))
@@ -935,8 +936,8 @@ sp_status autotune(sp_program *P, cudaStream_t s)
         }
     }
     std::vector<std::pair<int, int>> cand;
-    for (auto c : {std::make_pair(2, 1), std::make_pair(1, 1), std::make_pair(2, 2), std::make_pair(4, 1),
-                   std::make_pair(4, 2)})
+    for (auto c : {std::make_pair(2, 1), std::make_pair(1, 1), std::make_pair(2, 2), std::make_pair(2, 3),
+                   std::make_pair(4, 1), std::make_pair(4, 2)})
         if (fused_words(P, c.first) * 4 <= (size_t)P->smem_max) cand.push_back(c);
     const uint64_t shots = (uint64_t)P->num_sms * 2u * 64u * 4u;
     const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;

@@ -127,7 +127,7 @@ def test_fused_tiles_straddling_2_pow_32_shots(name, tile):
     np.testing.assert_array_equal(_u64(o), ro)
 
 
-@pytest.mark.parametrize("tile,variant", [(32, 1), (32, 2), (64, 1), (64, 2), (128, 1), (128, 2)])
+@pytest.mark.parametrize("tile,variant", [(32, 1), (32, 2), (64, 1), (64, 2), (64, 3), (128, 1), (128, 2)])
 @pytest.mark.parametrize("name", ["rep5", "surf5", "layered40", "rand6", "noisy5"])
 def test_every_fused_variant_matches_oracle(name, tile, variant):
     c = CIRCUITS[name]()
@@ -213,7 +213,7 @@ def test_full_size_d11_both_paths_agree(d11, path):
         prog.set_path(sp.PATH_AUTO)
 
 
-@pytest.mark.parametrize("tile,variant", [(64, 1), (128, 1), (128, 2)])
+@pytest.mark.parametrize("tile,variant", [(64, 1), (64, 3), (128, 1), (128, 2)])
 def test_full_size_d11_fused_variants_agree(d11, tile, variant):
     """Every 64- and 128-shot launch shape gives the records of the
     autotuner's choice at d=11 (200,000 shots, ragged tail), and a few shots
