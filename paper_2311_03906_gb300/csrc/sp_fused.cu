@@ -935,10 +935,17 @@ sp_status autotune(sp_program *P, cudaStream_t s)
             return fused_select(P, it->second.first, it->second.second);
         }
     }
+    int smem_sm = 0;
+    SP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device));
     std::vector<std::pair<int, int>> cand;
     for (auto c : {std::make_pair(2, 1), std::make_pair(1, 1), std::make_pair(2, 2), std::make_pair(2, 3),
-                   std::make_pair(4, 1), std::make_pair(4, 2)})
-        if (fused_words(P, c.first) * 4 <= (size_t)P->smem_max) cand.push_back(c);
+                   std::make_pair(4, 1), std::make_pair(4, 2)}) {
+        const size_t bytes = fused_words(P, c.first) * 4;
+        if (bytes > (size_t)P->smem_max) continue;
+        // the 4-CTA shape only where four tiles' records fit in one SM
+        if (c.second == 3 && 4 * (bytes + 1024) > (size_t)smem_sm) continue;
+        cand.push_back(c);
+    }
     const uint64_t shots = (uint64_t)P->num_sms * 2u * 64u * 4u;
     const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
     uint64_t *out = nullptr;
