@@ -244,14 +244,15 @@ __global__ void k_coef_e4m3(const uint32_t *__restrict__ A, int64_t apitch, int6
     out[i] = bits16_to_e4m3(h);
 }
 
-// Grid: x = tile of 128 shots, y = tile of 128 rows of one record kind.
+// Grid: x = tile of TC_M = 128 shots, y = tile of TC_N = 256 rows of one
+// record kind.
 // Warp specialised, synchronised by per-stage mbarriers instead of CTA
 // barriers: warps 0-7 (expanders) turn the shots' fault bits, loaded one
 // stage ahead into registers, into the E4M3 operand of each stage and
 // arrive on its afull barrier; lane 0 of warp 8 (issuer) keeps the
 // coefficient blocks of the next TC_NS-1 stages in flight (bulk copies on
 // the full barriers), waits for both operands of a stage, issues TC_KS/32
-// MMAs of K = 32 into the TMEM accumulator (128 lanes = shots x 128
+// MMAs of K = 32 into the TMEM accumulator (128 lanes = shots x TC_N
 // columns = rows, held by warp 8) and commits them to the stage's done
 // barrier, which frees the stage's buffers.  The epilogue (warps 0-7) reads
 // the exact FP32 counts and keeps their parity.  Every wait is bounded; a
