@@ -20,6 +20,7 @@
 // observable rows are XORs of measurement rows (K3).
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -1250,7 +1251,9 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     tp.rec_const = d_recconst; tp.counts = d_counts; tp.ev_pos = d_evpos; tp.ev_cap = ev_cap;
     tp.qp = qp;
     bool launched = false;
-    if (CL > 1) {
+    // SP_TRAVERSE_NO_CLUSTER set: the one-CTA fallback (tableau in global
+    // memory) even where a cluster could be launched -- for testing that path
+    if (CL > 1 && !getenv("SP_TRAVERSE_NO_CLUSTER")) {
         const size_t smem = (size_t)qp * qbytes;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)CL);

@@ -237,6 +237,24 @@ def test_full_size_d11_fused_variants_agree(d11, tile, variant):
         prog.set_fused_config(*tuned)
 
 
+@pytest.mark.parametrize("name", ["rand640", "rand1000"])
+def test_traversal_without_a_cluster(name, monkeypatch):
+    """The one-CTA traversal with its tableau in global memory (the fallback
+    when no thread-block cluster can be launched) gives the same rows and
+    records as the oracle."""
+    monkeypatch.setenv("SP_TRAVERSE_NO_CLUSTER", "1")
+    c = CIRCUITS[name]()
+    prog, ref = sp.build(c), oracle.Program(c)
+    w = (ref.num_symbols + 1 + 63) // 64
+    for which in ("meas", "det"):
+        np.testing.assert_array_equal(prog.rows(which)[:, :w], ref.rows(which)[:, :w], err_msg=which)
+    m, d, o = prog.sample(1061, seed=3, shot0=7)
+    torch.cuda.synchronize()
+    rm, rd, ro = ref.sample(3, 7, 1061)
+    np.testing.assert_array_equal(_u64(m), rm)
+    np.testing.assert_array_equal(_u64(d), rd)
+
+
 def _long_repetition(rounds: int, noisy_every: int, p: float):
     """Distance-3 repetition memory with many rounds (about four record rows
     per round) and X_ERROR(p) on the data qubits only every noisy_every
