@@ -59,6 +59,11 @@ def _desc(binding, nq, ops):
     (2, [(6, [0], 0.0), (14, [2], 0.0)], 1), # look-back beyond the records
     (2, [(42, [0], 0.0)], 2),                # unknown opcode
     (2000, [(0, [0], 0.0)], 7),              # too many qubits
+    (2, [(13, [0, 0], 0.1)], 1),             # DEPOLARIZE2 on one qubit
+    (2, [(6, [0], 0.0), (17, [1], 0.0)], 1),     # feed-forward needs (rec, qubit) pairs
+    (2, [(6, [0], 0.0), (17, [2, 0], 0.0)], 1),  # feed-forward look-back beyond the records
+    (2, [(6, [0], 0.0), (18, [1, 5], 0.0)], 1),  # feed-forward qubit out of range
+    (2, [(19, [1, 0], 0.0)], 1),                 # feed-forward before any record
 ])
 def test_build_rejects_on_host(lib, nq, ops, status):
     from paper_2311_03906_gb300 import binding
@@ -79,5 +84,9 @@ def test_null_arguments(lib):
     assert lib.sp_expect_grad(None, None, None, None, None) == 1
     assert lib.sp_export_rows(None, 0, None, 1) == 1
     assert lib.sp_set_chunk(None, 1024) == 1
+    assert lib.sp_set_path(None, 0) == 1
+    assert lib.sp_set_fused_config(None, 64, 1) == 1
+    st = C.c_int32(7)
+    assert lib.sp_device_status(None, C.byref(st)) == 1
     lib.sp_free(None)
     assert b"NULL" in lib.sp_last_error()
