@@ -72,7 +72,7 @@ def _peaks():
 
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -83,16 +83,18 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
-            self.fh = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Median SM clock and throttle reasons of the samples taken inside
+        window = (t0, t1) (host wall-clock seconds), or of all samples."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -101,23 +103,31 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        import datetime
+        rows = []
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
+        inside = [r for r in rows if window and window[0] - 0.02 <= r[0] <= window[1] + 0.02]
+        use = inside if inside else rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in use for n, v in zip(names, r[3]) if v.lower() == "active"})
+        sm = [r[1] for r in use]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": reasons, "samples": len(sm),
+                "scope": "timed region" if inside else "whole sampler run (no sample inside the timed region)"}
 
 
 def _dist():
@@ -125,21 +135,56 @@ def _dist():
     return world()
 
 
-def _cpu_baseline(circuit, budget_s: float = 12.0, seed: int = 1):
-    """The oracle as it stands, single-threaded, on a bounded sample."""
+def _oracle_rate(prog, budget_s: float, threads: int, seed: int = 1):
+    """Shots/s of the oracle as it stands on `threads` host threads, each
+    sampling its own contiguous shot ranges of 64 (the oracle's C calls run
+    without the GIL), over about budget_s seconds."""
+    import concurrent.futures as cf
+    batch = 64
+
+    def worker(t):
+        done, k = 0, 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            prog.sample(seed, (k * threads + t) * batch, batch)
+            done += batch
+            k += 1
+        return done
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        done = sum(ex.map(worker, range(threads)))
+    dt = time.perf_counter() - t0
+    return done, dt
+
+
+def _cpu_baseline_child(budget_s: float):
+    """Runs in its own process (no CUDA library loaded): the oracle on one
+    host thread, then on every host core."""
     import oracle
+    from workloads import surface_code
+    circuit = surface_code(WORKLOAD["distance"], WORKLOAD["rounds"], WORKLOAD["p"])
     t0 = time.perf_counter()
     prog = oracle.Program(circuit)
     build_s = time.perf_counter() - t0
-    done, batch = 0, 64
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        prog.sample(seed, done, batch)
-        done += batch
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} shots of {WORKLOAD['name']} (shots 0..{done - 1}, seed {seed}), "
-                      f"single-threaded plain C oracle, {dt:.1f} s; oracle build {build_s * 1e3:.0f} ms"}
+    n1, dt1 = _oracle_rate(prog, budget_s, 1)
+    cores = os.cpu_count() or 1
+    nn, dtn = _oracle_rate(prog, max(2.0, budget_s / 2), cores)
+    return {"value": n1 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n1} shots of {WORKLOAD['name']} (seed 1), single-threaded plain C oracle, {dt1:.1f} s; "
+                      f"oracle build {build_s * 1e3:.0f} ms",
+            "all_cores": {"value": nn / dtn, "unit": UNIT, "cores": cores, "kind": "oracle",
+                          "sample": f"{nn} shots in 64-shot ranges on {cores} host threads (nproc), {dtn:.1f} s"}}
+
+
+def _cpu_baseline(budget_s: float = 12.0):
+    """The oracle timed in a child process, so that this process maps only
+    the CUDA library."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child",
+                        "--cpu-seconds", str(budget_s)], capture_output=True, text=True, cwd=ROOT)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
+                "sample": "oracle child process failed: " + r.stderr.strip()[-200:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
@@ -172,6 +217,63 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _mul_roofline(info, shots, avg_ms):
+    """Achieved integer multiplies of the fused kernel's Philox draw against
+    the multiply pipe: 32 multiply issues per (shot, 4-channel block)."""
+    peaks = _peaks()
+    nblocks = -(-info["num_channels"] // 4)
+    achieved = nblocks * 32.0 * shots / (avg_ms / 1e3) / 1e12
+    peak = 152 * 64 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
+            "peak_source": "152 SMs x 64 int32 multiplies/clk x max SM clock (derived)"}
+
+
+def _config_section(name, gen, gen_args, shots, chunk, seed, steps):
+    """Another configuration of the same step: build, warm up, then `steps`
+    timed sp_sample calls of `shots` shots (in chunks of `chunk` shots when
+    nonzero) with the per-kernel CUDA-event profile."""
+    import torch
+    import paper_2311_03906_gb300 as sp
+    import workloads
+    circuit = getattr(workloads, gen)(*gen_args)
+    t0 = time.perf_counter()
+    prog = sp.build(circuit)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    if chunk:
+        prog.set_chunk(chunk)
+    info = prog.info
+    out = prog.alloc_outputs(shots)
+    stream = torch.cuda.current_stream()
+    for w in range(3):
+        prog.sample(shots, seed=seed, shot0=w * shots, out=out)
+    torch.cuda.synchronize()
+    prog.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        prog.sample(shots, seed=seed, shot0=(3 + k) * shots, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = prog.profile_read()
+    prog.profile(False)
+    ms = e0.elapsed_time(e1) / steps
+    nrec = info["num_measurements"] + info["num_detectors"] + info["num_observables"]
+    value = shots / (ms / 1e3)
+    kern = {k: {"launches_per_step": v[1] / steps, "ms_per_step": v[0] / steps} for k, v in prof.items() if v[1]}
+    roof = None
+    if "fused" in prof and prof["fused"][1]:
+        kms, n = prof["fused"]
+        roof = dict(_mul_roofline(info, shots * steps / n, kms / n), kernel="fused")
+    prog.close()
+    return {"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": 3,
+            "record_gbit_s": value * nrec / 1e9, "build_ms": build_ms, "kernels": kern, "roofline": roof,
+            "config": {"workload": name, "shots_per_step": shots, "chunk_shots": info["chunk_shots"],
+                       "symbols": info["num_symbols"], "channels": info["num_channels"],
+                       "measurements": info["num_measurements"], "detectors": info["num_detectors"],
+                       "path": {1: "staged-sparse", 2: "dense", 3: "fused", 4: "tensor"}.get(info["path"], "?"),
+                       "fused_tile_shots": info["fused_tile_shots"], "fused_variant": info["fused_variant"]}}
+
+
 def _batched_vs_plain(args):
     """64 uneven circuits (rotated surface codes d = 3..15, p in {5e-4, 1e-3,
     2e-3}, seeds 0..63), 1e5 shots each: one graph-captured batched enqueue
@@ -186,13 +288,14 @@ def _batched_vs_plain(args):
     seeds = [s for _, s in suite]
     shots = [args.batch_shots] * len(progs)
     outs = [p.alloc_outputs(n) for p, n in zip(progs, shots)]
+    outs_plain = [p.alloc_outputs(n) for p, n in zip(progs, shots)]
     stream = torch.cuda.current_stream()
 
     def batched():
         sp.sample_batch(progs, seeds, shots, outs=outs)
 
     def plain():
-        for p, s, n, o in zip(progs, seeds, shots, outs):
+        for p, s, n, o in zip(progs, seeds, shots, outs_plain):
             p.sample(n, seed=s, out=o)
 
     res = {}
@@ -202,7 +305,7 @@ def _batched_vs_plain(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        reps = 3
+        reps = 5
         for _ in range(reps):
             fn()
         e1.record(stream)
@@ -210,10 +313,17 @@ def _batched_vs_plain(args):
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms": ms, "shots_per_s": sum(shots) / (ms / 1e3)}
     res["speedup"] = res["plain"]["ms"] / res["batched"]["ms"]
+    res["identical"] = all(torch.equal(a, b) for oa, ob in zip(outs, outs_plain) for a, b in zip(oa, ob))
+    shapes = {}
+    for p in progs:
+        k = f"{p.info['fused_tile_shots']}-shot tiles, variant {p.info['fused_variant']}"
+        shapes[k] = shapes.get(k, 0) + 1
     res["config"] = {"workload": "64 rotated surface codes d=3+2*(i mod 7), p=(5e-4,1e-3,2e-3)[(i//7) mod 3], seed i",
                      "shots_per_circuit": args.batch_shots, "build_s": build_s,
                      "paths": {"fused": sum(p.info["path"] == 3 for p in progs),
-                               "staged": sum(p.info["path"] == 1 for p in progs)}}
+                               "staged": sum(p.info["path"] == 1 for p in progs)},
+                     "launch_shapes": shapes,
+                     "identical": "torch.equal of every record tensor, batched vs 64 separate sp_sample calls"}
     for p in progs:
         p.close()
     return res
@@ -223,63 +333,71 @@ def _dense_paths(args):
     """A circuit whose coefficient rows are dense (mirror circuit: 512 qubits,
     16 random Clifford layers then their inverse, DEPOLARIZE1(p) after
     every layer, every qubit measured with one detector each; about 33k
-    symbols, 1,024 record rows, ~40 % of the coefficients set): the same
-    shots sampled with the product as the tcgen05 tensor-core contraction,
-    the CUDA-core AND/popcount form and the sparse fused kernel, plus the
-    build's own timed choice. The tensor kernel's roofline is its FP8 rate
-    (measured bf16 peak x 2, the nominal FP8:BF16 ratio)."""
+    symbols, 1,024 record rows, ~11 % of the coefficients set), over noise
+    rates p: the same shots sampled with the product as the tcgen05
+    tensor-core contraction, the CUDA-core AND/popcount form and the sparse
+    fused kernel, plus the build's own timed choice. The tensor kernel's
+    roofline is its FP8 rate (measured bf16 peak x 2, the nominal FP8:BF16
+    ratio), counted on the dense contraction (2 rows (n_s+1) FLOP per shot)
+    and on the set coefficients only (2 nnz FLOP per shot)."""
     import torch
     import paper_2311_03906_gb300 as sp
     from workloads import mirror_circuit
     peaks = _peaks()
-    c = mirror_circuit(512, 16, p=args.dense_p, seed=1)
-    t0 = time.perf_counter()
-    prog = sp.build(c)
-    build_s = time.perf_counter() - t0
-    info = prog.info
-    auto = info["path"]
-    shots = args.dense_shots
-    out = prog.alloc_outputs(shots)
-    rows = info["num_measurements"] + info["num_detectors"] + info["num_observables"]
-    flops = 2.0 * rows * (info["num_symbols"] + 1) * shots
-    stream = torch.cuda.current_stream()
     names = {sp.PATH_TENSOR: "tensor", sp.PATH_DENSE: "dense", sp.PATH_FUSED: "fused", sp.PATH_SPARSE: "staged-sparse"}
-    sparse_path = sp.PATH_FUSED if info["fused_tile_shots"] else sp.PATH_SPARSE
-    res = {}
-    for path in (sp.PATH_TENSOR, sp.PATH_DENSE, sparse_path):
-        prog.set_path(path)
-        prog.sample(shots, seed=1, out=out)
-        torch.cuda.synchronize()
-        prog.profile(True)
-        prog.profile_read()
-        reps = 3
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for r in range(reps):
-            prog.sample(shots, seed=1, shot0=(r + 1) * shots, out=out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        prof = prog.profile_read()
-        prog.profile(False)
-        kern = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in prof.items() if v[1]}
-        res[names[path]] = {"ms": ms, "shots_per_s": shots / (ms / 1e3), "kernels": kern}
-    status = prog.device_status()
-    t = res["tensor"]["kernels"].get("tensor")
-    roof = None
-    if t:
-        achieved = flops / (t["ms_per_step"] / 1e3) / 1e12
-        peak = 2.0 * peaks["bf16_tflops"]
-        roof = {"kernel": "k_tc_product", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"MEASURED_PEAKS.json bf16_tflops x 2 (nominal FP8:BF16 ratio; {peaks['source']})"}
-    prog.close()
-    return {"config": {"workload": f"mirror_circuit(n=512, layers=16, p={args.dense_p:g}, seed=1)", "shots_per_step": shots,
-                       "symbols": info["num_symbols"], "record_rows": rows, "density": info["density"],
-                       "build_s": build_s, "auto_path": names.get(auto, str(auto)),
-                       "build_probe_ms": {names[k]: v for k, v in enumerate(info["path_probe_ms"]) if v > 0 and k in names}},
-            "paths": res, "tensor_roofline": roof, "device_status": status,
-            "algorithmic_flops_per_shot": flops / shots}
+    sweep = []
+    for p in args.dense_p:
+        c = mirror_circuit(512, 16, p=p, seed=1)
+        t0 = time.perf_counter()
+        prog = sp.build(c)
+        build_s = time.perf_counter() - t0
+        info = prog.info
+        auto = info["path"]
+        shots = args.dense_shots
+        out = prog.alloc_outputs(shots)
+        rows = info["num_measurements"] + info["num_detectors"] + info["num_observables"]
+        flops = 2.0 * rows * (info["num_symbols"] + 1) * shots
+        flops_set = 2.0 * info["nnz_rows"] * shots
+        stream = torch.cuda.current_stream()
+        sparse_path = sp.PATH_FUSED if info["fused_tile_shots"] else sp.PATH_SPARSE
+        res = {}
+        for path in (sp.PATH_TENSOR, sp.PATH_DENSE, sparse_path):
+            prog.set_path(path)
+            prog.sample(shots, seed=1, out=out)
+            torch.cuda.synchronize()
+            prog.profile(True)
+            prog.profile_read()
+            reps = 3
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for r in range(reps):
+                prog.sample(shots, seed=1, shot0=(r + 1) * shots, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            prof = prog.profile_read()
+            prog.profile(False)
+            kern = {k: {"ms_per_step": v[0] / reps, "launches_per_step": v[1] / reps} for k, v in prof.items() if v[1]}
+            res[names[path]] = {"ms": ms, "shots_per_s": shots / (ms / 1e3), "kernels": kern}
+        status = prog.device_status()
+        t = res["tensor"]["kernels"].get("tensor")
+        roof = None
+        if t:
+            sec = t["ms_per_step"] / 1e3
+            peak = 2.0 * peaks["bf16_tflops"]
+            roof = {"kernel": "k_tc_product", "bound": "tensor", "achieved": flops / sec / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": flops / sec / 1e12 / peak,
+                    "achieved_set_coefficients": flops_set / sec / 1e12, "frac_set_coefficients": flops_set / sec / 1e12 / peak,
+                    "traffic": None,
+                    "peak_source": f"MEASURED_PEAKS.json bf16_tflops x 2 (nominal FP8:BF16 ratio; {peaks['source']})"}
+        fastest = min(res, key=lambda k: res[k]["ms"])
+        sweep.append({"p": p, "symbols": info["num_symbols"], "record_rows": rows, "density": info["density"],
+                      "build_s": build_s, "auto_path": names.get(auto, str(auto)), "fastest": fastest,
+                      "build_probe_ms": {names[k]: v for k, v in enumerate(info["path_probe_ms"]) if v > 0 and k in names},
+                      "paths": res, "tensor_roofline": roof, "device_status": status})
+        prog.close()
+    return {"config": {"workload": "mirror_circuit(n=512, layers=16, p, seed=1)", "shots_per_step": args.dense_shots},
+            "sweep": sweep}
 
 
 def _build_times(args):
@@ -424,25 +542,29 @@ def run_ours(args):
     def step(i):
         prog.sample(shots, seed=1, shot0=shard_range(rank, world, shots, i, steps_total)[0], out=out)
 
+    # the clock sampler starts first, so that it samples from the first timed step on
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     prog.profile(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    wall0 = time.time()
     ev0.record(stream)
     for i in range(args.steps):
         step(args.warmup + i)
     ev1.record(stream)
     torch.cuda.synchronize()
+    wall1 = time.time()
     prof = prog.profile_read()
     prog.profile(False)
     ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
+    clk = clocks.stop(window=(wall0, wall1))
     if world > 1:
         ms = max_over_ranks(ms, device="cuda")
         torch.distributed.barrier()
@@ -532,8 +654,16 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": shots * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "inputs": "a step's inputs are its seed and shot range (16 bytes), passed as kernel launch "
+                          "parameters; the program is resident; every record is copied to pinned host memory"},
     }
+    if world == 1 and not args.no_c1:
+        line["c1"] = _config_section("repetition_code_d5_r5_p0.01", "repetition_code", (5, 5, 0.01), 10_000, 0,
+                                     seed=1, steps=20)
+    if world == 1 and not args.no_d17:
+        line["d17"] = _config_section("surface_code_d17_r17_p2e-3", "surface_code", (17, 17, 2e-3), 1_000_000, 65536,
+                                      seed=3, steps=3)
     if world == 1 and not args.no_batch:
         line["batched"] = _batched_vs_plain(args)
     if world == 1 and not args.no_dense:
@@ -543,7 +673,7 @@ def run_ours(args):
     if world == 1 and not args.no_fit:
         line["fit"] = _fit(args)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(circuit, budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = _cpu_baseline(budget_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -562,14 +692,20 @@ def main():
     ap.add_argument("--batch-shots", type=int, default=100_000)
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-row (mirror circuit) section")
     ap.add_argument("--dense-shots", type=int, default=262_144)
-    ap.add_argument("--dense-p", type=float, default=0.01, help="noise rate of the dense-row workload")
+    ap.add_argument("--dense-p", type=float, nargs="*", default=[1e-3, 1e-2, 3e-2, 1e-1],
+                    help="noise rates of the dense-row workload")
     ap.add_argument("--no-build-times", action="store_true", help="skip the sampler-initialization timings")
     ap.add_argument("--no-fit", action="store_true", help="skip the noise-model fit (config 5)")
     ap.add_argument("--build-sizes", type=int, nargs="*", default=[100, 200, 300, 500])
+    ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-d17", action="store_true", help="skip the d=17 configuration")
+    ap.add_argument("--no-c1", action="store_true", help="skip the repetition-code configuration")
     ap.add_argument("--profile", action="store_true",
                     help="build, then one 65536-shot sample only (the case captured by ncu)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.cpu_baseline_child:
+        print(json.dumps(_cpu_baseline_child(args.cpu_seconds)), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.profile:
         run_profile_case()

@@ -190,25 +190,42 @@ SP_API sp_status sp_sample_host(sp_program *prog, uint64_t seed, uint64_t shot0,
  *   Limit: a program with num_symbols + num_rows > 8,388,608 (more than
  *   32 MiB per 32 shots) is rejected with SP_ERR_TOO_LARGE.
  *   Set-up: the first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current) and caches it; make
- *   that first call before any stream capture on the device.
+ *   (cudaGetSymbolAddress, with that device current) and caches it for the
+ *   life of the process, so the device's primary context must not be reset
+ *   (cudaDeviceReset) after it; make that first call before any stream
+ *   capture on the device.  The program must live on the current device.
  *   Sharing: every call on a device uses the same array and leaves its last
  *   contents there.  Calls whose work overlaps on the GPU (different
  *   streams, or different host threads) race on it and must be ordered by
  *   the caller; calls on one stream are ordered by the stream.
- * Errors: INVALID_ARG (NULL prog, misaligned pointer), TOO_LARGE, CUDA.
+ * Errors: INVALID_ARG (NULL prog, misaligned pointer, program of another
+ * device), TOO_LARGE, CUDA.
  */
 SP_API sp_status sp_sample_static(sp_program *prog, uint64_t seed, uint64_t shot0, uint64_t nshots,
                                   uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, void *cuda_stream);
 
 /*
  * sp_sample_batch -- many programs (uneven sizes, shot counts, seeds) in one
- * enqueue.  Program i samples shots 0..nshots[i]-1 with seeds[i] into
- * d_meas[i], d_det[i], d_obs[i] (entries may be NULL).  The work of all
- * programs is laid out as one list of (program, shot tile) items and run by
- * persistent kernels; the enqueue sequence is captured once in a CUDA graph
- * per (program set, shot counts) and replayed.  Records are identical to nprog
- * separate sp_sample calls.
+ * enqueue: Algorithm 1 "Sampling" (Eq. sampling) for each program.  Program
+ * i samples shots 0..nshots[i]-1 with seeds[i] into d_meas[i], d_det[i],
+ * d_obs[i] (the arrays, or any entry, may be NULL).  Records are identical
+ * to nprog separate sp_sample calls.
+ *   Programs on the fused path are grouped by the launch shape their build-
+ *   time autotuner chose (shots per tile, threads, CTAs per SM); each group
+ *   runs as one persistent kernel over a list of (program, shot tile) work
+ *   items.  The enqueue sequence is captured once in a CUDA graph per plan
+ *   = (device, program set, each program's configuration, shot counts) and
+ *   replayed: seeds and output pointers are not part of the plan, they are
+ *   copied into the plan's device parameter block on cuda_stream before
+ *   every launch.  Other programs are sampled through their own path on
+ *   cuda_stream after the graph.
+ *   Plans are cached per process (at most 8, least recently used dropped);
+ *   a plan is dropped when one of its programs is freed or reconfigured
+ *   (sp_set_path, sp_set_fused_config, sp_set_chunk).  Dropping a plan waits
+ *   for the device.  Calls that share a plan must be ordered by the caller
+ *   (same stream, or synchronised): they share its parameter block.
+ * Errors: INVALID_ARG (NULL arrays or programs, misaligned outputs, programs
+ * of another device), OOM, CUDA.
  */
 SP_API sp_status sp_sample_batch(sp_program *const *progs, uint32_t nprog, const uint64_t *seeds,
                           const uint64_t *nshots, uint64_t *const *d_meas,
@@ -217,20 +234,34 @@ SP_API sp_status sp_sample_batch(sp_program *const *progs, uint32_t nprog, const
 /*
  * sp_expect -- analytic detector (then observable) parity expectations
  * E_j = E[(-1)^{D_j}] as log|E_j| in FP32:
- *     log|E_j| = sum_c [channel c touches row j] * log(1 - 2 kappa_c p_c)
+ *     log|E_j| = sum_c [channel c touches row j] * log|1 - 2 kappa_c p_c|
  * with kappa = 1 (X/Y/Z_ERROR), 2/3 (DEPOLARIZE1), 8/15 (DEPOLARIZE2): the
- * share of a channel's outcomes with odd overlap with any nonzero mask.
+ * share of a channel's outcomes with odd overlap with any nonzero mask
+ * (Sec. 3.1's channel distributions, applied to the row's affine form).
+ * Valid for every p in [0, 1]: a factor is negative above kappa*p = 1/2 and
+ * zero at equality, where log|E_j| = -inf (sp_expect_sign gives the sign).
  *   d_p     num_channels FP32 probabilities (random-measurement channels are
  *           ignored), or NULL for the circuit's own probabilities.
  *   d_logE  num_detectors + num_observables FP32 outputs.
- * The sign of E_j is (-1)^{c_j} (constant bit of the row, see sp_export_rows).
+ * Errors: INVALID_ARG (NULL prog or d_logE), OOM, CUDA.
  */
 SP_API sp_status sp_expect(sp_program *prog, const float *d_p, float *d_logE, void *cuda_stream);
 
 /*
+ * sp_expect_sign -- the signs of the expectations of sp_expect:
+ *     sign E_j = (-1)^{c_j} * prod_c [channel c touches row j] sign(1 - 2 kappa_c p_c)
+ * written as FP32 +1 or -1, and 0 where some factor is exactly zero (then
+ * E_j = 0).  c_j is the constant bit of the row (sp_export_rows).
+ *   d_p     as in sp_expect;  d_sign  num_detectors + num_observables outputs.
+ * Errors: INVALID_ARG (NULL prog or d_sign), OOM, CUDA.
+ */
+SP_API sp_status sp_expect_sign(sp_program *prog, const float *d_p, float *d_sign, void *cuda_stream);
+
+/*
  * sp_expect_grad -- adjoint of sp_expect:
  *     d_grad_p[c] = sum_j d_grad_logE[j] * d log|E_j| / d p_c
- *                 = -2 kappa_c / (1 - 2 kappa_c p_c) * sum_j A[c,j] g_j.
+ *                 = -2 kappa_c / (1 - 2 kappa_c p_c) * sum_j A[c,j] g_j
+ * (valid on both sides of kappa_c p_c = 1/2; infinite at equality).
  *   d_p, d_grad_logE  inputs (d_p may be NULL as in sp_expect)
  *   d_grad_p          num_channels FP32 outputs (overwritten)
  */
@@ -274,11 +305,23 @@ SP_API sp_status sp_set_chunk(sp_program *prog, uint64_t chunk_shots);
 /*
  * sp_device_status -- wait for the device, then report and clear the status
  * word that the program's tensor-core kernel sets when one of its bounded
- * waits (on a bulk copy or on its own MMAs) ran out: *status = 0 if every
- * launch since the last call completed, 1 if some tile gave up (its records
- * are then not written).  Other kernels have no waits and leave it 0.
+ * waits (on a bulk copy or on its own MMAs) ran out: *status = 0 and SP_OK
+ * if every launch since the last call completed; *status = 1 and
+ * SP_ERR_TIMEOUT if some tile gave up (its records are then not written).
+ * sp_sample_host, which synchronises anyway, returns SP_ERR_TIMEOUT the same
+ * way.  Other kernels have no waits and leave the word 0.
  */
 SP_API sp_status sp_device_status(sp_program *prog, int32_t *status);
+
+/*
+ * sp_set_wait_limit -- bound, in nanoseconds, of the tensor-core kernel's
+ * waits for a stage's operands and for the MMAs that free a stage (0 = the
+ * default, 2 s).  A wait that runs out makes the tile give up: the kernel
+ * stops issuing work, waits for the copies and MMAs already issued (with
+ * the fixed 2 s bound), frees its TMEM, records status 1 and returns.
+ * Failure-path tests set a bound too short for any stage to be ready.
+ */
+SP_API sp_status sp_set_wait_limit(sp_program *prog, uint64_t ns);
 
 /* Kernel classes reported by sp_profile_read. */
 enum {
@@ -300,6 +343,27 @@ enum {
  */
 SP_API sp_status sp_profile_enable(sp_program *prog, int32_t on);
 SP_API sp_status sp_profile_read(sp_program *prog, double *ms, uint64_t *launches);
+
+/*
+ * sp_debug_fail_alloc -- allocation-failure injection for tests of the
+ * error paths (host-side: no GPU fault is involved).  After `after` more
+ * successful library allocations (device buffers from cudaMalloc, and the
+ * host-side program object of sp_build), the next one fails as if the
+ * device or host were out of memory and the hook disarms; after < 0
+ * disarms it.  The failing call returns SP_ERR_OOM, releases what it had
+ * allocated and leaves the program (if any) usable.  No paper counterpart.
+ */
+SP_API sp_status sp_debug_fail_alloc(int64_t after);
+
+/* sp_debug_live_allocs -- device allocations and programs the library
+ * currently holds (either pointer may be NULL); used to check that failing
+ * calls leak nothing.  Host only; no paper counterpart. */
+SP_API sp_status sp_debug_live_allocs(int64_t *device_allocs, int64_t *host_programs);
+
+/* sp_batch_plans -- number of cached sp_sample_batch plans and the cache's
+ * capacity (either pointer may be NULL).  Host only; no paper counterpart
+ * (inspection of the batched form's plan cache). */
+SP_API sp_status sp_batch_plans(uint32_t *count, uint32_t *capacity);
 
 /* sp_free -- release a program (NULL is allowed). */
 SP_API void sp_free(sp_program *prog);

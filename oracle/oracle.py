@@ -216,6 +216,25 @@ class Program:
             self._lib.or_sample(self._h, seed, shot0, nshots, _p(m), _p(d), _p(o))
         return m[:, :wm], d[:, :wd], o[:, :wo]
 
+    def sample_parallel(self, seed: int, shot0: int, nshots: int, threads: Optional[int] = None,
+                        piece: int = 256):
+        """``sample`` split into contiguous pieces run on host threads (the C
+        calls release the GIL); the records are the same as one call's."""
+        import concurrent.futures as cf
+        threads = threads or os.cpu_count() or 1
+        wm, wd, wo = self._words()
+        m = np.zeros((nshots, max(wm, 1)), np.uint64)
+        d = np.zeros((nshots, max(wd, 1)), np.uint64)
+        o = np.zeros((nshots, max(wo, 1)), np.uint64)
+
+        def run(a):
+            n = min(piece, nshots - a)
+            self._lib.or_sample(self._h, seed, shot0 + a, n, _p(m[a:]), _p(d[a:]), _p(o[a:]))
+
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(run, range(0, nshots, piece)))
+        return m[:, :wm], d[:, :wd], o[:, :wo]
+
     def sample_shots(self, seed: int, shots: Sequence[int]):
         shots = np.ascontiguousarray(np.asarray(shots, dtype=np.uint64))
         n = len(shots)

@@ -26,10 +26,11 @@ PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED, PATH_TENSOR = 0, 1, 2, 3, 4
 
 # every entry point declared in include/symphase.h
 EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",
-           "sp_sample_batch", "sp_expect",
+           "sp_sample_batch", "sp_expect", "sp_expect_sign",
            "sp_expect_grad", "sp_export_rows", "sp_export_channels", "sp_set_path", "sp_set_fused_config",
-           "sp_set_chunk", "sp_device_status",
-           "sp_profile_enable", "sp_profile_read", "sp_free", "sp_last_error")
+           "sp_set_chunk", "sp_device_status", "sp_set_wait_limit",
+           "sp_profile_enable", "sp_profile_read", "sp_batch_plans", "sp_debug_fail_alloc",
+           "sp_debug_live_allocs", "sp_free", "sp_last_error")
 KERNEL_CLASSES = ("draw", "product", "emit", "fused", "tensor")
 
 
@@ -84,14 +85,19 @@ def load() -> C.CDLL:
     lib.sp_sample_batch.argtypes = [vp, u32, vp, vp, vp, vp, vp, vp]
     lib.sp_expect.argtypes = [vp, vp, vp, vp]
     lib.sp_expect_grad.argtypes = [vp, vp, vp, vp, vp]
+    lib.sp_expect_sign.argtypes = [vp, vp, vp, vp]
     lib.sp_export_rows.argtypes = [vp, i32, vp, u64]
     lib.sp_export_channels.argtypes = [vp, vp, vp, vp]
     lib.sp_set_path.argtypes = [vp, i32]
     lib.sp_set_chunk.argtypes = [vp, u64]
     lib.sp_device_status.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.sp_set_wait_limit.argtypes = [vp, u64]
     lib.sp_set_fused_config.argtypes = [vp, i32, i32]
     lib.sp_profile_enable.argtypes = [vp, i32]
     lib.sp_profile_read.argtypes = [vp, vp, vp]
+    lib.sp_batch_plans.argtypes = [vp, vp]
+    lib.sp_debug_fail_alloc.argtypes = [C.c_int64]
+    lib.sp_debug_live_allocs.argtypes = [vp, vp]
     lib.sp_free.argtypes = [vp]
     lib.sp_free.restype = None
     lib.sp_last_error.restype = C.c_char_p
@@ -237,10 +243,17 @@ class Program:
 
     def device_status(self) -> int:
         """Waits for the device; 0 if every tensor-core tile since the last
-        call completed, 1 if one gave up on a bounded wait."""
+        call completed, 1 if one gave up on a bounded wait (the library then
+        also returns SP_ERR_TIMEOUT, which this method turns into the value)."""
         v = C.c_int32(0)
-        _check(self._lib.sp_device_status(self._h, C.byref(v)))
+        st = self._lib.sp_device_status(self._h, C.byref(v))
+        if st != 6:
+            _check(st)
         return int(v.value)
+
+    def set_wait_limit(self, ns: int):
+        """Bound of the tensor-core kernel's stage waits (0 = default 2 s)."""
+        _check(self._lib.sp_set_wait_limit(self._h, int(ns)))
 
     def profile(self, on: bool = True):
         _check(self._lib.sp_profile_enable(self._h, 1 if on else 0))
@@ -258,6 +271,14 @@ class Program:
         n = self.num_detectors + self.num_observables
         out = torch.empty(n, dtype=torch.float32, device="cuda") if out is None else out
         _check(self._lib.sp_expect(self._h, _ptr(p), _ptr(out), C.c_void_p(_stream_handle(stream))))
+        return out
+
+    def expect_sign_raw(self, p=None, out=None, stream=None):
+        """sign E_j (+1, -1, or 0 where E_j = 0) for detectors then observables."""
+        import torch
+        n = self.num_detectors + self.num_observables
+        out = torch.empty(n, dtype=torch.float32, device="cuda") if out is None else out
+        _check(self._lib.sp_expect_sign(self._h, _ptr(p), _ptr(out), C.c_void_p(_stream_handle(stream))))
         return out
 
     def expect_grad_raw(self, p, grad_logE, out=None, stream=None):
@@ -303,6 +324,27 @@ def sample_batch(progs: Sequence[Program], seeds: Sequence[int], shots: Sequence
     O = (C.c_void_p * n)(*[_ptr(o[2]) for o in outs])
     _check(lib.sp_sample_batch(H, n, S, N, M, D, O, C.c_void_p(_stream_handle(stream))))
     return outs
+
+
+def batch_plans() -> Tuple[int, int]:
+    """(cached sp_sample_batch plans, cache capacity)."""
+    lib = load()
+    cnt, cap = C.c_uint32(0), C.c_uint32(0)
+    _check(lib.sp_batch_plans(C.byref(cnt), C.byref(cap)))
+    return int(cnt.value), int(cap.value)
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Make the library's allocation number `after` (0 = the next) fail
+    once; a negative value disarms the hook."""
+    _check(load().sp_debug_fail_alloc(int(after)))
+
+
+def debug_live_allocs() -> Tuple[int, int]:
+    """(device allocations, programs) the library currently holds."""
+    dev, host = C.c_int64(0), C.c_int64(0)
+    _check(load().sp_debug_live_allocs(C.byref(dev), C.byref(host)))
+    return int(dev.value), int(host.value)
 
 
 def _expect_function():

@@ -1150,7 +1150,7 @@ template <typename T>
 sp_status dalloc(T **p, size_t count)
 {
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    cudaError_t e = dev_alloc((void **)p, count * sizeof(T));
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -1161,7 +1161,7 @@ sp_status dalloc(T **p, size_t count)
 
 struct Temp {
     std::vector<void *> ptrs;
-    ~Temp() { for (void *p : ptrs) cudaFree(p); }
+    ~Temp() { for (void *p : ptrs) dev_free(p); }
     template <typename T> sp_status alloc(T **p, size_t count)
     {
         sp_status st = dalloc(p, count);

@@ -1,5 +1,6 @@
 // sp_capi.cu -- the extern "C" entry points declared in include/symphase.h.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -10,6 +11,39 @@
 namespace sp {
 
 static thread_local std::string g_last_error;
+
+// Allocation-failure hook: the allocation that finds the counter at zero
+// fails, then the hook disarms (-1 = off).  Live allocation counts.
+static std::atomic<int64_t> g_fail_after{-1};
+static std::atomic<int64_t> g_live_dev{0}, g_live_host{0};
+
+static bool hook_fires()
+{
+    int64_t v = g_fail_after.load();
+    while (v >= 0) {
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (hook_fires()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_dev++;
+    else *p = nullptr;
+    return e;
+}
+
+void dev_free(void *p)
+{
+    if (!p) return;
+    cudaFree(p);
+    g_live_dev--;
+}
+
+bool host_alloc_fails() { return hook_fires(); }
 
 sp_status set_error(sp_status st, const std::string &msg)
 {
@@ -36,7 +70,7 @@ static void release(sp_program *P)
                     P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs,
                     P->d_colOff, P->d_colRows, P->d_AT, P->d_tc_coef[0], P->d_tc_coef[1], P->d_tc_coef[2],
                     P->d_tc_status};
-    for (void *b : bufs) if (b) cudaFree(b);
+    for (void *b : bufs) if (b) dev_free(b);
     if (P->h_stage) cudaFreeHost(P->h_stage);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     for (auto &pe : P->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -44,6 +78,7 @@ static void release(sp_program *P)
     if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
     if (cur >= 0 && cur != P->device) cudaSetDevice(cur);
     delete P;
+    g_live_host--;
 }
 
 static int64_t words64(int64_t n) { return (n + 63) / 64; }
@@ -85,6 +120,36 @@ static sp_status check_ptr(const void *p, const char *name)
     return SP_OK;
 }
 
+sp_status sample_range(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                       uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s)
+{
+    if (nshots == 0) return SP_OK;
+    if (P->path == SP_PATH_FUSED && P->fused_tw)
+        return fused_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
+    const int64_t chunk = P->chunk_shots;
+    sp_status st;
+    if (uses_staged_scratch(P)) {
+        st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)chunk));
+        if (st != SP_OK) return st;
+    }
+    const int64_t wm = words64(P->n_meas), wd = words64(P->n_det), wo = words64(P->n_obs);
+    for (uint64_t done = 0; done < nshots;) {
+        const uint64_t n = std::min<uint64_t>(nshots - done, (uint64_t)chunk);
+        st = sample_chunk(P, seed, shot0 + done, n, d_meas ? d_meas + done * wm : nullptr,
+                          d_det ? d_det + done * wd : nullptr, d_obs ? d_obs + done * wo : nullptr, s);
+        if (st != SP_OK) return st;
+        done += n;
+    }
+    return SP_OK;
+}
+
+// A configuration change makes every batch plan holding the program stale.
+static void reconfigured(sp_program *P)
+{
+    P->gen++;
+    batch_forget(P);
+}
+
 }  // namespace sp
 
 using namespace sp;
@@ -96,8 +161,9 @@ sp_status sp_build(const sp_circuit_desc *circuit, void *cuda_stream, sp_program
     if (!out) return set_error(SP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!circuit) return set_error(SP_ERR_INVALID_ARG, "circuit is NULL");
-    sp_program *P = new (std::nothrow) sp_program();
-    if (!P) return set_error(SP_ERR_OOM, "host allocation failed");
+    sp_program *P = host_alloc_fails() ? nullptr : new (std::nothrow) sp_program();
+    if (!P) return set_error(SP_ERR_OOM, "host allocation of the program failed");
+    g_live_host++;
     sp_status st = build_program(circuit, (cudaStream_t)cuda_stream, P);
     if (st != SP_OK) {
         cudaStreamSynchronize((cudaStream_t)cuda_stream);
@@ -144,23 +210,7 @@ sp_status sp_sample(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshot
         return st;
     if (nshots == 0) return SP_OK;
     if (shot0 + nshots < shot0) return set_error(SP_ERR_INVALID_ARG, "shot range overflows 64 bits");
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (P->path == SP_PATH_FUSED && P->fused_tw)
-        return fused_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
-    const int64_t chunk = P->chunk_shots;
-    if (uses_staged_scratch(P)) {
-        st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots, (uint64_t)chunk));
-        if (st != SP_OK) return st;
-    }
-    const int64_t wm = words64(P->n_meas), wd = words64(P->n_det), wo = words64(P->n_obs);
-    for (uint64_t done = 0; done < nshots;) {
-        const uint64_t n = std::min<uint64_t>(nshots - done, (uint64_t)chunk);
-        st = sample_chunk(P, seed, shot0 + done, n, d_meas ? d_meas + done * wm : nullptr,
-                          d_det ? d_det + done * wd : nullptr, d_obs ? d_obs + done * wo : nullptr, s);
-        if (st != SP_OK) return st;
-        done += n;
-    }
-    return SP_OK;
+    return sample_range(P, seed, shot0, nshots, d_meas, d_det, d_obs, (cudaStream_t)cuda_stream);
 }
 
 sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
@@ -188,10 +238,10 @@ sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t 
     }
     const size_t stage_words = (size_t)piece * (size_t)per_shot;
     if (P->d_out_stage_bytes < 2 * stage_words * 8) {
-        if (P->d_out_stage) cudaFree(P->d_out_stage);
+        if (P->d_out_stage) dev_free(P->d_out_stage);
         P->d_out_stage = nullptr;
         P->d_out_stage_bytes = 0;
-        if (cudaMalloc((void **)&P->d_out_stage, 2 * stage_words * 8) != cudaSuccess) {
+        if (dev_alloc((void **)&P->d_out_stage, 2 * stage_words * 8) != cudaSuccess) {
             cudaGetLastError();
             P->d_out_stage = nullptr;
             return set_error(SP_ERR_OOM, "cudaMalloc of the output staging buffers failed");
@@ -224,6 +274,10 @@ sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t 
     }
     SP_CUDA(cudaStreamSynchronize(P->copy_stream));
     SP_CUDA(cudaStreamSynchronize(s));
+    if (P->path == SP_PATH_TENSOR && P->d_tc_status) {
+        int32_t v = 0;
+        return sp_device_status(P, &v);
+    }
     return SP_OK;
 }
 
@@ -250,6 +304,12 @@ sp_status sp_expect(sp_program *P, const float *d_p, float *d_logE, void *cuda_s
 {
     if (!P || !d_logE) return set_error(SP_ERR_INVALID_ARG, "NULL argument");
     return expect_fwd(P, d_p, d_logE, (cudaStream_t)cuda_stream);
+}
+
+sp_status sp_expect_sign(sp_program *P, const float *d_p, float *d_sign, void *cuda_stream)
+{
+    if (!P || !d_sign) return set_error(SP_ERR_INVALID_ARG, "NULL argument");
+    return expect_sign(P, d_p, d_sign, (cudaStream_t)cuda_stream);
 }
 
 sp_status sp_expect_grad(sp_program *P, const float *d_p, const float *d_grad_logE, float *d_grad_p,
@@ -295,7 +355,11 @@ sp_status sp_export_channels(const sp_program *P, uint32_t *h_T, uint8_t *h_kind
 sp_status sp_set_path(sp_program *P, int32_t path)
 {
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
-    if (path == SP_PATH_AUTO) { P->path = P->build_path; return SP_OK; }
+    if (path == SP_PATH_AUTO) {
+        P->path = P->build_path;
+        reconfigured(P);
+        return SP_OK;
+    }
     if (path == SP_PATH_FUSED && !P->fused_tw)
         return set_error(SP_ERR_INVALID_ARG, "the fused path is unavailable for this program");
     if (path == SP_PATH_TENSOR && !tensor_path_available(P))
@@ -303,6 +367,7 @@ sp_status sp_set_path(sp_program *P, int32_t path)
     if (path != SP_PATH_SPARSE && path != SP_PATH_FUSED && path != SP_PATH_DENSE && path != SP_PATH_TENSOR)
         return set_error(SP_ERR_INVALID_ARG, "unsupported path");
     P->path = path;
+    reconfigured(P);
     return SP_OK;
 }
 
@@ -311,7 +376,9 @@ sp_status sp_set_fused_config(sp_program *P, int32_t tile_shots, int32_t variant
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
     if (tile_shots != 32 && tile_shots != 64 && tile_shots != 128)
         return set_error(SP_ERR_INVALID_ARG, "tile_shots must be 32, 64 or 128");
-    return fused_select(P, tile_shots / 32, variant);
+    const sp_status st = fused_select(P, tile_shots / 32, variant);
+    if (st == SP_OK) reconfigured(P);
+    return st;
 }
 
 sp_status sp_device_status(sp_program *P, int32_t *status)
@@ -324,15 +391,23 @@ sp_status sp_device_status(sp_program *P, int32_t *status)
     SP_CUDA(cudaMemcpy(&v, P->d_tc_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (v) SP_CUDA(cudaMemset(P->d_tc_status, 0, sizeof(int)));
     *status = v;
+    if (v) return set_error(SP_ERR_TIMEOUT, "a tensor-core tile gave up on a bounded wait; its records were not written");
+    return SP_OK;
+}
+
+sp_status sp_set_wait_limit(sp_program *P, uint64_t ns)
+{
+    if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
+    P->tc_wait_ns = ns;
     return SP_OK;
 }
 
 sp_status sp_set_chunk(sp_program *P, uint64_t chunk_shots)
 {
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
-    if (chunk_shots == 0) { P->chunk_shots = default_chunk(P); return SP_OK; }
     if (chunk_shots % 1024) return set_error(SP_ERR_INVALID_ARG, "chunk_shots must be a multiple of 1024");
-    P->chunk_shots = (int64_t)chunk_shots;
+    P->chunk_shots = chunk_shots ? (int64_t)chunk_shots : default_chunk(P);
+    reconfigured(P);
     return SP_OK;
 }
 
@@ -364,6 +439,26 @@ sp_status sp_profile_read(sp_program *P, double *ms, uint64_t *launches)
         if (ms) ms[k] = acc[k];
         if (launches) launches[k] = cnt[k];
     }
+    return SP_OK;
+}
+
+sp_status sp_debug_fail_alloc(int64_t after)
+{
+    g_fail_after.store(after < 0 ? -1 : after);
+    return SP_OK;
+}
+
+sp_status sp_debug_live_allocs(int64_t *device_allocs, int64_t *host_programs)
+{
+    if (device_allocs) *device_allocs = g_live_dev.load();
+    if (host_programs) *host_programs = g_live_host.load();
+    return SP_OK;
+}
+
+sp_status sp_batch_plans(uint32_t *count, uint32_t *capacity)
+{
+    if (count) *count = (uint32_t)batch_plan_count();
+    if (capacity) *capacity = (uint32_t)BATCH_MAX_PLANS;
     return SP_OK;
 }
 

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_popc_product(const uint32_t *__restrict
 // Tensor-core product (tcgen05, kind::f8f6f4, E4M3 operands, FP32 in TMEM)
 // ---------------------------------------------------------------------------
 // Tile: M = 128 shots x N = 256 record rows of one record kind, K in stages of
-// TC_KS = 128 symbols held in a ring of TC_NS stage buffers.  Operands are
+// TC_KS = 192 symbols held in a ring of TC_NS = 3 stage buffers.  Operands are
 // K-major with no swizzle, in 8-row x 16-byte core matrices; in a stage
 // buffer the core matrix (row group rg, K group kg) sits at
 // kg * LBO + rg * TC_SBO, LBO = (rows / 8) * 128 bytes.
@@ -107,7 +107,7 @@ constexpr uint32_t TC_BBYTES = TC_N * TC_KS;                       // 32 KB: row
 constexpr uint32_t TC_SBO = 128, TC_ALBO = (TC_M / 8) * 128, TC_BLBO = (TC_N / 8) * 128;
 constexpr int TC_KG = TC_KS / 16;                                    // K groups per stage
 constexpr uint32_t TC_TMEM_COLS = TC_N;
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;                      // 2 s bound on every wait
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // 2 s: default bound on the stage waits, and the drain's bound
 constexpr uint32_t E4M3_ONE = 0x38u;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -138,13 +138,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 }
 
 // Wait for the phase with the given parity to complete, for at most
-// TC_WAIT_NS; false if the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// limit_ns; false if the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > TC_WAIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 
@@ -224,8 +224,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32])
 }
 
 // The coefficient rows of one record kind as tile-ready E4M3 stage blocks:
-// block (tile, ks) holds rows tile*128.. of the kind and symbols (with s_0)
-// ks*256.., in the stage-buffer layout; rows past the kind and symbols past
+// block (tile, ks) holds rows tile*TC_N.. of the kind and symbols (with s_0)
+// ks*TC_KS.., in the stage-buffer layout; rows past the kind and symbols past
 // the row are zero.
 __global__ void k_coef_e4m3(const uint32_t *__restrict__ A, int64_t apitch, int64_t row0, int64_t nrow,
                             int64_t ntiles, int64_t nks, uint4 *__restrict__ out)
@@ -258,10 +258,14 @@ __global__ void k_coef_e4m3(const uint32_t *__restrict__ A, int64_t apitch, int6
 // the exact FP32 counts and keeps their parity.  Every wait is bounded; a
 // timeout raises the CTA's abort flag, every loop stops at its next check,
 // the issuer drains its own copies and MMAs (again bounded), status 1 is
-// recorded and TMEM is freed.
+// recorded and TMEM is freed.  wait_ns bounds the stage waits (tests shorten
+// it to make them run out); the drain of copies and MMAs already issued
+// keeps the fixed bound TC_WAIT_NS, since they must land before TMEM is
+// freed and the CTA exits.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_product(const uint32_t *__restrict__ Bd, int64_t bpitch, int64_t ngroups, const uint4 *__restrict__ coef,
-                 int64_t nks, int64_t words32, uint64_t nshots, uint32_t *__restrict__ out, int *status)
+                 int64_t nks, int64_t words32, uint64_t nshots, uint32_t *__restrict__ out, int *status,
+                 uint64_t wait_ns)
 {
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (*abort_flag) break;
             const int b = (int)(ks % TC_NS);
             // the MMAs of stage ks - TC_NS read this buffer last
-            if (ks >= TC_NS && !mbar_wait(done + 8 * b, (uint32_t)(((ks / TC_NS) - 1) & 1))) {
+            if (ks >= TC_NS && !mbar_wait(done + 8 * b, (uint32_t)(((ks / TC_NS) - 1) & 1), wait_ns)) {
                 failed = true;
                 *abort_flag = 1;
                 break;
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (*abort_flag) break;
             const int b = (int)(ks % TC_NS);
             const uint32_t par = (uint32_t)((ks / TC_NS) & 1);
-            if (!mbar_wait(afull + 8 * b, par) || !mbar_wait(full + 8 * b, par)) {
+            if (!mbar_wait(afull + 8 * b, par, wait_ns) || !mbar_wait(full + 8 * b, par, wait_ns)) {
                 failed = true;
                 *abort_flag = 1;
                 break;
@@ -369,7 +373,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // the MMAs of stage ks keep the tensor pipe busy meanwhile
             const int64_t j = ks + TC_NS - 1;
             if (j < nks) {
-                if (ks >= 1 && !mbar_wait(done + 8 * (int)((ks - 1) % TC_NS), (uint32_t)(((ks - 1) / TC_NS) & 1))) {
+                if (ks >= 1 &&
+                    !mbar_wait(done + 8 * (int)((ks - 1) % TC_NS), (uint32_t)(((ks - 1) / TC_NS) & 1), wait_ns)) {
                     failed = true;
                     *abort_flag = 1;
                     break;
@@ -380,10 +385,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // drain: the last committed stage covers every MMA before it
         if (issued > 0) {
             const int64_t last = issued - 1;
-            if (!mbar_wait(done + 8 * (int)(last % TC_NS), (uint32_t)((last / TC_NS) & 1))) failed = true;
+            if (!mbar_wait(done + 8 * (int)(last % TC_NS), (uint32_t)((last / TC_NS) & 1), TC_WAIT_NS)) failed = true;
         }
         for (int64_t j = landed; j < copied; j++)
-            if (!mbar_wait(full + 8 * (int)(j % TC_NS), (uint32_t)((j / TC_NS) & 1))) failed = true;
+            if (!mbar_wait(full + 8 * (int)(j % TC_NS), (uint32_t)((j / TC_NS) & 1), TC_WAIT_NS)) failed = true;
         if (issued != nks) failed = true;
     }
     const bool all_ok = !__syncthreads_or(failed || *abort_flag);
@@ -421,7 +426,7 @@ sp_status ensure_dense(sp_program *P, size_t shots, cudaStream_t s)
 {
     if (!P->d_AT) {
         P->rpitch = ceil_div(std::max<int64_t>(P->n_rows, 1), 32) * 32;
-        if (cudaMalloc((void **)&P->d_AT, (size_t)P->apitch * (size_t)P->rpitch * 4) != cudaSuccess) {
+        if (dev_alloc((void **)&P->d_AT, (size_t)P->apitch * (size_t)P->rpitch * 4) != cudaSuccess) {
             cudaGetLastError();
             P->d_AT = nullptr;
             return set_error(SP_ERR_OOM, "cudaMalloc of the transposed coefficient words failed");
@@ -431,11 +436,11 @@ sp_status ensure_dense(sp_program *P, size_t shots, cudaStream_t s)
         SP_CUDA(cudaGetLastError());
     }
     if (P->dense_shots < shots || !P->d_Bd) {
-        cudaFree(P->d_Bd);
+        dev_free(P->d_Bd);
         P->d_Bd = nullptr;
         P->dense_shots = 0;
         const size_t groups = (shots + 31) / 32;
-        if (cudaMalloc((void **)&P->d_Bd, groups * (size_t)P->apitch * 32u * 4u) != cudaSuccess) {
+        if (dev_alloc((void **)&P->d_Bd, groups * (size_t)P->apitch * 32u * 4u) != cudaSuccess) {
             cudaGetLastError();
             P->d_Bd = nullptr;
             return set_error(SP_ERR_OOM, "cudaMalloc of the shot-major fault-bit scratch failed");
@@ -467,11 +472,11 @@ static sp_status ensure_tensor(sp_program *P, cudaStream_t s)
     P->tc_nks = ceil_div(P->apitch, TC_KS / 32);
     for (int k = 0; k < 3; k++) {
         P->tc_ntiles[k] = nrow[k] ? ceil_div(2 * ceil_div(nrow[k], 64), TC_N / 32) : 0;
-        cudaFree(P->d_tc_coef[k]);
+        dev_free(P->d_tc_coef[k]);
         P->d_tc_coef[k] = nullptr;
         if (!P->tc_ntiles[k]) continue;
         const int64_t chunks = P->tc_ntiles[k] * P->tc_nks * (TC_BBYTES / 16);
-        if (cudaMalloc((void **)&P->d_tc_coef[k], (size_t)chunks * 16) != cudaSuccess) {
+        if (dev_alloc((void **)&P->d_tc_coef[k], (size_t)chunks * 16) != cudaSuccess) {
             cudaGetLastError();
             P->d_tc_coef[k] = nullptr;
             return set_error(SP_ERR_OOM, "cudaMalloc of the tensor-core coefficient blocks failed");
@@ -483,7 +488,7 @@ static sp_status ensure_tensor(sp_program *P, cudaStream_t s)
     }
     if (!P->d_tc_status) {
         int *st = nullptr;
-        if (cudaMalloc((void **)&st, sizeof(int)) != cudaSuccess) {
+        if (dev_alloc((void **)&st, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             return set_error(SP_ERR_OOM, "cudaMalloc of the device status word failed");
         }
@@ -519,7 +524,7 @@ sp_status dense_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
             k_tc_product<<<grid, TC_THREADS, TC_SMEM, s>>>(P->d_Bd, P->apitch, groups,
                                                           reinterpret_cast<const uint4 *>(P->d_tc_coef[k]), P->tc_nks,
                                                           words32, nshots, reinterpret_cast<uint32_t *>(g.dst),
-                                                          P->d_tc_status);
+                                                          P->d_tc_status, P->tc_wait_ns ? P->tc_wait_ns : TC_WAIT_NS);
             SP_CUDA(cudaGetLastError());
         }
         return SP_OK;
@@ -557,9 +562,9 @@ sp_status run_path(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t shots,
 
 void drop_dense_buffers(sp_program *P)
 {
-    cudaFree(P->d_Bd);
-    cudaFree(P->d_AT);
-    for (auto &c : P->d_tc_coef) { cudaFree(c); c = nullptr; }
+    dev_free(P->d_Bd);
+    dev_free(P->d_AT);
+    for (auto &c : P->d_tc_coef) { dev_free(c); c = nullptr; }
     P->tc_ready = false;
     P->d_Bd = nullptr;
     P->d_AT = nullptr;
@@ -586,7 +591,7 @@ sp_status choose_path(sp_program *P, cudaStream_t s)
     const uint64_t shots = 32768;
     const int64_t words = (P->n_meas + 63) / 64 + (P->n_det + 63) / 64 + (P->n_obs + 63) / 64;
     uint64_t *out = nullptr;
-    if (cudaMalloc((void **)&out, (size_t)shots * (size_t)std::max<int64_t>(words, 1) * 8) != cudaSuccess) {
+    if (dev_alloc((void **)&out, (size_t)shots * (size_t)std::max<int64_t>(words, 1) * 8) != cudaSuccess) {
         cudaGetLastError();
         return set_error(SP_ERR_OOM, "cudaMalloc of the path probe outputs failed");
     }
@@ -617,8 +622,9 @@ sp_status choose_path(sp_program *P, cudaStream_t s)
         if (st != SP_OK) break;
         if (cand[ci] == SP_PATH_TENSOR) {
             int32_t bad = 0;
-            if ((st = sp_device_status(P, &bad)) != SP_OK) break;
-            if (bad) continue;   // a tile gave up on a bounded wait: never pick this form
+            st = sp_device_status(P, &bad);
+            if (st == SP_ERR_TIMEOUT) { st = SP_OK; continue; }   // a tile gave up on a bounded wait: never pick this form
+            if (st != SP_OK) break;
         }
         P->path_probe_ms[cand[ci]] = ms;
         if (ci == 0 || ms < 0.97f * best) { best = ms; pick = cand[ci]; }
@@ -626,7 +632,7 @@ sp_status choose_path(sp_program *P, cudaStream_t s)
     P->profiling = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(out);
+    dev_free(out);
     if (st != SP_OK) return st;
     P->build_path = pick;
     P->path = pick;

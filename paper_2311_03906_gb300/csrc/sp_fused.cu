@@ -595,15 +595,16 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fus
         fused_tile<TW, fused_threads(TW, U)>(p, tile, sm);
 }
 
-// Batched form: many programs in one persistent launch.  Work items are
-// (program, 64-shot tile) pairs handed out in order by an atomic counter;
-// items of program i are [tileEnd[i-1], tileEnd[i]).  The launcher orders
-// the programs by decreasing cost per tile so the tail is made of the
-// cheapest items.
-template <int MINB>
-__global__ void __launch_bounds__(FUSED_THREADS, MINB) k_fused_batch(const FusedParams *__restrict__ progs, int nprog,
-                                                                  const uint64_t *__restrict__ tileEnd,
-                                                                  unsigned long long *counter)
+// Batched form: many programs in one persistent launch per launch shape.
+// Work items are (program, tile) pairs handed out in order by an atomic
+// counter; items of member i are [tileEnd[i-1], tileEnd[i]).  Every member
+// of one launch uses the tile size and launch shape its own build-time
+// autotuner chose (TW, U); the launcher orders the members by decreasing
+// cost per tile so the tail is made of the cheapest items.
+template <int TW, int U>
+__global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U))
+    k_fused_batch(const FusedParams *__restrict__ progs, int nprog, const uint64_t *__restrict__ tileEnd,
+                  unsigned long long *counter)
 {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ unsigned long long s_item;
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, MINB) k_fused_batch(const Fused
             const int mid = (lo + hi) >> 1;
             if (tileEnd[mid] > item) hi = mid; else lo = mid + 1;
         }
-        fused_tile<2>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
+        fused_tile<TW, fused_threads(TW, U)>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
     }
 }
 
@@ -713,7 +714,7 @@ template <typename T>
 sp_status upload(T **dst, const std::vector<T> &src, cudaStream_t s)
 {
     const size_t n = std::max<size_t>(src.size(), 1);
-    if (cudaMalloc((void **)dst, n * sizeof(T)) != cudaSuccess) {
+    if (dev_alloc((void **)dst, n * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         *dst = nullptr;
         return set_error(SP_ERR_OOM, "cudaMalloc of the sampler program failed");
@@ -949,7 +950,7 @@ sp_status autotune(sp_program *P, cudaStream_t s)
     const uint64_t shots = (uint64_t)P->num_sms * 2u * 64u * 4u;
     const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
     uint64_t *out = nullptr;
-    if (cudaMalloc((void **)&out, (size_t)shots * (size_t)std::max<int64_t>(wm + wd + wo, 1) * 8) != cudaSuccess) {
+    if (dev_alloc((void **)&out, (size_t)shots * (size_t)std::max<int64_t>(wm + wd + wo, 1) * 8) != cudaSuccess) {
         cudaGetLastError();
         return set_error(SP_ERR_OOM, "cudaMalloc of the autotuner outputs failed");
     }
@@ -987,7 +988,7 @@ sp_status autotune(sp_program *P, cudaStream_t s)
     P->profiling = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(out);
+    dev_free(out);
     if (st != SP_OK) return st;
     {
         std::lock_guard<std::mutex> lock(mu);
@@ -1043,54 +1044,110 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
 // ---------------------------------------------------------------------------
 // Batched sampling: plan, capture, replay
 // ---------------------------------------------------------------------------
+// A plan belongs to one (device, program set, configuration generations,
+// shot counts).  It holds, per launch shape, the members' FusedParams in
+// device memory, their tile ends and a work counter, and a CUDA graph that
+// zeroes the counters and runs one persistent k_fused_batch per shape.  The
+// graph reads seeds and output pointers from the parameter block, which
+// every call refreshes with one copy on the caller's stream before it
+// launches the graph, so new seeds or buffers reuse the plan.  The graph
+// touches only build-time tables of its programs (no per-program scratch),
+// and a program's plans are dropped when it is freed or reconfigured.
+// Members without a fused kernel (or set to another path) are sampled
+// through their own path on the caller's stream after the graph.
 namespace {
 
-struct BatchClass {
-    FusedParams *d_params = nullptr;
-    uint64_t *d_tileEnd = nullptr;
-    unsigned long long *d_counter = nullptr;
-    int nprog = 0;
+typedef void (*BatchFn)(const FusedParams *, int, const uint64_t *, unsigned long long *);
+
+BatchFn batch_kernel(int tw, int unroll)
+{
+    if (tw == 4) return unroll == 2 ? k_fused_batch<4, 2> : k_fused_batch<4, 1>;
+    if (tw == 2) return unroll == 3 ? k_fused_batch<2, 3> : unroll == 2 ? k_fused_batch<2, 2> : k_fused_batch<2, 1>;
+    return unroll == 2 ? k_fused_batch<1, 2> : k_fused_batch<1, 1>;
+}
+
+struct BatchGroup {
+    int tw = 0, unroll = 0, threads = 0, ctas = 0;
     size_t smem = 0;
-    int minb = 1;
     int grid = 0;
+    std::vector<uint32_t> members;   // indices into the call's arrays, by decreasing cost per tile
+    size_t param0 = 0;               // first entry of this group in the parameter block
 };
 
+
 struct BatchPlan {
+    int device = 0;
     std::vector<uint64_t> key;
     std::vector<const sp_program *> progs;
-    BatchClass cls[2];                 // [0] two CTAs per SM fit, [1] one
+    std::vector<BatchGroup> groups;
+    std::vector<uint32_t> others;              // members sampled through their own path
+    size_t nparams = 0;
+    FusedParams *d_params = nullptr;           // [nparams], refreshed by every call
+    uint64_t *d_tileEnd = nullptr;             // [nparams]
+    unsigned long long *d_counter = nullptr;   // [groups]
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
     ~BatchPlan()
     {
-        for (auto &c : cls) {
-            cudaFree(c.d_params);
-            cudaFree(c.d_tileEnd);
-            cudaFree(c.d_counter);
-        }
+        // launches of this plan may still be in flight
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != device) cudaSetDevice(device);
+        cudaDeviceSynchronize();
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        dev_free(d_params);
+        dev_free(d_tileEnd);
+        dev_free(d_counter);
+        if (cur >= 0 && cur != device) cudaSetDevice(cur);
+        cudaGetLastError();
     }
 };
 
 std::mutex g_batch_mu;
 std::vector<BatchPlan *> g_plans;
+uint64_t g_batch_clock = 0;
 cudaStream_t g_capture_stream[64] = {};
+
+// The per-call part of the members' parameters: seeds and output pointers.
+void fill_params(const BatchPlan &plan, sp_program *const *progs, const uint64_t *seeds, const uint64_t *nshots,
+                 uint64_t *const *d_meas, uint64_t *const *d_det, uint64_t *const *d_obs,
+                 std::vector<FusedParams> &out)
+{
+    out.resize(plan.nparams);
+    for (const BatchGroup &g : plan.groups)
+        for (size_t k = 0; k < g.members.size(); k++) {
+            const uint32_t i = g.members[k];
+            out[g.param0 + k] = fused_params(progs[i], g.tw, seeds[i], 0, nshots[i], d_meas ? d_meas[i] : nullptr,
+                                             d_det ? d_det[i] : nullptr, d_obs ? d_obs[i] : nullptr);
+        }
+}
 
 }  // namespace
 
-void batch_forget(const sp_program *P)
+size_t batch_plan_count()
 {
     std::lock_guard<std::mutex> lock(g_batch_mu);
-    for (size_t i = 0; i < g_plans.size();) {
-        BatchPlan *b = g_plans[i];
-        if (std::find(b->progs.begin(), b->progs.end(), P) != b->progs.end()) {
-            delete b;
-            g_plans.erase(g_plans.begin() + i);
-        } else {
-            i++;
+    return g_plans.size();
+}
+
+void batch_forget(const sp_program *P)
+{
+    std::vector<BatchPlan *> drop;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        for (size_t i = 0; i < g_plans.size();) {
+            BatchPlan *b = g_plans[i];
+            if (std::find(b->progs.begin(), b->progs.end(), P) != b->progs.end()) {
+                drop.push_back(b);
+                g_plans.erase(g_plans.begin() + i);
+            } else {
+                i++;
+            }
         }
     }
+    for (BatchPlan *b : drop) delete b;
 }
 
 sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *seeds, const uint64_t *nshots,
@@ -1103,112 +1160,113 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
     key.push_back((uint64_t)dev);
     for (uint32_t i = 0; i < n; i++) {
         if (progs[i]->device != dev) return set_error(SP_ERR_INVALID_ARG, "all programs must live on the current device");
-        key.insert(key.end(), {(uint64_t)(uintptr_t)progs[i], seeds[i], nshots[i],
-                               (uint64_t)(uintptr_t)(d_meas ? d_meas[i] : nullptr),
-                               (uint64_t)(uintptr_t)(d_det ? d_det[i] : nullptr),
-                               (uint64_t)(uintptr_t)(d_obs ? d_obs[i] : nullptr)});
+        key.insert(key.end(), {(uint64_t)(uintptr_t)progs[i], progs[i]->gen, nshots[i]});
     }
-    std::lock_guard<std::mutex> lock(g_batch_mu);
+    std::vector<FusedParams> hp;
+    std::unique_lock<std::mutex> lock(g_batch_mu);
+    BatchPlan *plan = nullptr;
     for (BatchPlan *b : g_plans)
-        if (b->key == key) {
-            SP_CUDA(cudaGraphLaunch(b->exec, s));
-            return SP_OK;
+        if (b->key == key) { plan = b; break; }
+    if (!plan) {
+        // ---- new plan ------------------------------------------------------
+        std::unique_ptr<BatchPlan> np(new BatchPlan());
+        np->device = dev;
+        np->key = key;
+        std::map<std::tuple<int, int, int>, BatchGroup> by_shape;
+        for (uint32_t i = 0; i < n; i++) {
+            const sp_program *P = progs[i];
+            np->progs.push_back(P);
+            if (nshots[i] == 0) continue;
+            if (P->path == SP_PATH_FUSED && P->fused_tw) {
+                BatchGroup &g = by_shape[std::make_tuple(P->fused_tw, P->fused_unroll, P->fused_ctas_per_sm)];
+                g.tw = P->fused_tw;
+                g.unroll = P->fused_unroll;
+                g.threads = P->fused_threads;
+                g.ctas = P->fused_ctas_per_sm;
+                g.smem = std::max(g.smem, P->fused_smem);
+                g.members.push_back(i);
+            } else {
+                np->others.push_back(i);
+            }
         }
-    // ---- new plan ---------------------------------------------------------
-    std::unique_ptr<BatchPlan> plan(new BatchPlan());
-    plan->key = key;
-    int smem_max = 0, nsm = 0;
-    SP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    SP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    struct Entry { uint32_t i; double cost; };
-    std::vector<Entry> fused[2];
-    std::vector<uint32_t> staged;
-    for (uint32_t i = 0; i < n; i++) {
-        const sp_program *P = progs[i];
-        plan->progs.push_back(P);
-        if (nshots[i] == 0) continue;
-        const bool fused_ok = P->path == SP_PATH_FUSED && P->fused_tw;
-        const size_t bytes = fused_ok ? fused_words(P, 2) * 4 : 0;
-        if (fused_ok && bytes <= (size_t)smem_max / 2 - 1024) fused[0].push_back({i, (double)P->n_blk});
-        else if (fused_ok && bytes <= (size_t)smem_max) fused[1].push_back({i, (double)P->n_blk});
-        else staged.push_back(i);
+        std::vector<uint64_t> tileEnd;
+        for (auto &kv : by_shape) {
+            BatchGroup g = kv.second;
+            std::stable_sort(g.members.begin(), g.members.end(),
+                             [&](uint32_t a, uint32_t b) { return progs[a]->n_blk > progs[b]->n_blk; });
+            g.param0 = tileEnd.size();
+            uint64_t acc = 0;
+            for (uint32_t i : g.members) {
+                acc += (nshots[i] + 32u * g.tw - 1) / (32u * g.tw);
+                tileEnd.push_back(acc);
+            }
+            BatchFn fn = batch_kernel(g.tw, g.unroll);
+            SP_CUDA(max_dynamic_smem(fn));
+            int occ = 0;
+            SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, g.threads, g.smem));
+            int nsm = 0;
+            SP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            g.grid = (int)std::min<uint64_t>(acc, (uint64_t)nsm * (uint64_t)std::max(occ, 1));
+            np->groups.push_back(g);
+        }
+        np->nparams = tileEnd.size();
+        if (np->nparams) {
+            if (dev_alloc((void **)&np->d_params, np->nparams * sizeof(FusedParams)) != cudaSuccess ||
+                dev_alloc((void **)&np->d_tileEnd, np->nparams * 8) != cudaSuccess ||
+                dev_alloc((void **)&np->d_counter, np->groups.size() * 8) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(SP_ERR_OOM, "cudaMalloc of the batch plan failed");
+            }
+            SP_CUDA(cudaMemcpy(np->d_tileEnd, tileEnd.data(), tileEnd.size() * 8, cudaMemcpyHostToDevice));
+            // ---- capture on a library stream, replay on the caller's -------
+            if (!g_capture_stream[dev])
+                SP_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
+            cudaStream_t cs = g_capture_stream[dev];
+            SP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            sp_status st = SP_OK;
+            if (cudaMemsetAsync(np->d_counter, 0, np->groups.size() * 8, cs) != cudaSuccess)
+                st = set_error(SP_ERR_CUDA, "counter reset failed during capture");
+            for (size_t k = 0; k < np->groups.size() && st == SP_OK; k++) {
+                const BatchGroup &g = np->groups[k];
+                batch_kernel(g.tw, g.unroll)<<<g.grid, g.threads, g.smem, cs>>>(
+                    np->d_params + g.param0, (int)g.members.size(), np->d_tileEnd + g.param0, np->d_counter + k);
+                if (cudaGetLastError() != cudaSuccess) st = set_error(SP_ERR_CUDA, "batch kernel launch failed during capture");
+            }
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+            if (st != SP_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ec != cudaSuccess) return cuda_error(ec, "cudaStreamEndCapture");
+            np->graph = graph;
+            SP_CUDA(cudaGraphInstantiate(&np->exec, graph, 0));
+        }
+        // bounded cache: drop the least recently used plan
+        if (g_plans.size() >= BATCH_MAX_PLANS) {
+            auto lru = std::min_element(g_plans.begin(), g_plans.end(),
+                                        [](const BatchPlan *a, const BatchPlan *b) { return a->last_use < b->last_use; });
+            BatchPlan *old = *lru;
+            g_plans.erase(lru);
+            delete old;
+        }
+        plan = np.release();
+        g_plans.push_back(plan);
     }
-    for (uint32_t i : staged) {
-        sp_program *P = progs[i];
-        sp_status st = ensure_scratch(P, (size_t)std::min<uint64_t>(nshots[i], (uint64_t)P->chunk_shots));
+    plan->last_use = ++g_batch_clock;
+    if (plan->exec) {
+        fill_params(*plan, progs, seeds, nshots, d_meas, d_det, d_obs, hp);
+        // pageable source: staged by the runtime before the call returns
+        SP_CUDA(cudaMemcpyAsync(plan->d_params, hp.data(), hp.size() * sizeof(FusedParams), cudaMemcpyHostToDevice, s));
+        SP_CUDA(cudaGraphLaunch(plan->exec, s));
+    }
+    const std::vector<uint32_t> others = plan->others;
+    lock.unlock();
+    for (uint32_t i : others) {
+        sp_status st = sample_range(progs[i], seeds[i], 0, nshots[i], d_meas ? d_meas[i] : nullptr,
+                                    d_det ? d_det[i] : nullptr, d_obs ? d_obs[i] : nullptr, s);
         if (st != SP_OK) return st;
     }
-    for (int c = 0; c < 2; c++) {
-        auto &v = fused[c];
-        if (v.empty()) continue;
-        std::stable_sort(v.begin(), v.end(), [](const Entry &a, const Entry &b) { return a.cost > b.cost; });
-        std::vector<FusedParams> params;
-        std::vector<uint64_t> tileEnd;
-        uint64_t acc = 0;
-        size_t smem = 0;
-        for (const Entry &e : v) {
-            sp_program *P = progs[e.i];
-            const size_t bytes = fused_words(P, 2) * 4;
-            params.push_back(fused_params(P, 2, seeds[e.i], 0, nshots[e.i], d_meas ? d_meas[e.i] : nullptr,
-                                          d_det ? d_det[e.i] : nullptr, d_obs ? d_obs[e.i] : nullptr));
-            acc += (nshots[e.i] + 63) / 64;
-            tileEnd.push_back(acc);
-            smem = std::max(smem, bytes);
-        }
-        BatchClass &bc = plan->cls[c];
-        bc.nprog = (int)params.size();
-        bc.smem = smem;
-        bc.minb = c == 0 ? 2 : 1;
-        bc.grid = (int)std::min<uint64_t>(acc, (uint64_t)nsm * (uint64_t)bc.minb);
-        if (cudaMalloc((void **)&bc.d_params, params.size() * sizeof(FusedParams)) != cudaSuccess ||
-            cudaMalloc((void **)&bc.d_tileEnd, tileEnd.size() * 8) != cudaSuccess ||
-            cudaMalloc((void **)&bc.d_counter, 8) != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(SP_ERR_OOM, "cudaMalloc of the batch plan failed");
-        }
-        SP_CUDA(cudaMemcpy(bc.d_params, params.data(), params.size() * sizeof(FusedParams), cudaMemcpyHostToDevice));
-        SP_CUDA(cudaMemcpy(bc.d_tileEnd, tileEnd.data(), tileEnd.size() * 8, cudaMemcpyHostToDevice));
-        if (c == 0) SP_CUDA(max_dynamic_smem(k_fused_batch<2>));
-        else SP_CUDA(max_dynamic_smem(k_fused_batch<1>));
-    }
-    // ---- capture on a library stream, replay on the caller's --------------
-    if (!g_capture_stream[dev]) SP_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
-    cudaStream_t cs = g_capture_stream[dev];
-    SP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    sp_status st = SP_OK;
-    for (int c = 0; c < 2 && st == SP_OK; c++) {
-        BatchClass &bc = plan->cls[c];
-        if (!bc.nprog) continue;
-        if (cudaMemsetAsync(bc.d_counter, 0, 8, cs) != cudaSuccess) { st = cuda_error(cudaGetLastError(), "memset"); break; }
-        if (c == 0) k_fused_batch<2><<<bc.grid, FUSED_THREADS, bc.smem, cs>>>(bc.d_params, bc.nprog, bc.d_tileEnd, bc.d_counter);
-        else k_fused_batch<1><<<bc.grid, FUSED_THREADS, bc.smem, cs>>>(bc.d_params, bc.nprog, bc.d_tileEnd, bc.d_counter);
-        if (cudaGetLastError() != cudaSuccess) st = set_error(SP_ERR_CUDA, "batch kernel launch failed during capture");
-    }
-    for (uint32_t i : staged) {
-        if (st != SP_OK) break;
-        sp_program *P = progs[i];
-        const int64_t pitch = (int64_t)((P->scratch_shots + 31) / 32);
-        const int64_t wm = (P->n_meas + 63) / 64, wd = (P->n_det + 63) / 64, wo = (P->n_obs + 63) / 64;
-        for (uint64_t done = 0; done < nshots[i] && st == SP_OK;) {
-            const uint64_t k = std::min<uint64_t>(nshots[i] - done, (uint64_t)pitch * 32u);
-            st = sample_chunk_into(P, P->d_B, P->d_recT, pitch, seeds[i], done, k,
-                                   d_meas && d_meas[i] ? d_meas[i] + done * wm : nullptr,
-                                   d_det && d_det[i] ? d_det[i] + done * wd : nullptr,
-                                   d_obs && d_obs[i] ? d_obs[i] + done * wo : nullptr, cs);
-            done += k;
-        }
-    }
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
-    if (st != SP_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
-    }
-    if (ec != cudaSuccess) return cuda_error(ec, "cudaStreamEndCapture");
-    plan->graph = graph;
-    SP_CUDA(cudaGraphInstantiate(&plan->exec, graph, 0));
-    SP_CUDA(cudaGraphLaunch(plan->exec, s));
-    g_plans.push_back(plan.release());
     return SP_OK;
 }
 

@@ -93,7 +93,7 @@ struct sp_program {
     uint32_t *d_incT = nullptr;     // [n_ch][incTPitch]
     int64_t incPitch = 0, incTPitch = 0;
     float *d_kappa = nullptr;       // [n_ch]
-    float *d_wbuf = nullptr;        // [2 * n_ch] channel weights and derivatives
+    float *d_wbuf = nullptr;        // [3 * n_ch] channel weights, derivatives, sign classes
     // scratch (owned, reused across sample calls)
     uint32_t *d_B = nullptr;        // fault bits, bit-sliced: [n_sym][chunk/32]
     uint32_t *d_recT = nullptr;     // records, bit-sliced: [n_rows][chunk/32]
@@ -102,15 +102,17 @@ struct sp_program {
     uint32_t *d_AT = nullptr;       // dense paths: coefficient words transposed, [apitch][rpitch]
     int64_t rpitch = 0;             // rows of d_AT (n_rows rounded up to 32)
     uint8_t *d_tc_coef[3] = {nullptr, nullptr, nullptr};  // tensor path: E4M3 stage blocks per record kind
-    int64_t tc_ntiles[3] = {0, 0, 0};                     // 128-row tiles per record kind
-    int64_t tc_nks = 0;                                   // 256-symbol K stages
+    int64_t tc_ntiles[3] = {0, 0, 0};                     // 256-row tiles per record kind
+    int64_t tc_nks = 0;                                   // 192-symbol K stages
     int *d_tc_status = nullptr;                           // tensor kernel status word (0 = ok)
+    uint64_t tc_wait_ns = 0;                              // bound of the tensor kernel's stage waits (0 = 2 s)
     bool tc_ready = false;                                // d_tc_coef built for the current program
     double path_probe_ms[5] = {0, 0, 0, 0, 0};            // build-time probe per path (0 = not timed)
     size_t scratch_shots = 0;
     int64_t chunk_shots = 0;
     int path = SP_PATH_SPARSE;
     int build_path = SP_PATH_SPARSE;
+    uint64_t gen = 0;               // configuration generation: bumped by sp_set_path / _fused_config / _chunk
     double build_ms = 0.0;
     double density = 0.0;
     // host-side copies used for host entry points and batching
@@ -167,6 +169,15 @@ sp_status cuda_error(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::sp::cuda_error(_e, #call);     \
     } while (0)
 
+// Every device allocation of the library goes through dev_alloc / dev_free
+// (sp_capi.cu): they count the allocations held and honour the allocation-
+// failure hook of sp_debug_fail_alloc, which makes one chosen allocation
+// fail as if the device were out of memory.  host_alloc_fails() is the same
+// hook for the host-side program object.
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+bool host_alloc_fails();
+
 // build (sp_build.cu)
 sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_program *P);
 
@@ -190,6 +201,9 @@ inline bool uses_staged_scratch(const sp_program *P)
 sp_status ensure_scratch(sp_program *P, size_t shots);
 sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
                        uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
+// shots shot0 .. shot0+nshots-1 through the program's current path, in chunks
+sp_status sample_range(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                       uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
 int64_t default_chunk(const sp_program *P);
 // dense paths (sp_dense.cu)
 sp_status ensure_dense(sp_program *P, size_t shots, cudaStream_t s);
@@ -206,6 +220,8 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
 sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *seeds, const uint64_t *nshots,
                        uint64_t *const *d_meas, uint64_t *const *d_det, uint64_t *const *d_obs, cudaStream_t s);
 void batch_forget(const sp_program *P);
+size_t batch_plan_count();
+constexpr size_t BATCH_MAX_PLANS = 8;
 sp_status fused_select(sp_program *P, int tw, int unroll);
 sp_status autotune(sp_program *P, cudaStream_t s);
 sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *B,
@@ -217,6 +233,7 @@ sp_status sample_chunk_into(const sp_program *P, uint32_t *B, uint32_t *recT, in
 // expectation (sp_expect.cu)
 sp_status expect_fwd(sp_program *P, const float *d_p, float *d_logE, cudaStream_t s);
 sp_status expect_bwd(sp_program *P, const float *d_p, const float *d_g, float *d_grad, cudaStream_t s);
+sp_status expect_sign(sp_program *P, const float *d_p, float *d_sign, cudaStream_t s);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

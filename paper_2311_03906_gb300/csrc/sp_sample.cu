@@ -143,22 +143,22 @@ int64_t default_chunk(const sp_program *P)
 sp_status ensure_scratch(sp_program *P, size_t shots)
 {
     if (P->scratch_shots >= shots && P->d_B && P->d_recT) return SP_OK;
-    cudaFree(P->d_B);
-    cudaFree(P->d_recT);
+    dev_free(P->d_B);
+    dev_free(P->d_recT);
     P->d_B = nullptr;
     P->d_recT = nullptr;
     P->scratch_shots = 0;
     const size_t words = (shots + 31) / 32;
     const size_t bsz = (size_t)std::max<int64_t>(P->n_sym, 1) * words * 4;
     const size_t rsz = (size_t)std::max<int64_t>(P->n_rows, 1) * words * 4;
-    if (cudaMalloc((void **)&P->d_B, bsz) != cudaSuccess) {
+    if (dev_alloc((void **)&P->d_B, bsz) != cudaSuccess) {
         cudaGetLastError();
         P->d_B = nullptr;
         return set_error(SP_ERR_OOM, "cudaMalloc of the fault-bit scratch failed");
     }
-    if (cudaMalloc((void **)&P->d_recT, rsz) != cudaSuccess) {
+    if (dev_alloc((void **)&P->d_recT, rsz) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(P->d_B);
+        dev_free(P->d_B);
         P->d_B = nullptr;
         P->d_recT = nullptr;
         return set_error(SP_ERR_OOM, "cudaMalloc of the record scratch failed");

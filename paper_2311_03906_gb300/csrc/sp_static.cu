@@ -26,14 +26,13 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 uint32_t *g_scratch_ptr[MAX_DEVICES] = {};
 
-// Device address of the array on the current device.  The host-side symbol
-// g_static_scratch is only a stand-in for it and must never be passed to a
-// kernel, so the address is looked up once per device, with that device
-// current, and cached.
-sp_status scratch_for_current_device(uint32_t **out)
+// Device address of the array on device dev, which must be current.  The
+// host-side symbol g_static_scratch is only a stand-in for it and must never
+// be passed to a kernel, so the address is looked up once per device, with
+// that device current, and cached for the life of the process (the cache
+// assumes the device's primary context is not reset meanwhile).
+sp_status scratch_for_device(int dev, uint32_t **out)
 {
-    int dev = -1;
-    SP_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= MAX_DEVICES) return set_error(SP_ERR_INVALID_ARG, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
@@ -73,8 +72,14 @@ extern "C" sp_status sp_sample_static(sp_program *P, uint64_t seed, uint64_t sho
                          "program needs " + std::to_string(rows * 4) + " bytes per 32 shots; the static scratch holds " +
                              std::to_string(STATIC_SCRATCH_BYTES) + " bytes");
     if (nshots == 0) return SP_OK;
+    // the program's tables and the scratch must live on the same GPU
+    int dev = -1;
+    SP_CUDA(cudaGetDevice(&dev));
+    if (dev != P->device)
+        return set_error(SP_ERR_INVALID_ARG, "the program lives on device " + std::to_string(P->device) +
+                                                 " but device " + std::to_string(dev) + " is current");
     uint32_t *base = nullptr;
-    sp_status st = scratch_for_current_device(&base);
+    sp_status st = scratch_for_device(dev, &base);
     if (st != SP_OK) return st;
     uint32_t *B = base;
     uint32_t *recT = base + (size_t)std::max<int64_t>(P->n_sym, 0) * pitch;

@@ -90,3 +90,31 @@ def test_null_arguments(lib):
     assert lib.sp_device_status(None, C.byref(st)) == 1
     lib.sp_free(None)
     assert b"NULL" in lib.sp_last_error()
+
+
+def test_failed_program_allocation_is_reported_without_a_leak(lib):
+    """The allocation-failure hook on the host: sp_build's first allocation
+    (the program object) fails before any CUDA call, so this runs without a
+    GPU; the call returns SP_ERR_OOM and holds nothing afterwards."""
+    from paper_2311_03906_gb300 import binding
+    desc, keep = _desc(binding, 2, [(0, [0], 0.0), (6, [0, 1], 0.0)])
+    dev0, host0 = C.c_int64(0), C.c_int64(0)
+    assert lib.sp_debug_live_allocs(C.byref(dev0), C.byref(host0)) == 0
+    assert lib.sp_debug_fail_alloc(0) == 0
+    h = C.c_void_p()
+    st = lib.sp_build(C.byref(desc), None, C.byref(h))
+    assert st == 4 and not h.value
+    assert b"allocation" in lib.sp_last_error()
+    dev1, host1 = C.c_int64(0), C.c_int64(0)
+    lib.sp_debug_live_allocs(C.byref(dev1), C.byref(host1))
+    assert (dev1.value, host1.value) == (dev0.value, host0.value)
+    # the hook fired once and disarmed itself: the next failure is the
+    # missing GPU, not an injected one
+    st = lib.sp_build(C.byref(desc), None, C.byref(h))
+    assert st != 4
+
+
+def test_batch_plan_cache_is_empty_and_bounded(lib):
+    n, cap = C.c_uint32(7), C.c_uint32(0)
+    assert lib.sp_batch_plans(C.byref(n), C.byref(cap)) == 0
+    assert n.value == 0 and cap.value == 8

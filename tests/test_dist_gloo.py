@@ -60,3 +60,48 @@ def test_shard_range_rejects_bad_rank():
     with pytest.raises(ValueError):
         shard_range(2, 2, 10, 0, 1)
     assert max_over_ranks(3.0) == 3.0
+
+
+def _sample_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from workloads import surface_code
+        ref = oracle.Program(surface_code(3, 3, 0.01))
+        steps, per = 3, 500
+        mine = []
+        for k in range(steps):
+            a, b = shard_range(rank, world, per, k, steps)
+            mine.append((a, ref.sample(5, a, b - a)))
+        gathered = [None] * world
+        dist.all_gather_object(gathered, mine)
+        if rank == 0:
+            q.put(gathered)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_records_concatenate_to_one_rank_run():
+    """Each gloo rank samples its own shot ranges (the oracle stands in for
+    a GPU); ordered by shot index, the ranks' records are exactly those of
+    one rank sampling every shot: the sharded path needs no exchange."""
+    import numpy as np
+    import oracle
+    from workloads import surface_code
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_sample_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    gathered = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    pieces = sorted((a, recs) for per_rank in gathered for a, recs in per_rank)
+    total = pieces[-1][0] + len(pieces[-1][1][0])
+    whole = oracle.Program(surface_code(3, 3, 0.01)).sample(5, 0, total)
+    for k in range(3):
+        np.testing.assert_array_equal(np.concatenate([recs[k] for _, recs in pieces]), whole[k])

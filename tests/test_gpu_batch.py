@@ -1,7 +1,9 @@
 """Batched sampling (sp_sample_batch): many circuits of uneven size, shot
-count and noise rate in one graph-captured enqueue of persistent kernels.
-Records must be bit-identical to one sp_sample call per circuit (and to the
-oracle on sampled shots), also when the captured graph is replayed."""
+count and noise rate in one graph-captured enqueue of persistent kernels,
+one per autotuned launch shape. Records must be bit-identical to one
+sp_sample call per circuit (and to the oracle on sampled shots), also when
+the captured graph is replayed with new seeds and new output buffers, and
+after a member's configuration or scratch changed between two calls."""
 import numpy as np
 import pytest
 
@@ -92,3 +94,86 @@ def test_config4_suite_builds_and_samples_a_slice():
         torch.cuda.synchronize()
         for a, b in zip(o, want):
             assert torch.equal(a, b)
+
+
+def _check_members(progs, seeds, shots, outs):
+    for p, s, n, o in zip(progs, seeds, shots, outs):
+        want = p.sample(n, seed=s)
+        torch.cuda.synchronize()
+        for a, b in zip(o, want):
+            assert torch.equal(a, b), "batch differs from sp_sample"
+
+
+def test_plan_is_reused_for_new_seeds_and_outputs():
+    """Seeds and output pointers are per-call data: 100 seed sets on new
+    buffers replay one plan, and the cache stays within its bound when the
+    shot counts change."""
+    specs = _suite()[:4]
+    progs = [sp.build(c) for c, _, _ in specs]
+    shots = [n for _, _, n in specs]
+    before, cap = sp.batch_plans()
+    for k in range(100):
+        seeds = [1000 * k + i for i in range(len(progs))]
+        outs = sp.sample_batch(progs, seeds, shots)
+        if k in (0, 57, 99):
+            torch.cuda.synchronize()
+            _check_members(progs, seeds, shots, outs)
+    assert sp.batch_plans()[0] <= before + 1
+    for k in range(3 * cap):
+        sp.sample_batch(progs, [7] * len(progs), [n + 32 * k for n in shots])
+    assert sp.batch_plans()[0] <= cap
+    outs = sp.sample_batch(progs, [3, 4, 5, 6], shots)
+    torch.cuda.synchronize()
+    _check_members(progs, [3, 4, 5, 6], shots, outs)
+
+
+def test_batch_after_member_scratch_and_config_change():
+    """batch -> set_chunk and a larger sp_sample on a staged member (its
+    scratch is reallocated) -> the same batch with new seeds: the records
+    still equal separate calls and the oracle. Then a fused member is moved
+    to other tile shapes and the staged one back to the fused path."""
+    specs = _suite()[:5]
+    progs = [sp.build(c) for c, _, _ in specs]
+    progs[1].set_path(sp.PATH_SPARSE)
+    shots = [n for _, _, n in specs]
+    outs = sp.sample_batch(progs, [1, 2, 3, 4, 5], shots)
+    torch.cuda.synchronize()
+    _check_members(progs, [1, 2, 3, 4, 5], shots, outs)
+    progs[1].set_chunk(65536)
+    progs[1].sample(50_000, seed=9)       # the staged scratch is reallocated, larger
+    progs[1].set_chunk(0)
+    seeds = [11, 12, 13, 14, 15]
+    outs = sp.sample_batch(progs, seeds, shots)
+    torch.cuda.synchronize()
+    _check_members(progs, seeds, shots, outs)
+    for (c, _, n), s, (m, d, o) in zip(specs, seeds, outs):
+        ref = oracle.Program(c)
+        pick = np.unique(np.array([0, 1, n // 3, n - 1]))
+        rm, rd, ro = ref.sample_shots(s, pick)
+        idx = torch.as_tensor(pick, device="cuda")
+        np.testing.assert_array_equal(_u64(m[idx]), rm)
+        np.testing.assert_array_equal(_u64(d[idx]), rd)
+        np.testing.assert_array_equal(_u64(o[idx]), ro)
+    progs[1].set_path(sp.PATH_AUTO)
+    progs[2].set_fused_config(128, 1)
+    progs[3].set_fused_config(32, 1)
+    progs[4].set_fused_config(64, 3)
+    outs = sp.sample_batch(progs, seeds, shots)
+    torch.cuda.synchronize()
+    _check_members(progs, seeds, shots, outs)
+
+
+def test_every_launch_shape_in_one_batch():
+    """Members with every fused launch shape (32-, 64- and 128-shot tiles,
+    each variant) in one call: one persistent launch per shape."""
+    shapes = [(32, 1), (32, 2), (64, 1), (64, 2), (64, 3), (128, 1), (128, 2)]
+    progs, seeds, shots = [], [], []
+    for k, (tile, var) in enumerate(shapes):
+        p = sp.build(surface_code(3 + 2 * (k % 3), 3, 2e-3))
+        p.set_fused_config(tile, var)
+        progs.append(p)
+        seeds.append(40 + k)
+        shots.append(1000 + 333 * k)
+    outs = sp.sample_batch(progs, seeds, shots)
+    torch.cuda.synchronize()
+    _check_members(progs, seeds, shots, outs)

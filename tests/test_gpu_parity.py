@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from workloads import (Circuit, random_clifford_circuit, random_feedforward_circuit, random_layered,
-                       random_small_circuit, repetition_code, surface_code)
+                       random_small_circuit, repetition_code, surface_code, surface_code_all_channels)
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +41,8 @@ CIRCUITS = {
     "rep5": lambda: repetition_code(5, 5, 0.01),
     "surf3": lambda: surface_code(3, 3, 1e-2),
     "surf5": lambda: surface_code(5, 5, 2e-3),
+    # X/Y/Z_ERROR, DEPOLARIZE1 and DEPOLARIZE2 channels all reach the detectors
+    "allkinds": lambda: surface_code_all_channels(3, 3, 1e-3),
     "layered40": lambda: random_layered(40, 40, depolarize=0.01, seed=3),
     "wide1000": lambda: random_layered(1000, 3, cnot_pairs=500, depolarize=0.001, seed=4),
     # depolarizing events in most (block, shot) pairs: the warps' event queues fill and drain
@@ -196,6 +198,41 @@ def test_full_size_d11_sampled_shots(d11):
     assert not np.any(last & pad_mask)
 
 
+def test_config1_every_shot():
+    """Repetition-code memory d=5, 5 rounds, X_ERROR(0.01): all 1e4 shots at
+    seed 1 against the oracle, record for record."""
+    c = repetition_code(5, 5, 0.01)
+    prog, ref = sp.build(c), oracle.Program(c)
+    m, d, o = prog.sample(10_000, seed=1, shot0=0)
+    torch.cuda.synchronize()
+    rm, rd, ro = ref.sample_parallel(1, 0, 10_000)
+    np.testing.assert_array_equal(_u64(m), rm)
+    np.testing.assert_array_equal(_u64(d), rd)
+    np.testing.assert_array_equal(_u64(o), ro)
+
+
+@pytest.mark.parametrize("path", ["fused", "staged"])
+def test_full_size_d11_contiguous_range(d11, path):
+    """One call of 1,100,000 shots of the d=11 configuration; 16,384
+    consecutive shots from 1,040,000 on are recomputed by the oracle (on all
+    host cores). The range spans the staged path's 1,048,576-shot chunk
+    boundary and, on the fused path, the boundary of kernel waves of
+    num_SMs x CTAs/SM tiles at 1,050,624 (54 waves of 304 x 64 shots)."""
+    c, prog, ref = d11
+    prog.set_path(sp.PATH_FUSED if path == "fused" else sp.PATH_SPARSE)
+    try:
+        assert prog.info["chunk_shots"] == 1 << 20
+        m, d, o = prog.sample(1_100_000, seed=6, shot0=0)
+        torch.cuda.synchronize()
+        a, n = 1_040_000, 16_384
+        rm, rd, ro = ref.sample_parallel(6, a, n)
+        np.testing.assert_array_equal(_u64(m[a:a + n]), rm)
+        np.testing.assert_array_equal(_u64(d[a:a + n]), rd)
+        np.testing.assert_array_equal(_u64(o[a:a + n]), ro)
+    finally:
+        prog.set_path(sp.PATH_AUTO)
+
+
 @pytest.mark.parametrize("path", ["fused", "staged"])
 def test_full_size_d11_both_paths_agree(d11, path):
     c, prog, ref = d11
@@ -344,17 +381,78 @@ def test_full_size_d11_detector_rates(d11):
     assert z.max() < 5.0, z.max()
 
 
-@pytest.mark.parametrize("name", ["rep5", "surf3", "surf5", "rand5"])
-def test_expectation_matches_oracle(name):
+def _draw_p(rng, n, regime):
+    """Per-channel probabilities: circuit-level noise, or large rates where
+    factors 1 - 2 kappa p turn negative (X_ERROR above 1/2, DEPOLARIZE1 above
+    3/4, DEPOLARIZE2 at 1) or vanish (X/Y/Z_ERROR at exactly 1/2)."""
+    if regime == "small":
+        return rng.uniform(5e-4, 2e-3, n).astype(np.float32)
+    p = rng.uniform(5e-4, 2e-3, n)
+    big = rng.random(n) < 0.05
+    p[big] = rng.choice([0.3, 0.5, 0.6, 0.8, 1.0], big.sum())
+    return p.astype(np.float32)
+
+
+def _check_expect(prog, ref, p):
+    pt = torch.as_tensor(p, device="cuda")
+    got = prog.expect_raw(pt).cpu().numpy().astype(np.float64)
+    sgn = prog.expect_sign_raw(pt).cpu().numpy()
+    la, sa = ref.expect(p.astype(np.float64))
+    zero = np.isneginf(la)
+    np.testing.assert_array_equal(np.isneginf(got), zero)
+    np.testing.assert_allclose(got[~zero], la[~zero], rtol=1e-4, atol=1e-6)
+    np.testing.assert_array_equal(sgn[zero], 0.0)
+    np.testing.assert_array_equal(sgn[~zero], sa[~zero].astype(np.float32))
+    return zero
+
+
+@pytest.mark.parametrize("regime", ["small", "large"])
+@pytest.mark.parametrize("name", ["rep5", "surf3", "surf5", "allkinds"])
+def test_expectation_matches_oracle(name, regime):
+    """log|E| and sign E of every detector and observable against the FP64
+    oracle, over channel probabilities up to 1 (negative and zero factors)."""
     c = CIRCUITS[name]()
     prog, ref = sp.build(c), oracle.Program(c)
-    if prog.num_detectors + prog.num_observables == 0:
-        pytest.skip("no detectors")
+    assert prog.num_detectors > 0
     rng = np.random.default_rng(1)
-    p = rng.uniform(5e-4, 2e-3, prog.num_channels).astype(np.float32)
-    got = prog.expect_raw(torch.as_tensor(p, device="cuda")).cpu().numpy().astype(np.float64)
-    la, _ = ref.expect(p.astype(np.float64))
-    np.testing.assert_allclose(got, la, rtol=1e-4, atol=1e-7)
+    p = _draw_p(rng, prog.num_channels, regime)
+    if regime == "large":
+        # every 37th one-symbol channel at exactly 1/2: its factor vanishes
+        _, kind, _ = prog.channels()
+        p[np.flatnonzero(kind == 0)[::37]] = 0.5
+    zero = _check_expect(prog, ref, p)
+    if regime == "large":
+        _, sa = ref.expect(p.astype(np.float64))
+        assert (sa[~zero] < 0).any(), "no negative expectation was exercised"
+        assert zero.any(), "no vanishing expectation was exercised"
+
+
+def _check_grad(prog, ref, p, g):
+    """The adjoint against the FP64 oracle, element by element: relative 1e-4,
+    with an absolute floor of 1e-5 times the element's own scale, the sum of
+    the absolute values of its terms (what FP32 accumulation error is
+    relative to)."""
+    pt = torch.as_tensor(p, device="cuda")
+    grad = prog.expect_grad_raw(pt, torch.as_tensor(g, device="cuda")).cpu().numpy().astype(np.float64)
+    want = ref.expect_vjp(p.astype(np.float64), g.astype(np.float64))
+    scale = np.abs(ref.expect_vjp(p.astype(np.float64), np.abs(g).astype(np.float64)))
+    err = np.abs(grad - want)
+    bad = err > 1e-4 * np.abs(want) + 1e-5 * scale
+    assert not bad.any(), (np.flatnonzero(bad)[:5], grad[bad][:5], want[bad][:5])
+    return grad, want
+
+
+@pytest.mark.parametrize("regime", ["small", "large"])
+def test_gradient_all_channel_kinds(regime):
+    c = CIRCUITS["allkinds"]()
+    prog, ref = sp.build(c), oracle.Program(c)
+    rng = np.random.default_rng(3)
+    p = _draw_p(rng, prog.num_channels, regime)
+    # keep the gradient finite: no factor exactly zero
+    _, kind, _ = prog.channels()
+    p[(kind == 0) & (p == 0.5)] = 0.6
+    g = rng.normal(size=prog.num_detectors + prog.num_observables).astype(np.float32)
+    _check_grad(prog, ref, p, g)
 
 
 def test_expectation_d11_and_gradient(d11):
@@ -366,10 +464,8 @@ def test_expectation_d11_and_gradient(d11):
     la, _ = ref.expect(p.astype(np.float64))
     np.testing.assert_allclose(got, la, rtol=1e-4)
     g = rng.normal(size=prog.num_detectors + prog.num_observables).astype(np.float32)
-    grad = prog.expect_grad_raw(pt, torch.as_tensor(g, device="cuda")).cpu().numpy().astype(np.float64)
-    want = ref.expect_vjp(p.astype(np.float64), g.astype(np.float64))
+    grad, want = _check_grad(prog, ref, p, g)
     scale = np.abs(want).max()
-    np.testing.assert_allclose(grad, want, rtol=1e-4, atol=1e-4 * scale)
     # central differences of the FP64 oracle on 64 channels
     h = 1e-6
     p64 = p.astype(np.float64)

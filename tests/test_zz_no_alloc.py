@@ -46,3 +46,23 @@ def test_static_scratch_rejects_misaligned_output():
     st = lib.sp_sample_static(prog.handle, 1, 0, 10, C.c_void_p(buf.data_ptr() + 1), None, None, None)
     assert st == 1
     assert b"aligned" in lib.sp_last_error()
+
+
+def test_static_scratch_rejects_a_program_of_another_device():
+    """The scratch and the program's tables must be on one GPU: a program
+    whose device field names another ordinal is refused before any launch
+    (the field is forged here, since one GPU is all this test has)."""
+    import ctypes as C
+    prog = sp.build(repetition_code(3, 2, 0.1))
+    lib = sp.load()
+    dev = C.cast(prog.handle, C.POINTER(C.c_int))   # sp_program's first field: its device
+    saved = dev[0]
+    out = prog.alloc_outputs(10)
+    try:
+        dev[0] = saved + 7
+        st = lib.sp_sample_static(prog.handle, 1, 0, 10, C.c_void_p(out[0].data_ptr()), None, None, None)
+    finally:
+        dev[0] = saved
+    assert st == 1
+    assert b"device" in lib.sp_last_error()
+    prog.close()

@@ -326,6 +326,27 @@ def surface_code(distance: int = 11, rounds: Optional[int] = None, p: float = 1e
     return c
 
 
+def surface_code_all_channels(distance: int = 3, rounds: Optional[int] = None, p: float = 1e-3) -> Circuit:
+    """``surface_code`` with every channel kind reaching the detectors: at the
+    start of each round, after the X-ancillas' H and DEPOLARIZE1, a Y_ERROR(p)
+    on every data qubit and a Z_ERROR(p) on every X-ancilla (in |+>, where a
+    Z flips its outcome), next to the DEPOLARIZE1, DEPOLARIZE2 and X_ERROR
+    channels of the base circuit."""
+    base = surface_code(distance, rounds, p)
+    nd = distance * distance
+    out = Circuit(base.num_qubits)
+    after_tick = False
+    for op in base.ops:
+        out.append(op.name, op.targets, op.arg)
+        if op.name == "TICK":
+            after_tick = True
+        elif op.name == "DEPOLARIZE1" and after_tick:
+            out.append("Y_ERROR", list(range(nd)), p)
+            out.append("Z_ERROR", list(op.targets), p)
+            after_tick = False
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Random layered circuits (the paper's Fig. 3 benchmark family)
 # ---------------------------------------------------------------------------
