@@ -64,6 +64,8 @@ def _load():
         lib.or_eval.argtypes = [P, ptr, ptr, ptr, ptr]
         lib.or_sample.argtypes = [P, U64, U64, I64, ptr, ptr, ptr]
         lib.or_sample_shots.argtypes = [P, U64, ptr, I64, ptr, ptr, ptr]
+        lib.or_draw_grouped.argtypes = [P, U64, U64, ptr]
+        lib.or_sample_grouped.argtypes = [P, U64, U64, I64, ptr, ptr, ptr]
         lib.or_expect.argtypes = [P, ptr, ptr, ptr]
         lib.or_expect_vjp.argtypes = [P, ptr, ptr, ptr]
         lib.or_philox.argtypes = [ptr, ptr, ptr]
@@ -193,6 +195,26 @@ class Program:
     def draw_bits(self, seed: int, shot: int) -> np.ndarray:
         b = self.draw(seed, shot)
         return np.unpackbits(b.view(np.uint8), bitorder="little")[: self.num_symbols + 1]
+
+    def draw_grouped(self, seed: int, shot: int) -> np.ndarray:
+        """b of one shot under the grouped draw (stream 2), packed."""
+        b = np.zeros(self.pw, np.uint64)
+        self._lib.or_draw_grouped(self._h, seed, shot, _p(b))
+        return b
+
+    def draw_grouped_bits(self, seed: int, shot: int) -> np.ndarray:
+        b = self.draw_grouped(seed, shot)
+        return np.unpackbits(b.view(np.uint8), bitorder="little")[: self.num_symbols + 1]
+
+    def sample_grouped(self, seed: int, shot0: int, nshots: int):
+        """Records of shots shot0.. under the grouped draw (stream 2)."""
+        wm, wd, wo = self._words()
+        m = np.zeros((nshots, max(wm, 1)), np.uint64)
+        d = np.zeros((nshots, max(wd, 1)), np.uint64)
+        o = np.zeros((nshots, max(wo, 1)), np.uint64)
+        if nshots:
+            self._lib.or_sample_grouped(self._h, seed, shot0, nshots, _p(m), _p(d), _p(o))
+        return m[:, :wm], d[:, :wd], o[:, :wo]
 
     def evaluate(self, b_bits: np.ndarray):
         """Records for an explicit symbol assignment (b_bits[0] must be 1)."""

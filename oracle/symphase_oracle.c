@@ -532,6 +532,115 @@ void or_sample(const orc_prog *P, uint64_t seed, uint64_t shot0, int64_t nshots,
     free(b);
 }
 
+/* ------------------------------------------------ grouped draw (stream 2) */
+/* An opt-in second definition of "sample b from P_C" (Algorithm 1), exact
+ * for the same Sec. 3.1 distributions but drawing far fewer words when the
+ * channels rarely fire.  Counter word 3 tells the streams apart (the first
+ * stream uses 0):
+ *   - random-measurement channel of rank r (in channel order): bit r%32 of
+ *     word (r/32)%4 of Philox(counter (shot lo, shot hi, r/128, 3));
+ *   - the other channels, in channel order, form groups of 32; group g
+ *     fires with probability 1 - prod_i (1 - p_i): word g%4 of Philox(
+ *     counter (shot lo, shot hi, g/4, 1)) below G_g = floor((1 - prod) 2^32);
+ *   - in a group that fired, channel i (word i%4 of Philox(counter (shot lo,
+ *     shot hi, 8g + i/4, 2))) is the first to fire with probability
+ *     q_i = p_i / (1 - R_i), R_i = prod_{j >= i} (1 - p_j), while no earlier
+ *     one has (threshold Q_i = floor(q_i 2^32)); the last channel with
+ *     p > 0 fires if none before it did; after the first, each channel
+ *     fires independently with its own threshold T_i = floor(p_i 2^32);
+ *   - a depolarizing channel that fired takes k = min(floor(u m / U), m-1)
+ *     with U the threshold that decided it (Q_i or T_i), m = 3 / 15.
+ * Conditioning on "the group fired" and walking to the first fired channel
+ * reproduces independent Bernoulli(p_i) channels: P(first = i | fired) =
+ * prod_{j<i}(1 - p_j) p_i / (1 - R_0). */
+#define OR_GROUP 32
+
+static uint32_t stream_word(uint64_t seed, uint64_t shot, uint32_t ctr2, uint32_t tag, int w)
+{
+    uint32_t ctr[4] = {(uint32_t)shot, (uint32_t)(shot >> 32), ctr2, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    or_philox(ctr, key, out);
+    return out[w];
+}
+
+static uint32_t outcome_after(int32_t type, uint32_t u, uint32_t U)
+{
+    if (type != CH_DEP1 && type != CH_DEP2) return 1u;
+    uint64_t m = type == CH_DEP1 ? 3u : 15u;
+    uint64_t k = ((uint64_t)u * m) / U;
+    if (k > m - 1) k = m - 1;
+    return (uint32_t)k + 1u;
+}
+
+static void apply_outcome(const orc_prog *P, int64_t c, uint32_t v, uint64_t *b)
+{
+    for (int32_t i = 0; i < P->ch_nsym[c]; i++)
+        if ((v >> i) & 1u) flipb(b, P->ch_sym0[c] + i);
+}
+
+void or_draw_grouped(const orc_prog *P, uint64_t seed, uint64_t shot, uint64_t *b)
+{
+    memset(b, 0, (size_t)P->pw * 8);
+    b[0] = 1u;
+    int64_t *fault = (int64_t *)malloc((size_t)(P->nch > 0 ? P->nch : 1) * sizeof(int64_t));
+    if (!fault) return;
+    int64_t nf = 0, r = 0;
+    for (int64_t c = 0; c < P->nch; c++) {
+        if (P->ch_type[c] == CH_RANDOM) {
+            uint32_t w = stream_word(seed, shot, (uint32_t)(r / 128), 3u, (int)((r / 32) % 4));
+            if ((w >> (r % 32)) & 1u) apply_outcome(P, c, 1u, b);
+            r++;
+        } else {
+            fault[nf++] = c;
+        }
+    }
+    for (int64_t g = 0; g * OR_GROUP < nf; g++) {
+        int64_t n = nf - g * OR_GROUP < OR_GROUP ? nf - g * OR_GROUP : OR_GROUP;
+        const int64_t *ch = fault + g * OR_GROUP;
+        /* R[i] = prod_{j >= i} (1 - p_j), R[n] = 1 */
+        double R[OR_GROUP + 1];
+        R[n] = 1.0;
+        for (int64_t i = n - 1; i >= 0; i--) R[i] = R[i + 1] * (1.0 - P->ch_p[ch[i]]);
+        uint32_t G = or_threshold(1.0 - R[0]);
+        uint32_t ug = stream_word(seed, shot, (uint32_t)(g / 4), 1u, (int)(g % 4));
+        if (ug >= G) continue;
+        int64_t last = -1;
+        for (int64_t i = 0; i < n; i++)
+            if (P->ch_p[ch[i]] > 0.0) last = i;
+        int searching = 1;
+        for (int64_t i = 0; i < n; i++) {
+            int64_t c = ch[i];
+            uint32_t u = stream_word(seed, shot, (uint32_t)(8 * g + i / 4), 2u, (int)(i % 4));
+            uint32_t U;
+            int fired;
+            if (searching) {
+                U = i == last ? 4294967295u : or_threshold(P->ch_p[c] / (1.0 - R[i]));
+                fired = i == last || u < U;
+                if (fired) searching = 0;
+            } else {
+                U = P->ch_T[c];
+                fired = u < U;
+            }
+            if (fired) apply_outcome(P, c, outcome_after(P->ch_type[c], u, U), b);
+        }
+    }
+    free(fault);
+}
+
+void or_sample_grouped(const orc_prog *P, uint64_t seed, uint64_t shot0, int64_t nshots,
+                       uint64_t *meas, uint64_t *det, uint64_t *obs)
+{
+    int64_t wm = (P->nmeas + 63) / 64, wd = (P->ndet + 63) / 64, wo = (P->nobs + 63) / 64;
+    uint64_t *b = (uint64_t *)malloc((size_t)P->pw * 8);
+    if (!b) return;
+    for (int64_t t = 0; t < nshots; t++) {
+        or_draw_grouped(P, seed, shot0 + (uint64_t)t, b);
+        or_eval(P, b, meas + t * wm, det + t * wd, obs + t * wo);
+    }
+    free(b);
+}
+
 /* ---------------------------------------------------------- expectation */
 static int channel_outcomes(int32_t type) { return type == CH_DEP1 ? 3 : (type == CH_DEP2 ? 15 : 1); }
 

@@ -66,7 +66,7 @@ static void release(sp_program *P)
     if (cur != P->device) cudaSetDevice(P->device);
     void *bufs[] = {P->d_A, P->d_chT, P->d_chKind, P->d_chP, P->d_chSym0, P->d_rowOff, P->d_idx,
                     P->d_parent, P->d_cflag, P->d_A64, P->d_const, P->d_inc, P->d_incT, P->d_kappa,
-                    P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta,
+                    P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta, P->d_blkFilt,
                     P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs,
                     P->d_colOff, P->d_colRows, P->d_AT, P->d_tc_coef[0], P->d_tc_coef[1], P->d_tc_coef[2],
                     P->d_tc_status};

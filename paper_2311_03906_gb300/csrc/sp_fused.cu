@@ -3,16 +3,16 @@
 // Algorithm 1 "Sampling" (arXiv 2311.03906, Sec. 3.2.3, Eq. sampling) for a
 // tile of 32*TW shots per CTA iteration, entirely in shared memory:
 //   phase 1  draw: Philox4x32-10 keyed by (seed, shot, channel/4); each warp
-//            owns a contiguous range of 4-channel blocks and the symbols they
-//            feed, lane = shot.  It zeroes those symbols in the tile B_s, then
-//            per block draws, compares with the four thresholds and votes;
-//            only a block where some channel fired in some lane (rare at
-//            circuit-level noise) writes: a warp ballot per fired one-symbol
-//            channel (bit = shot within the tile), and a queued event per
-//            lane whose depolarizing channels fired, resolved later by all
-//            lanes of the warp together;
+//            owns a contiguous range of 4-channel blocks, lane = shot.  Per
+//            block it draws and compares with the four thresholds; per group
+//            of 8 blocks the fired bits of a lane's shots are gathered into
+//            one word per tile word.  Faults are rare at circuit-level noise:
+//            each (block, shot) in which some channel fired is queued as one
+//            event, and the queue is drained by all lanes of the warp
+//            together (a depolarizing channel draws its category again);
+//            each fired symbol XORs its shot bit into the rows holding it;
 //   phase 2  product: (A) every measurement row's own part, c'_j ^ XOR of
-//            B_s over its delta symbols, for all rows in parallel; (B) the
+//            its delta symbols, applied symbol by symbol in phase 1; (B) the
 //            parent chains m_j ^= m_parent; (C) detectors and observables as
 //            XORs of their measurement records, which is their definition;
 //   phase 3  emit: 32x32 warp transposes turn the bit-sliced rows into
@@ -261,16 +261,23 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
 }
 
 // Fired-event queue of one warp: FUSED_QCAP 32-bit words in shared memory.
-// An event is one (channel block, shot) in which at least one of the block's
-// depolarizing channels fired: bits 0..3 the fired channels, bits 4..8 lane,
-// then the tile word t (one bit for TW <= 2, two for TW = 4), then block -
-// the warp's first block in the remaining bits.
+// An event is one (channel block, shot) in which some channel may have
+// fired: bits 0..4 lane, bit 5 "depolarizing channels only" (its one-symbol
+// channels were already applied), then the tile word t (one bit for
+// TW <= 2, two for TW = 4), then block - the warp's first block in the
+// remaining bits.
 constexpr uint32_t FUSED_QCAP = 128;
+constexpr uint32_t EV_DEP_ONLY = 1u << 5;
 __host__ __device__ constexpr int event_tbits(int tw) { return tw == 4 ? 2 : 1; }
-__host__ __device__ constexpr uint32_t event_max_blocks(int tw) { return 1u << (32 - 9 - event_tbits(tw)); }
+__host__ __device__ constexpr uint32_t event_max_blocks(int tw) { return 1u << (32 - 6 - event_tbits(tw)); }
 // Channel blocks whose compare results are gathered before one vote.
 constexpr uint32_t DRAW_GROUP = 8;
 static_assert(4 * DRAW_GROUP == 32, "a group's channels map one to one onto the lanes");
+// A block is "frequent" when its channels' thresholds add up to at least
+// 2^28 (a lane's shot sees one of them fire with probability >= 1/16); its
+// blkFilt entry is then FREQUENT, else the largest of its four thresholds.
+constexpr uint32_t FREQUENT = 0xFFFFFFFFu;
+constexpr uint64_t FREQUENT_SUM = 1ull << 28;
 
 // XOR the word x into tile word t of every measurement row whose own part
 // holds symbol s (Eq. sampling restricted to the symbol's column; shared
@@ -283,9 +290,17 @@ __device__ __forceinline__ void xor_column(const uint32_t *__restrict__ colOff, 
     for (uint32_t k = colOff[s]; k < e; k++) atomicXor(&Rw[colRows[k] * TW + t], x);
 }
 
+// Fired mask of one Philox block: bit i = channel i of the block fired.
+__device__ __forceinline__ uint32_t fired4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, const uint4 T)
+{
+    return (uint32_t)(r0 < T.x) | ((uint32_t)(r1 < T.y) << 1) | ((uint32_t)(r2 < T.z) << 2) |
+           ((uint32_t)(r3 < T.w) << 3);
+}
+
 // Apply the queued events e = lane, lane+32, ... < n: recompute the event's
-// Philox block, turn each fired channel into its symbol bits and hand each
-// (symbol, tile word, shot bit) to apply.
+// Philox block, compare its four words with the thresholds, turn each fired
+// channel into its symbol bits and hand each (symbol, tile word, shot bit)
+// to apply.
 template <int TW, typename Apply>
 __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const uint4 *__restrict__ blkT,
                                             const uint32_t *__restrict__ blkMeta, const uint32_t *__restrict__ blkSym0,
@@ -296,16 +311,21 @@ __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const
     constexpr int TB = event_tbits(TW);
     for (uint32_t e = lane; e < n; e += 32) {
         const uint32_t ev = q[e];
-        const uint32_t b = b0 + (ev >> (9 + TB));
-        const int t = (ev >> 9) & ((1u << TB) - 1u);
-        const uint32_t ln = (ev >> 4) & 31u;
-        uint32_t fmask = ev & 15u;
+        const uint32_t b = b0 + (ev >> (6 + TB));
+        const int t = (ev >> 6) & ((1u << TB) - 1u);
+        const uint32_t ln = ev & 31u;
         const ShotConst s = shot_const(shot_base + 32u * (uint32_t)t + ln, k1);
         const uint64_t ub = (uint64_t)PH_M1 * b;
         uint32_t r0, r1, r2, r3;
         philox_block(s, s.c1, (uint32_t)(ub >> 32), (uint32_t)ub, K, r0, r1, r2, r3);
         const uint4 T = blkT[b];
         const uint32_t meta = blkMeta[b], s0 = blkSym0[b];
+        uint32_t fmask = fired4(r0, r1, r2, r3, T);
+        if (ev & EV_DEP_ONLY) {
+            const uint32_t dep = (((meta >> 0) & 3u) ? 1u : 0u) | (((meta >> 2) & 3u) ? 2u : 0u) |
+                                 (((meta >> 4) & 3u) ? 4u : 0u) | (((meta >> 6) & 3u) ? 8u : 0u);
+            fmask &= dep;
+        }
         while (fmask) {
             const int i = __ffs(fmask) - 1;
             fmask &= fmask - 1;
@@ -324,81 +344,69 @@ __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const
     __syncwarp();
 }
 
-// Fired mask of one Philox block: bit i = channel i of the block fired.
-__device__ __forceinline__ uint32_t fired4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, const uint4 T)
-{
-    return (uint32_t)(r0 < T.x) | ((uint32_t)(r1 < T.y) << 1) | ((uint32_t)(r2 < T.z) << 2) |
-           ((uint32_t)(r3 < T.w) << 3);
-}
-
 // Phase 1 with the product folded in, for blocks [b0, b1) and 32*TW shots:
 // every fired symbol XORs its bit-sliced word (bit = shot in the tile) into
-// the rows Rw (TW 32-bit words per row) whose own part holds it.  Per group
-// of DRAW_GROUP blocks (32 channels) each lane gathers the fired bits of its
-// shots' channels into one word per tile word, and the warp votes once;
-// faults are rare at circuit-level noise, so most of the time goes to
-// Philox.  A group that fired is resolved lane-parallel: lane j stands for
-// channel j&3 of block g + j/4 (descriptor jmeta, first symbol js0, loaded
-// at the group's start), a 32x32 transpose per tile word gives it the shots
-// in which its channel fired, and a one-symbol channel (a Pauli error or a
-// random outcome) applies that word to its symbol's rows.  Depolarizing
-// channels need the category index: one event per (block, shot) goes to the
-// warp's queue q, drained by all 32 lanes when it fills and at the end.
+// the rows Rw (TW 32-bit words per row) whose own part holds it.  Blocks go
+// in groups of DRAW_GROUP (32 channels), with one of two treatments chosen
+// per group by a warp vote on the blocks' blkFilt entries:
+//  - rare groups (every block's thresholds add up to less than 2^28; at
+//    circuit-level noise all of them): per block and shot only the least of
+//    the four Philox words is compared, with the block's largest threshold,
+//    which no fired channel can miss; each (block, shot) that passes is
+//    queued as an event, and the drain recomputes its Philox block and
+//    compares channel by channel, so the records are exact;
+//  - frequent groups (some block holds a channel that fires often, such as a
+//    random outcome at T = 2^31): every channel is compared; a one-symbol
+//    channel's fired shots come out of a 32x32 transpose (lane j = channel j
+//    of the group) as one column word per tile word, and a depolarizing
+//    channel is queued as an event that applies only its depolarizing
+//    channels.
+// The queue is drained by all 32 lanes together when it fills and at the end.
 // UHI: every shot of the tile has the same high counter word c1u, so round
 // 2's M0 product is the same in all lanes and tile words.
 template <int TW, bool UHI, typename Apply>
 __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
-                                                const uint32_t *__restrict__ blkSym0, uint32_t b0, uint32_t b1,
-                                                const Shots<TW> sc, uint64_t shot_base, uint32_t k0, uint32_t k1,
+                                                const uint32_t *__restrict__ blkSym0,
+                                                const uint32_t *__restrict__ blkFilt, uint32_t b0, uint32_t b1,
+                                                const Shots<TW> sc, uint64_t shot_base, const Keys &K, uint32_t k1,
                                                 int lane, uint32_t *q, const Apply &apply)
 {
     static_assert(TW == 1 || TW == 2 || TW == 4, "one, two or four tile words");
     constexpr int TB = event_tbits(TW);
-    const Keys K = make_keys(k0, k1);
     const uint32_t c1u = (uint32_t)(shot_base >> 32);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t cnt = 0;
-    auto resolve = [&](uint32_t g, const uint32_t (&word)[TW], uint32_t jmeta, uint32_t js0) {
-        uint32_t any = 0;
-#pragma unroll
-        for (int t = 0; t < TW; t++) any |= word[t];
-        const uint32_t wm = __reduce_or_sync(FM, any);
-        const int i = lane & 3;
-        const uint32_t kind = (jmeta >> (2 * i)) & 3u;
-        const bool mine = (wm >> lane) & 1u;
-        const bool is_dep = kind == CK_DEP1 || kind == CK_DEP2;
-        const uint32_t dep = __ballot_sync(FM, mine && is_dep);
-        if (wm & ~dep) {
-            const uint32_t sym = js0 + ((jmeta >> (8 + 4 * i)) & 15u);
-#pragma unroll
-            for (int t = 0; t < TW; t++) {
-                const uint32_t col = transpose32(word[t], lane);
-                if (mine && !is_dep && col) apply(sym, t, col);
+    // queue the events flagged in m (bit k = block g + k), one per set bit
+    auto enqueue = [&](uint32_t g, int t, uint32_t m, uint32_t flags, int stride) {
+        while (__any_sync(FM, m != 0u)) {
+            if (cnt > FUSED_QCAP - 32u) {
+                drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, b0, shot_base, K, k1, lane, apply);
+                cnt = 0;
             }
-        }
-        if (!dep) return;
-#pragma unroll
-        for (int t = 0; t < TW; t++) {
-            uint32_t m = word[t] & dep;
-            while (__any_sync(FM, m != 0u)) {
-                if (cnt > FUSED_QCAP - 32u) {
-                    drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, b0, shot_base, K, k1, lane, apply);
-                    cnt = 0;
-                }
-                const int k = m ? (__ffs(m) - 1) >> 2 : 0;
-                const uint32_t nib = (m >> (4 * k)) & 15u;
-                const uint32_t bal = __ballot_sync(FM, nib != 0u);
-                if (nib)
-                    q[cnt + __popc(bal & lt)] =
-                        ((g + (uint32_t)k - b0) << (9 + TB)) | ((uint32_t)t << 9) | ((uint32_t)lane << 4) | nib;
-                cnt += __popc(bal);
-                m &= ~(15u << (4 * k));
-            }
+            const uint32_t k = m ? (uint32_t)(__ffs(m) - 1) / (uint32_t)stride : 0u;
+            const uint32_t bal = __ballot_sync(FM, m != 0u);
+            if (m)
+                q[cnt + __popc(bal & lt)] = ((g + k - b0) << (6 + TB)) | ((uint32_t)t << 6) | flags | (uint32_t)lane;
+            cnt += __popc(bal);
+            m &= ~(((1u << stride) - 1u) << (stride * k));
         }
     };
-    // block g+kk of a group: bit 4*kk+i of word[t] = channel i fired in
-    // shot t of this lane
-    auto step = [&](uint32_t g, uint32_t kk, uint64_t ub, uint32_t (&word)[TW]) {
+    // rare block g+kk: bit kk of word[t] = the least of the shot's four
+    // words is below tm, the block's largest threshold
+    auto step_rare = [&](uint32_t kk, uint64_t ub, uint32_t tm, uint32_t (&word)[TW]) {
+        const uint32_t uhi = (uint32_t)(ub >> 32), ulo = (uint32_t)ub;
+        uint64_t p = 0;
+        if (UHI) p = (uint64_t)PH_M0 * (uhi ^ c1u ^ K.k0[0]);
+#pragma unroll
+        for (int t = 0; t < TW; t++) {
+            if (!UHI) p = (uint64_t)PH_M0 * (uhi ^ sc.s[t].c1 ^ K.k0[0]);
+            uint32_t r0, r1, r2, r3;
+            philox_from_p(sc.s[t], p, ulo, K, r0, r1, r2, r3);
+            if (min(min(r0, r1), min(r2, r3)) < tm) word[t] |= 1u << kk;
+        }
+    };
+    // frequent block g+kk: bit 4*kk+i of word[t] = channel i fired in shot t
+    auto step_exact = [&](uint32_t g, uint32_t kk, uint64_t ub, uint32_t (&word)[TW]) {
         const uint4 T = blkT[g + kk];
         const uint32_t uhi = (uint32_t)(ub >> 32), ulo = (uint32_t)ub;
         const uint32_t bit = 1u << (4 * kk);
@@ -416,48 +424,84 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
         }
     };
     for (uint32_t g = b0; g < b1; g += DRAW_GROUP) {
-        // descriptor of lane j's channel, used only if the group fired
-        uint32_t jmeta = 0, js0 = 0;
-        if (g + (uint32_t)(lane >> 2) < b1) {
-            jmeta = blkMeta[g + (lane >> 2)];
-            js0 = blkSym0[g + (lane >> 2)];
-        }
+        const uint32_t nb = min(DRAW_GROUP, b1 - g);
+        // lane k < nb holds block g+k's filter threshold
+        const uint32_t filt = (uint32_t)lane < nb ? blkFilt[g + lane] : 0u;
+        const uint64_t ug = (uint64_t)PH_M1 * g;
         uint32_t word[TW];
 #pragma unroll
         for (int t = 0; t < TW; t++) word[t] = 0u;
-        const uint64_t ug = (uint64_t)PH_M1 * g;
-        if (b1 - g >= DRAW_GROUP) {
+        if (!__any_sync(FM, filt == FREQUENT)) {
+            if (nb == DRAW_GROUP) {
 #pragma unroll
-            for (uint32_t kk = 0; kk < DRAW_GROUP; kk++) step(g, kk, ug + (uint64_t)kk * PH_M1, word);
+                for (uint32_t kk = 0; kk < DRAW_GROUP; kk++)
+                    step_rare(kk, ug + (uint64_t)kk * PH_M1, __shfl_sync(FM, filt, kk), word);
+            } else {
+#pragma unroll 1
+                for (uint32_t kk = 0; kk < nb; kk++)
+                    step_rare(kk, ug + (uint64_t)kk * PH_M1, __shfl_sync(FM, filt, kk), word);
+            }
+#pragma unroll
+            for (int t = 0; t < TW; t++) enqueue(g, t, word[t], 0u, 1);
+            continue;
+        }
+        // ---- frequent group: lane j stands for channel j&3 of block g + j/4
+        uint32_t jmeta = 0, js0 = 0;
+        if ((uint32_t)(lane >> 2) < nb) {
+            jmeta = blkMeta[g + (lane >> 2)];
+            js0 = blkSym0[g + (lane >> 2)];
+        }
+        if (nb == DRAW_GROUP) {
+#pragma unroll
+            for (uint32_t kk = 0; kk < DRAW_GROUP; kk++) step_exact(g, kk, ug + (uint64_t)kk * PH_M1, word);
         } else {
 #pragma unroll 1
-            for (uint32_t kk = 0; kk < b1 - g; kk++) step(g, kk, ug + (uint64_t)kk * PH_M1, word);
+            for (uint32_t kk = 0; kk < nb; kk++) step_exact(g, kk, ug + (uint64_t)kk * PH_M1, word);
         }
         uint32_t any = 0;
 #pragma unroll
         for (int t = 0; t < TW; t++) any |= word[t];
-        if (__any_sync(FM, any != 0u)) resolve(g, word, jmeta, js0);
+        const uint32_t wm = __reduce_or_sync(FM, any);
+        if (!wm) continue;
+        const int i = lane & 3;
+        const uint32_t kind = (jmeta >> (2 * i)) & 3u;
+        const bool mine = (wm >> lane) & 1u;
+        const bool is_dep = kind == CK_DEP1 || kind == CK_DEP2;
+        const uint32_t dep = __ballot_sync(FM, mine && is_dep);
+        if (wm & ~dep) {
+            const uint32_t sym = js0 + ((jmeta >> (8 + 4 * i)) & 15u);
+#pragma unroll
+            for (int t = 0; t < TW; t++) {
+                const uint32_t col = transpose32(word[t], lane);
+                if (mine && !is_dep && col) apply(sym, t, col);
+            }
+        }
+        if (dep) {
+#pragma unroll
+            for (int t = 0; t < TW; t++) enqueue(g, t, word[t] & dep, EV_DEP_ONLY, 4);
+        }
     }
     drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, b0, shot_base, K, k1, lane, apply);
 }
 
 template <int TW, typename Apply>
 __device__ __forceinline__ void draw_scatter(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
-                                             const uint32_t *__restrict__ blkSym0, uint32_t b0, uint32_t b1,
-                                             const Shots<TW> sc, uint64_t shot_base, uint32_t k0, uint32_t k1,
-                                             int lane, uint32_t *q, const Apply &apply)
+                                             const uint32_t *__restrict__ blkSym0, const uint32_t *__restrict__ blkFilt,
+                                             uint32_t b0, uint32_t b1, const Shots<TW> sc, uint64_t shot_base,
+                                             const Keys &K, uint32_t k1, int lane, uint32_t *q, const Apply &apply)
 {
     // a tile straddles a multiple of 2^32 shots only if shot0 is unaligned
     if ((shot_base >> 32) == ((shot_base + 32u * TW - 1u) >> 32))
-        draw_group_impl<TW, true>(blkT, blkMeta, blkSym0, b0, b1, sc, shot_base, k0, k1, lane, q, apply);
+        draw_group_impl<TW, true>(blkT, blkMeta, blkSym0, blkFilt, b0, b1, sc, shot_base, K, k1, lane, q, apply);
     else
-        draw_group_impl<TW, false>(blkT, blkMeta, blkSym0, b0, b1, sc, shot_base, k0, k1, lane, q, apply);
+        draw_group_impl<TW, false>(blkT, blkMeta, blkSym0, blkFilt, b0, b1, sc, shot_base, K, k1, lane, q, apply);
 }
 
 struct FusedParams {
     const uint4 *blkT;
     const uint32_t *blkMeta;
     const uint32_t *blkSym0;
+    const uint32_t *blkFilt;   // per block: FREQUENT, or the largest of its thresholds
     const uint32_t *colOff;    // [n_sym + 1]: rows of symbol s are colRows[colOff[s] .. colOff[s+1])
     const uint32_t *colRows;   // measurement rows whose own part holds the symbol
     int64_t n_blk, n_rows, n_meas, n_det, n_obs;
@@ -467,6 +511,7 @@ struct FusedParams {
     const uint32_t *cOff;      // step C: detector/observable t = XOR of measurement rows
     const uint32_t *cRefs;
     uint64_t seed, shot0, nshots;
+    Keys keys;                 // Philox round keys of the seed (k_fused reads them from its launch parameters)
     uint64_t *out[3];
     int64_t rows0[3], nrow[3];
     uint32_t aux_off_words;    // the warps' event queues (phase 1), the emit stage (phase 3)
@@ -500,8 +545,10 @@ __device__ __forceinline__ uint4 xorw(uint4 a, uint4 b)
 
 // One tile of 32*TW shots of one program, by the whole CTA of NT threads.
 // Ends with a barrier, so the caller may start another tile right away.
+// K: the seed's Philox round keys (from the launch parameters, where the
+// compiler reads them as constant-bank operands, or computed in registers).
 template <int TW, int NT = FUSED_THREADS>
-__device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, uint32_t *sm)
+__device__ __forceinline__ void fused_tile(const FusedParams &p, const Keys &K, uint64_t tile, uint32_t *sm)
 {
     typedef TileWord<TW> TWd;
     typedef typename TWd::T W;
@@ -509,7 +556,7 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
     uint32_t *aux = sm + p.aux_off_words;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const uint64_t trel = tile * (32u * TW);
-    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    const uint32_t k1 = (uint32_t)(p.seed >> 32);
     Shots<TW> sc;
 #pragma unroll
     for (int t = 0; t < TW; t++) sc.s[t] = shot_const(p.shot0 + trel + 32u * t + lane, k1);
@@ -522,7 +569,8 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, uint64_t tile, 
         const uint32_t b1 = (uint32_t)((uint64_t)(warp + 1) * (uint64_t)p.n_blk / (uint64_t)nwarps);
         const uint32_t *colOff = p.colOff, *colRows = p.colRows;
         uint32_t *Rw = sm;
-        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, b0, b1, sc, p.shot0 + trel, k0, k1, lane, aux + warp * FUSED_QCAP,
+        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, p.blkFilt, b0, b1, sc, p.shot0 + trel, K, k1, lane,
+                         aux + warp * FUSED_QCAP,
                          [=](uint32_t sym, int t, uint32_t word) { xor_column<TW>(colOff, colRows, sym, t, word, Rw); });
     }
     __syncthreads();
@@ -592,7 +640,7 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fus
     const uint64_t per_tile = 32u * TW;
     const uint64_t ntiles = (p.nshots + per_tile - 1) / per_tile;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        fused_tile<TW, fused_threads(TW, U)>(p, tile, sm);
+        fused_tile<TW, fused_threads(TW, U)>(p, p.keys, tile, sm);
 }
 
 // Batched form: many programs in one persistent launch per launch shape.
@@ -620,7 +668,10 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U))
             const int mid = (lo + hi) >> 1;
             if (tileEnd[mid] > item) hi = mid; else lo = mid + 1;
         }
-        fused_tile<TW, fused_threads(TW, U)>(progs[lo], item - (lo ? tileEnd[lo - 1] : 0ull), sm);
+        // parameters in global memory: the round keys are computed into registers
+        const uint64_t seed = progs[lo].seed;
+        const Keys K = make_keys((uint32_t)seed, (uint32_t)(seed >> 32));
+        fused_tile<TW, fused_threads(TW, U)>(progs[lo], K, item - (lo ? tileEnd[lo - 1] : 0ull), sm);
     }
 }
 
@@ -660,7 +711,8 @@ __global__ void __launch_bounds__(256) k_dense_fill(uint32_t *__restrict__ Bd, i
 
 __global__ void __launch_bounds__(256, 4) k_draw_dense(const uint4 *__restrict__ blkT,
                                                        const uint32_t *__restrict__ blkMeta,
-                                                       const uint32_t *__restrict__ blkSym0, int64_t n_blk,
+                                                       const uint32_t *__restrict__ blkSym0,
+                                                       const uint32_t *__restrict__ blkFilt, int64_t n_blk,
                                                        uint64_t seed, uint64_t shot0, int64_t ngroups,
                                                        uint32_t *__restrict__ Bd, int64_t bpitch)
 {
@@ -675,7 +727,8 @@ __global__ void __launch_bounds__(256, 4) k_draw_dense(const uint4 *__restrict__
     for (int t = 0; t < 2; t++) sc.s[t] = shot_const(shot_base + 32u * t + lane, k1);
     uint32_t *base = Bd + (size_t)(2 * gw) * (size_t)bpitch * 32u;
     const bool has2 = 2 * gw + 1 < ngroups;
-    draw_scatter<2>(blkT, blkMeta, blkSym0, 0u, (uint32_t)n_blk, sc, shot_base, k0, k1, lane, q + warp * FUSED_QCAP,
+    const Keys K = make_keys(k0, k1);
+    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, 0u, (uint32_t)n_blk, sc, shot_base, K, k1, lane, q + warp * FUSED_QCAP,
                     [=](uint32_t sym, int t, uint32_t word) {
                         if (t == 1 && !has2) return;
                         const uint32_t e = sym + 1u;
@@ -701,7 +754,7 @@ sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, 
     if ((uint64_t)P->n_blk >= event_max_blocks(2))
         return set_error(SP_ERR_INVALID_ARG, "too many channel blocks for the dense draw");
     k_draw_dense<<<(unsigned)ceil_div(ceil_div(ngroups, 2), 8), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->d_blkSym0,
-                                                                            P->n_blk, seed, shot0, ngroups, Bd, bpitch);
+                                                                            P->d_blkFilt, P->n_blk, seed, shot0, ngroups, Bd, bpitch);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
@@ -765,7 +818,7 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     const int64_t nb = (nch + 3) / 4;
     P->n_blk = nb;
     std::vector<uint4> bT((size_t)nb);
-    std::vector<uint32_t> bMeta((size_t)nb), bSym0((size_t)nb + 1, 0);
+    std::vector<uint32_t> bMeta((size_t)nb), bSym0((size_t)nb + 1, 0), bFilt((size_t)nb + 1, 0);
     uint32_t sym = 0;
     for (int64_t b = 0; b < nb; b++) {
         uint32_t Tv[4] = {0, 0, 0, 0}, meta = 0, off = 0;
@@ -782,13 +835,16 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
         }
         meta |= off << 24;
         bT[b] = make_uint4(Tv[0], Tv[1], Tv[2], Tv[3]);
+        const uint64_t sumT = (uint64_t)Tv[0] + Tv[1] + Tv[2] + Tv[3];
+        bFilt[b] = sumT >= FREQUENT_SUM ? FREQUENT : std::max(std::max(Tv[0], Tv[1]), std::max(Tv[2], Tv[3]));
         bMeta[b] = meta;
         sym += off;
     }
     bSym0[nb] = sym;
     if ((int64_t)sym != P->n_sym) return set_error(SP_ERR_CUDA, "channel symbol count mismatch");
     sp_status st;
-    if ((st = upload(&P->d_blkT, bT, s)) || (st = upload(&P->d_blkMeta, bMeta, s)) || (st = upload(&P->d_blkSym0, bSym0, s)))
+    if ((st = upload(&P->d_blkT, bT, s)) || (st = upload(&P->d_blkMeta, bMeta, s)) || (st = upload(&P->d_blkSym0, bSym0, s)) ||
+        (st = upload(&P->d_blkFilt, bFilt, s)))
         return st;
 
     // ---- product program: the measurement rows' own parts by symbol -------
@@ -1012,7 +1068,7 @@ static FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint
                                 uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs)
 {
     FusedParams fp;
-    fp.blkT = P->d_blkT; fp.blkMeta = P->d_blkMeta; fp.blkSym0 = P->d_blkSym0;
+    fp.blkT = P->d_blkT; fp.blkMeta = P->d_blkMeta; fp.blkSym0 = P->d_blkSym0; fp.blkFilt = P->d_blkFilt;
     fp.colOff = P->d_colOff; fp.colRows = P->d_colRows;
     fp.n_blk = P->n_blk; fp.n_rows = P->n_rows; fp.n_meas = P->n_meas; fp.n_det = P->n_det; fp.n_obs = P->n_obs;
     fp.cflag = P->d_fCflag; fp.bItem = P->d_fChain; fp.bOff = P->d_fBOff;
@@ -1022,6 +1078,10 @@ static FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint
     fp.rows0[0] = 0; fp.rows0[1] = P->n_meas; fp.rows0[2] = P->n_meas + P->n_det;
     fp.nrow[0] = P->n_meas; fp.nrow[1] = P->n_det; fp.nrow[2] = P->n_obs;
     fp.aux_off_words = aux_offset(P, tw);
+    for (int r = 0; r < 10; r++) {
+        fp.keys.k0[r] = (uint32_t)seed + (uint32_t)r * PH_W0;
+        fp.keys.k1[r] = (uint32_t)(seed >> 32) + (uint32_t)r * PH_W1;
+    }
     return fp;
 }
 
@@ -1108,7 +1168,10 @@ struct BatchPlan {
 std::mutex g_batch_mu;
 std::vector<BatchPlan *> g_plans;
 uint64_t g_batch_clock = 0;
-cudaStream_t g_capture_stream[64] = {};
+// per device: the capture stream and one branch stream per launch shape
+constexpr int MAX_SHAPES = 8;
+cudaStream_t g_capture_stream[64][MAX_SHAPES] = {};
+cudaEvent_t g_capture_event[64][MAX_SHAPES + 1] = {};
 
 // The per-call part of the members' parameters: seeds and output pointers.
 void fill_params(const BatchPlan &plan, sp_program *const *progs, const uint64_t *seeds, const uint64_t *nshots,
@@ -1190,8 +1253,17 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
             }
         }
         std::vector<uint64_t> tileEnd;
-        for (auto &kv : by_shape) {
-            BatchGroup g = kv.second;
+        // the group with the most work first: the others' CTAs fill its tail
+        std::vector<BatchGroup> shapes;
+        for (auto &kv : by_shape) shapes.push_back(kv.second);
+        auto work = [&](const BatchGroup &g) {
+            double w = 0;
+            for (uint32_t i : g.members) w += (double)progs[i]->n_blk * (double)nshots[i];
+            return w;
+        };
+        std::stable_sort(shapes.begin(), shapes.end(),
+                         [&](const BatchGroup &a, const BatchGroup &b) { return work(a) > work(b); });
+        for (BatchGroup g : shapes) {
             std::stable_sort(g.members.begin(), g.members.end(),
                              [&](uint32_t a, uint32_t b) { return progs[a]->n_blk > progs[b]->n_blk; });
             g.param0 = tileEnd.size();
@@ -1218,19 +1290,37 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
                 return set_error(SP_ERR_OOM, "cudaMalloc of the batch plan failed");
             }
             SP_CUDA(cudaMemcpy(np->d_tileEnd, tileEnd.data(), tileEnd.size() * 8, cudaMemcpyHostToDevice));
-            // ---- capture on a library stream, replay on the caller's -------
-            if (!g_capture_stream[dev])
-                SP_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
-            cudaStream_t cs = g_capture_stream[dev];
+            // ---- capture on library streams, replay on the caller's --------
+            // counter reset, then one branch per launch shape (the shapes'
+            // persistent kernels may overlap), then a join
+            const size_t ng = np->groups.size();
+            if (ng > MAX_SHAPES) return set_error(SP_ERR_INVALID_ARG, "too many launch shapes in one batch");
+            for (size_t k = 0; k < ng; k++)
+                if (!g_capture_stream[dev][k])
+                    SP_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev][k], cudaStreamNonBlocking));
+            for (size_t k : {(size_t)MAX_SHAPES, (size_t)1, (size_t)2, (size_t)3, (size_t)4, (size_t)5, (size_t)6, (size_t)7})
+                if (k == MAX_SHAPES || k < ng)
+                    if (!g_capture_event[dev][k])
+                        SP_CUDA(cudaEventCreateWithFlags(&g_capture_event[dev][k], cudaEventDisableTiming));
+            cudaStream_t cs = g_capture_stream[dev][0];
             SP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             sp_status st = SP_OK;
-            if (cudaMemsetAsync(np->d_counter, 0, np->groups.size() * 8, cs) != cudaSuccess)
-                st = set_error(SP_ERR_CUDA, "counter reset failed during capture");
-            for (size_t k = 0; k < np->groups.size() && st == SP_OK; k++) {
+            auto ok = [&](cudaError_t e, const char *what) {
+                if (e != cudaSuccess && st == SP_OK) st = cuda_error(e, what);
+            };
+            ok(cudaMemsetAsync(np->d_counter, 0, ng * 8, cs), "counter reset during capture");
+            ok(cudaEventRecord(g_capture_event[dev][MAX_SHAPES], cs), "fork during capture");
+            for (size_t k = 0; k < ng && st == SP_OK; k++) {
                 const BatchGroup &g = np->groups[k];
-                batch_kernel(g.tw, g.unroll)<<<g.grid, g.threads, g.smem, cs>>>(
+                cudaStream_t bs = g_capture_stream[dev][k];
+                if (k) ok(cudaStreamWaitEvent(bs, g_capture_event[dev][MAX_SHAPES], 0), "fork during capture");
+                batch_kernel(g.tw, g.unroll)<<<g.grid, g.threads, g.smem, bs>>>(
                     np->d_params + g.param0, (int)g.members.size(), np->d_tileEnd + g.param0, np->d_counter + k);
-                if (cudaGetLastError() != cudaSuccess) st = set_error(SP_ERR_CUDA, "batch kernel launch failed during capture");
+                ok(cudaGetLastError(), "batch kernel launch during capture");
+                if (k) {
+                    ok(cudaEventRecord(g_capture_event[dev][k], bs), "join during capture");
+                    ok(cudaStreamWaitEvent(cs, g_capture_event[dev][k], 0), "join during capture");
+                }
             }
             cudaGraph_t graph = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(cs, &graph);

@@ -132,6 +132,7 @@ struct sp_program {
     uint4 *d_blkT = nullptr;
     uint32_t *d_blkMeta = nullptr;
     uint32_t *d_blkSym0 = nullptr;
+    uint32_t *d_blkFilt = nullptr;  // per block: all-thresholds-large flag or the largest threshold
     // fused product program (see sp_fused.cu)
     uint8_t *d_fCflag = nullptr;      // step 0: constant bit of each measurement row's own part
     uint2 *d_fChain = nullptr;        // step B items (row, parent), per thread, parents first

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(ROOT, "oracle", "symphase_oracle.c")
 PINS = ["test_oracle_golden.py", "test_oracle_chp.py", "test_oracle_statevec.py",
-        "test_oracle_philox.py", "test_oracle_expect.py"]
+        "test_oracle_philox.py", "test_oracle_expect.py", "test_oracle_grouped.py"]
 
 MUTANTS = {
     "cx-phase-rule": ("if (x[a] & z[b] & (x[b] ^ z[a] ^ 1)) flipb(PH(P, r), 0);",
@@ -35,6 +35,13 @@ MUTANTS = {
     "conditional-pauli-rows": ("if ((xb && Z(P, r)[a]) ^ (zb && X(P, r)[a])) {", "if ((xb && X(P, r)[a]) ^ (zb && Z(P, r)[a])) {"),
     "feedforward-lookback": ("P->meas + (P->nmeas - lb) * P->pw);", "P->meas + (P->nmeas - lb + 1) * P->pw);"),
     "feedforward-y-as-x": ("cond_pauli(P, t[j + 1], c != OR_ZIF, c != OR_XIF,", "cond_pauli(P, t[j + 1], c != OR_ZIF, c == OR_ZIF,"),
+    "grouped-first-unconditioned": ("U = i == last ? 4294967295u : or_threshold(P->ch_p[c] / (1.0 - R[i]));",
+                                    "U = i == last ? 4294967295u : or_threshold(P->ch_p[c]);"),
+    "grouped-group-threshold": ("uint32_t G = or_threshold(1.0 - R[0]);", "uint32_t G = or_threshold(1.0 - R[1]);"),
+    "grouped-after-threshold": ("                U = P->ch_T[c];\n", "                U = or_threshold(P->ch_p[c] / (1.0 - R[i]));\n"),
+    "grouped-random-bit": ("if ((w >> (r % 32)) & 1u)", "if ((w >> (r % 2)) & 1u)"),
+    "grouped-dep-category": ("uint64_t m = type == CH_DEP1 ? 3u : 15u;", "uint64_t m = type == CH_DEP1 ? 3u : 14u;"),
+    "grouped-channel-counter": ("(uint32_t)(8 * g + i / 4), 2u", "(uint32_t)(8 * g + i / 8), 2u"),
     "counter-layout": ("uint32_t ctr[4] = {(uint32_t)shot, (uint32_t)(shot >> 32), (uint32_t)(c / 4), 0u};",
                        "uint32_t ctr[4] = {(uint32_t)shot, (uint32_t)(c / 4), (uint32_t)(shot >> 32), 0u};"),
 }
