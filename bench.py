@@ -274,6 +274,83 @@ def _config_section(name, gen, gen_args, shots, chunk, seed, steps):
                        "fused_tile_shots": info["fused_tile_shots"], "fused_variant": info["fused_variant"]}}
 
 
+def _grouped_stream(args):
+    """The opt-in grouped fault draw (stream 2: a group test per 32 channels,
+    then a walk to the first fired channel) on the d=11 and d=17
+    configurations: same records' distribution, other bits. Reported with
+    its expected Philox blocks per shot (group quads + walks of the groups
+    that fire + random-outcome blocks) against the multiply peak, and its
+    record bytes against the HBM peak."""
+    import torch
+    import numpy as np
+    import paper_2311_03906_gb300 as sp
+    from workloads import surface_code
+    peaks = _peaks()
+    out = {}
+    for name, d, p, shots, chunk in (("surface_code_d11_r11_p1e-3", 11, 1e-3, 1_000_000, 0),
+                                     ("surface_code_d17_r17_p2e-3", 17, 2e-3, 1_000_000, 65536)):
+        c = surface_code(d, d, p)
+        prog = sp.build(c)
+        if chunk:
+            prog.set_chunk(chunk)
+        prog.set_stream(2)
+        info = prog.info
+        o = prog.alloc_outputs(shots)
+        stream = torch.cuda.current_stream()
+        for w in range(3):
+            prog.sample(shots, seed=1, shot0=w * shots, out=o)
+        torch.cuda.synchronize()
+        steps = 10
+        prog.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            prog.sample(shots, seed=1, shot0=(3 + k) * shots, out=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = prog.profile_read()
+        prog.profile(False)
+        ms = e0.elapsed_time(e1) / steps
+        kms, kn = prof["fused"]
+        avg = kms / kn
+        # expected Philox blocks per shot: from the channels' probabilities
+        _, kind, _ = prog.channels()
+        pf = np.array([op_p for op_p in _fault_probabilities(c)])
+        ngrp = -(-len(pf) // 32)
+        walks = 0.0
+        for g in range(ngrp):
+            pg = 1.0 - np.prod(1.0 - pf[32 * g:32 * g + 32])
+            walks += pg * -(-len(pf[32 * g:32 * g + 32]) // 4)
+        nrnd = int((kind == 3).sum())
+        blocks = -(-ngrp // 4) + walks + -(-nrnd // 128)
+        mul = blocks * 32.0 * shots * (steps / kn) / (avg / 1e3) / 1e12
+        mul_peak = 152 * 64 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        nrec = info["num_measurements"] + info["num_detectors"] + info["num_observables"]
+        rec_bytes = nrec / 8.0 * shots * (steps / kn)
+        out[name] = {"value": shots / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                     "record_gbit_s": shots / (ms / 1e3) * nrec / 1e9,
+                     "philox_blocks_per_shot": blocks,
+                     "roofline_multiply": {"achieved": mul, "peak": mul_peak, "unit": "Tmul/s", "frac": mul / mul_peak},
+                     "roofline_hbm": {"achieved": rec_bytes / (avg / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                      "frac": rec_bytes / (avg / 1e3) / 1e9 / peaks["hbm_gbs"]},
+                     "fused_tile_shots": info["fused_tile_shots"], "fused_variant": info["fused_variant"]}
+        prog.close()
+    return out
+
+
+def _fault_probabilities(circuit):
+    """Probability of each channel other than random outcomes, in channel
+    order (one per target of a one-qubit noise op, one per pair of
+    DEPOLARIZE2)."""
+    ps = []
+    for op in circuit.ops:
+        if op.name in ("X_ERROR", "Y_ERROR", "Z_ERROR", "DEPOLARIZE1"):
+            ps += [op.arg] * len(op.targets)
+        elif op.name == "DEPOLARIZE2":
+            ps += [op.arg] * (len(op.targets) // 2)
+    return ps
+
+
 def _batched_vs_plain(args):
     """64 uneven circuits (rotated surface codes d = 3..15, p in {5e-4, 1e-3,
     2e-3}, seeds 0..63), 1e5 shots each: one graph-captured batched enqueue
@@ -664,6 +741,8 @@ def run_ours(args):
     if world == 1 and not args.no_d17:
         line["d17"] = _config_section("surface_code_d17_r17_p2e-3", "surface_code", (17, 17, 2e-3), 1_000_000, 65536,
                                       seed=3, steps=3)
+    if world == 1 and not args.no_grouped:
+        line["grouped_stream"] = _grouped_stream(args)
     if world == 1 and not args.no_batch:
         line["batched"] = _batched_vs_plain(args)
     if world == 1 and not args.no_dense:
@@ -700,6 +779,7 @@ def main():
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-d17", action="store_true", help="skip the d=17 configuration")
     ap.add_argument("--no-c1", action="store_true", help="skip the repetition-code configuration")
+    ap.add_argument("--no-grouped", action="store_true", help="skip the grouped fault-draw stream")
     ap.add_argument("--profile", action="store_true",
                     help="build, then one 65536-shot sample only (the case captured by ncu)")
     args = ap.parse_args()

@@ -28,7 +28,7 @@ PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED, PATH_TENSOR = 0, 1, 2, 3, 4
 EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",
            "sp_sample_batch", "sp_expect", "sp_expect_sign",
            "sp_expect_grad", "sp_export_rows", "sp_export_channels", "sp_set_path", "sp_set_fused_config",
-           "sp_set_chunk", "sp_device_status", "sp_set_wait_limit",
+           "sp_set_chunk", "sp_set_stream", "sp_device_status", "sp_set_wait_limit",
            "sp_profile_enable", "sp_profile_read", "sp_batch_plans", "sp_debug_fail_alloc",
            "sp_debug_live_allocs", "sp_free", "sp_last_error")
 KERNEL_CLASSES = ("draw", "product", "emit", "fused", "tensor")
@@ -56,7 +56,7 @@ class sp_info_t(C.Structure):
                 ("num_random", C.c_uint64), ("nnz_rows", C.c_uint64), ("nnz_delta", C.c_uint64),
                 ("log_words", C.c_uint64), ("density", C.c_double), ("path", C.c_int32),
                 ("fused_tile_shots", C.c_int32), ("fused_variant", C.c_int32),
-                ("fused_ctas_per_sm", C.c_int32), ("autotune_launches", C.c_int32), ("reserved", C.c_int32),
+                ("fused_ctas_per_sm", C.c_int32), ("autotune_launches", C.c_int32), ("stream", C.c_int32),
                 ("chunk_shots", C.c_uint64), ("build_ms", C.c_double), ("path_probe_ms", C.c_double * 5)]
 
 
@@ -90,6 +90,7 @@ def load() -> C.CDLL:
     lib.sp_export_channels.argtypes = [vp, vp, vp, vp]
     lib.sp_set_path.argtypes = [vp, i32]
     lib.sp_set_chunk.argtypes = [vp, u64]
+    lib.sp_set_stream.argtypes = [vp, i32]
     lib.sp_device_status.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.sp_set_wait_limit.argtypes = [vp, u64]
     lib.sp_set_fused_config.argtypes = [vp, i32, i32]
@@ -235,6 +236,11 @@ class Program:
 
     def set_fused_config(self, tile_shots: int, variant: int = 1):
         _check(self._lib.sp_set_fused_config(self._h, tile_shots, variant))
+        self.refresh_info()
+
+    def set_stream(self, stream: int):
+        """Fault-draw stream: 1 per-channel Philox (default), 2 grouped."""
+        _check(self._lib.sp_set_stream(self._h, int(stream)))
         self.refresh_info()
 
     def set_chunk(self, chunk_shots: int):

@@ -979,6 +979,7 @@ namespace {
 
 struct Flat {
     std::vector<Inst> insts;
+    std::vector<double> noise_p;   // probability of each noise instruction, in order (one per channel)
     std::vector<uint32_t> det_off{0}, det_refs;
     std::vector<std::vector<uint32_t>> obs;
     int64_t nmeas = 0;
@@ -1037,7 +1038,10 @@ sp_status flatten(const sp_circuit_desc *d, Flat &F)
         } break;
         case SP_OP_X_ERROR: case SP_OP_Y_ERROR: case SP_OP_Z_ERROR: case SP_OP_DEPOLARIZE1: {
             const uint32_t code = c == SP_OP_X_ERROR ? I_XERR : c == SP_OP_Y_ERROR ? I_YERR : c == SP_OP_Z_ERROR ? I_ZERR : I_DEP1;
-            for (uint32_t j = 0; j < k; j++) F.insts.push_back({code, op.targets[j], 0, T, pbits});
+            for (uint32_t j = 0; j < k; j++) {
+                F.insts.push_back({code, op.targets[j], 0, T, pbits});
+                F.noise_p.push_back(op.arg);
+            }
             F.cap_sym += (int64_t)k * (c == SP_OP_DEPOLARIZE1 ? 2 : 1);
         } break;
         case SP_OP_DEPOLARIZE2:
@@ -1045,6 +1049,7 @@ sp_status flatten(const sp_circuit_desc *d, Flat &F)
                 if (op.targets[j] == op.targets[j + 1])
                     return set_error(SP_ERR_INVALID_ARG, "op " + std::to_string(i) + ": DEPOLARIZE2 on one qubit");
                 F.insts.push_back({I_DEP2, op.targets[j], op.targets[j + 1], T, pbits});
+                F.noise_p.push_back(op.arg);
             }
             F.cap_sym += 2 * (int64_t)k;
             break;
@@ -1189,6 +1194,7 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     P->n_det = (int64_t)F.det_off.size() - 1;
     P->n_obs = (int64_t)F.obs.size();
     P->n_rows = P->n_meas + P->n_det + P->n_obs;
+    P->h_fault_p = F.noise_p;
 
     Temp tmp;
     const int Wq = std::max(1, (n + 31) / 32);

@@ -69,7 +69,7 @@ static void release(sp_program *P)
                     P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta, P->d_blkFilt,
                     P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs,
                     P->d_colOff, P->d_colRows, P->d_AT, P->d_tc_coef[0], P->d_tc_coef[1], P->d_tc_coef[2],
-                    P->d_tc_status};
+                    P->d_tc_status, P->d_s2Ch, P->d_s2G, P->d_s2Rand};
     for (void *b : bufs) if (b) dev_free(b);
     if (P->h_stage) cudaFreeHost(P->h_stage);
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -195,6 +195,7 @@ sp_status sp_info(const sp_program *P, sp_info_t *o)
     o->fused_variant = P->fused_tw ? P->fused_unroll : 0;
     o->fused_ctas_per_sm = P->fused_tw ? P->fused_ctas_per_sm : 0;
     o->autotune_launches = P->autotune_launches;
+    o->stream = P->stream;
     o->chunk_shots = (uint64_t)P->chunk_shots;
     o->build_ms = P->build_ms;
     for (int k = 0; k < 5; k++) o->path_probe_ms[k] = P->path_probe_ms[k];
@@ -355,6 +356,8 @@ sp_status sp_export_channels(const sp_program *P, uint32_t *h_T, uint8_t *h_kind
 sp_status sp_set_path(sp_program *P, int32_t path)
 {
     if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
+    if (P->stream == 2 && path != SP_PATH_FUSED && !(path == SP_PATH_AUTO && P->build_path == SP_PATH_FUSED))
+        return set_error(SP_ERR_INVALID_ARG, "the grouped draw (stream 2) runs on the fused path only");
     if (path == SP_PATH_AUTO) {
         P->path = P->build_path;
         reconfigured(P);
@@ -379,6 +382,21 @@ sp_status sp_set_fused_config(sp_program *P, int32_t tile_shots, int32_t variant
     const sp_status st = fused_select(P, tile_shots / 32, variant);
     if (st == SP_OK) reconfigured(P);
     return st;
+}
+
+sp_status sp_set_stream(sp_program *P, int32_t stream)
+{
+    if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
+    if (stream != 1 && stream != 2) return set_error(SP_ERR_INVALID_ARG, "stream must be 1 or 2");
+    if (stream == 2) {
+        if (!P->fused_tw) return set_error(SP_ERR_INVALID_ARG, "the grouped draw (stream 2) needs the fused path");
+        const sp_status st = ensure_grouped(P, nullptr);
+        if (st != SP_OK) return st;
+        P->path = SP_PATH_FUSED;
+    }
+    P->stream = stream;
+    reconfigured(P);
+    return SP_OK;
 }
 
 sp_status sp_device_status(sp_program *P, int32_t *status)

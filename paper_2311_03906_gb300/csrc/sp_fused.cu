@@ -29,6 +29,7 @@
 // computes it once per block: 16 of the 20 wide multiplies of a block remain
 // per (shot, block).
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -36,116 +37,13 @@
 #include <tuple>
 #include <vector>
 
-#include "sp_internal.h"
+#include "sp_fused_dev.cuh"
 
 namespace sp {
-
-constexpr uint32_t FM = 0xffffffffu;
-constexpr uint32_t PH_M0 = 0xD2511F53u, PH_M1 = 0xCD9E8D57u;
-constexpr uint32_t PH_W0 = 0x9E3779B9u, PH_W1 = 0xBB67AE85u;
-constexpr int FUSED_THREADS = 512;
-
-
-// Per-shot quantities of the first two Philox rounds that do not depend on
-// the channel block.
-struct ShotConst {
-    uint32_t c1;     // shot hi (counter word 1)
-    uint32_t x2;     // round-1 output word 2 = hi(M0*shot_lo) ^ k1
-    uint32_t x3;     // round-1 output word 3 = lo(M0*shot_lo)
-    uint32_t r2hi;   // hi(M1 * x2), round 2
-    uint32_t r2lo;   // lo(M1 * x2), round 2
-};
-
-__device__ __forceinline__ ShotConst shot_const(uint64_t shot, uint32_t k1)
-{
-    ShotConst s;
-    const uint64_t p0 = (uint64_t)PH_M0 * (uint32_t)shot;
-    s.c1 = (uint32_t)(shot >> 32);
-    s.x2 = (uint32_t)(p0 >> 32) ^ k1;
-    s.x3 = (uint32_t)p0;
-    const uint64_t q = (uint64_t)PH_M1 * s.x2;
-    s.r2hi = (uint32_t)(q >> 32);
-    s.r2lo = (uint32_t)q;
-    return s;
-}
-
-// Round keys k + r*W for r = 0..9 (the same for every lane).
-struct Keys {
-    uint32_t k0[10], k1[10];
-};
-
-__device__ __forceinline__ Keys make_keys(uint32_t k0, uint32_t k1)
-{
-    Keys K;
-#pragma unroll
-    for (int r = 0; r < 10; r++) {
-        K.k0[r] = k0 + (uint32_t)r * PH_W0;
-        K.k1[r] = k1 + (uint32_t)r * PH_W1;
-    }
-    return K;
-}
-
-// Rounds 3..10 of Philox4x32-10 from the state (c0, c1, c2, c3) after round 2.
-__device__ __forceinline__ void philox_tail(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const Keys &K,
-                                            uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
-{
-#pragma unroll
-    for (int r = 2; r < 10; r++) {
-        const uint64_t p0 = (uint64_t)PH_M0 * c0;
-        const uint64_t p1 = (uint64_t)PH_M1 * c2;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[r];
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[r];
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
-        c0 = n0;
-        c2 = n2;
-    }
-    o0 = c0; o1 = c1; o2 = c2; o3 = c3;
-}
-
-// Rounds 1..10 of Philox4x32-10 for counter (shot, b): uhi/ulo = M1*b and
-// shot_hi = the shot's high word s.c1.  Round 1's output word 0 is
-// uhi ^ shot_hi ^ k0 and round 2 multiplies it by M0: that product p is all
-// of round 2 that depends on b, so a caller that knows it to be the same in
-// several evaluations may compute it once and call philox_from_p.
-__device__ __forceinline__ void philox_from_p(const ShotConst &s, uint64_t p, uint32_t ulo, const Keys &K,
-                                              uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
-{
-    philox_tail(s.r2hi ^ ulo ^ K.k0[1], s.r2lo, (uint32_t)(p >> 32) ^ s.x3 ^ K.k1[1], (uint32_t)p, K, o0, o1, o2, o3);
-}
-
-__device__ __forceinline__ void philox_block(const ShotConst &s, uint32_t shot_hi, uint32_t uhi, uint32_t ulo,
-                                             const Keys &K, uint32_t &o0, uint32_t &o1, uint32_t &o2, uint32_t &o3)
-{
-    const uint64_t p = (uint64_t)PH_M0 * (uhi ^ shot_hi ^ K.k0[0]);
-    philox_from_p(s, p, ulo, K, o0, o1, o2, o3);
-}
-
-// floor(u*m/T) for u < T, exactly: a single-precision estimate (relative
-// error below 2^-21, so off by at most one) corrected with integer products.
-__device__ __forceinline__ uint32_t cat_index(uint32_t u, uint32_t T, uint32_t m)
-{
-    const uint64_t um = (uint64_t)u * m;
-    uint32_t k = (uint32_t)((float)um * __frcp_rn((float)T));
-    k = min(k, m - 1u);
-    if ((uint64_t)k * T > um) k--;
-    else if ((uint64_t)(k + 1u) * T <= um) k++;
-    return k;
-}
-
-__device__ __forceinline__ uint32_t chan_bits(uint32_t u, uint32_t T, uint32_t kind)
-{
-    if (u >= T) return 0u;
-    if (kind == CK_DEP1) return cat_index(u, T, 3u) + 1u;
-    if (kind == CK_DEP2) return cat_index(u, T, 15u) + 1u;
-    return 1u;
-}
 
 // Draw the symbols of blocks [b0, b1) for TW shots per lane (shot words
 // w_t = 32-shot groups).  Each flushed 32-symbol column group is handed to
 // sink(symbol base, lane's column words[TW]) with the lane's symbol = base+lane.
-template <int TW> struct Cols { uint32_t v[TW]; };
-template <int TW> struct Shots { ShotConst s[TW]; };
 
 template <int TW, int U, typename Sink>
 __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
@@ -260,43 +158,6 @@ __device__ __forceinline__ void draw_blocks(const uint4 *__restrict__ blkT, cons
     }
 }
 
-// Fired-event queue of one warp: FUSED_QCAP 32-bit words in shared memory.
-// An event is one (channel block, shot) in which some channel may have
-// fired: bits 0..4 lane, bit 5 "depolarizing channels only" (its one-symbol
-// channels were already applied), then the tile word t (one bit for
-// TW <= 2, two for TW = 4), then block - the warp's first block in the
-// remaining bits.
-constexpr uint32_t FUSED_QCAP = 128;
-constexpr uint32_t EV_DEP_ONLY = 1u << 5;
-__host__ __device__ constexpr int event_tbits(int tw) { return tw == 4 ? 2 : 1; }
-__host__ __device__ constexpr uint32_t event_max_blocks(int tw) { return 1u << (32 - 6 - event_tbits(tw)); }
-// Channel blocks whose compare results are gathered before one vote.
-constexpr uint32_t DRAW_GROUP = 8;
-static_assert(4 * DRAW_GROUP == 32, "a group's channels map one to one onto the lanes");
-// A block is "frequent" when its channels' thresholds add up to at least
-// 2^28 (a lane's shot sees one of them fire with probability >= 1/16); its
-// blkFilt entry is then FREQUENT, else the largest of its four thresholds.
-constexpr uint32_t FREQUENT = 0xFFFFFFFFu;
-constexpr uint64_t FREQUENT_SUM = 1ull << 28;
-
-// XOR the word x into tile word t of every measurement row whose own part
-// holds symbol s (Eq. sampling restricted to the symbol's column; shared
-// atomics, since several symbols of one row may be applied at once).
-template <int TW>
-__device__ __forceinline__ void xor_column(const uint32_t *__restrict__ colOff, const uint32_t *__restrict__ colRows,
-                                           uint32_t s, int t, uint32_t x, uint32_t *Rw)
-{
-    const uint32_t e = colOff[s + 1];
-    for (uint32_t k = colOff[s]; k < e; k++) atomicXor(&Rw[colRows[k] * TW + t], x);
-}
-
-// Fired mask of one Philox block: bit i = channel i of the block fired.
-__device__ __forceinline__ uint32_t fired4(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, const uint4 T)
-{
-    return (uint32_t)(r0 < T.x) | ((uint32_t)(r1 < T.y) << 1) | ((uint32_t)(r2 < T.z) << 2) |
-           ((uint32_t)(r3 < T.w) << 3);
-}
-
 // Apply the queued events e = lane, lane+32, ... < n: recompute the event's
 // Philox block, compare its four words with the thresholds, turn each fired
 // channel into its symbol bits and hand each (symbol, tile word, shot bit)
@@ -376,19 +237,26 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
     const uint32_t c1u = (uint32_t)(shot_base >> 32);
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t cnt = 0;
-    // queue the events flagged in m (bit k = block g + k), one per set bit
+    // queue the events flagged in m (bit k = block g + k), one per set bit;
+    // as soon as 32 are queued they are applied by one lane each, so that
+    // the drains' memory latency overlaps the other warps' draws
     auto enqueue = [&](uint32_t g, int t, uint32_t m, uint32_t flags, int stride) {
         while (__any_sync(FM, m != 0u)) {
-            if (cnt > FUSED_QCAP - 32u) {
-                drain_fired<TW>(q, cnt, blkT, blkMeta, blkSym0, b0, shot_base, K, k1, lane, apply);
-                cnt = 0;
-            }
             const uint32_t k = m ? (uint32_t)(__ffs(m) - 1) / (uint32_t)stride : 0u;
             const uint32_t bal = __ballot_sync(FM, m != 0u);
             if (m)
                 q[cnt + __popc(bal & lt)] = ((g + k - b0) << (6 + TB)) | ((uint32_t)t << 6) | flags | (uint32_t)lane;
             cnt += __popc(bal);
             m &= ~(((1u << stride) - 1u) << (stride * k));
+            if (cnt >= 32u) {
+                drain_fired<TW>(q, 32u, blkT, blkMeta, blkSym0, b0, shot_base, K, k1, lane, apply);
+                cnt -= 32u;
+                // the rest (fewer than 32) moves to the front
+                const uint32_t rest = (uint32_t)lane < cnt ? q[32 + lane] : 0u;
+                __syncwarp();
+                if ((uint32_t)lane < cnt) q[lane] = rest;
+                __syncwarp();
+            }
         }
     };
     // rare block g+kk: bit kk of word[t] = the least of the shot's four
@@ -497,141 +365,20 @@ __device__ __forceinline__ void draw_scatter(const uint4 *__restrict__ blkT, con
         draw_group_impl<TW, false>(blkT, blkMeta, blkSym0, blkFilt, b0, b1, sc, shot_base, K, k1, lane, q, apply);
 }
 
-struct FusedParams {
-    const uint4 *blkT;
-    const uint32_t *blkMeta;
-    const uint32_t *blkSym0;
-    const uint32_t *blkFilt;   // per block: FREQUENT, or the largest of its thresholds
-    const uint32_t *colOff;    // [n_sym + 1]: rows of symbol s are colRows[colOff[s] .. colOff[s+1])
-    const uint32_t *colRows;   // measurement rows whose own part holds the symbol
-    int64_t n_blk, n_rows, n_meas, n_det, n_obs;
-    const uint8_t *cflag;      // [n_meas] constant bit of each measurement row's own part
-    const uint2 *bItem;        // step B: (row, parent), parents first within a thread
-    const uint32_t *bOff;      // [threads + 1]
-    const uint32_t *cOff;      // step C: detector/observable t = XOR of measurement rows
-    const uint32_t *cRefs;
-    uint64_t seed, shot0, nshots;
-    Keys keys;                 // Philox round keys of the seed (k_fused reads them from its launch parameters)
-    uint64_t *out[3];
-    int64_t rows0[3], nrow[3];
-    uint32_t aux_off_words;    // the warps' event queues (phase 1), the emit stage (phase 3)
-};
-
-template <int TW> struct TileWord;
-template <> struct TileWord<1> {
-    typedef uint32_t T;
-    __device__ static T zero() { return 0u; }
-    __device__ static T ones() { return FM; }
-    __device__ static uint32_t get(T v, int) { return v; }
-};
-template <> struct TileWord<2> {
-    typedef uint2 T;
-    __device__ static T zero() { return make_uint2(0u, 0u); }
-    __device__ static T ones() { return make_uint2(FM, FM); }
-    __device__ static uint32_t get(T v, int t) { return t ? v.y : v.x; }
-};
-template <> struct TileWord<4> {
-    typedef uint4 T;
-    __device__ static T zero() { return make_uint4(0u, 0u, 0u, 0u); }
-    __device__ static T ones() { return make_uint4(FM, FM, FM, FM); }
-    __device__ static uint32_t get(T v, int t) { return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w; }
-};
-__device__ __forceinline__ uint32_t xorw(uint32_t a, uint32_t b) { return a ^ b; }
-__device__ __forceinline__ uint2 xorw(uint2 a, uint2 b) { return make_uint2(a.x ^ b.x, a.y ^ b.y); }
-__device__ __forceinline__ uint4 xorw(uint4 a, uint4 b)
-{
-    return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
-}
-
-// One tile of 32*TW shots of one program, by the whole CTA of NT threads.
-// Ends with a barrier, so the caller may start another tile right away.
-// K: the seed's Philox round keys (from the launch parameters, where the
-// compiler reads them as constant-bank operands, or computed in registers).
-template <int TW, int NT = FUSED_THREADS>
-__device__ __forceinline__ void fused_tile(const FusedParams &p, const Keys &K, uint64_t tile, uint32_t *sm)
-{
-    typedef TileWord<TW> TWd;
-    typedef typename TWd::T W;
-    W *Rs = reinterpret_cast<W *>(sm);                       // [n_rows] records, bit-sliced
-    uint32_t *aux = sm + p.aux_off_words;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const uint64_t trel = tile * (32u * TW);
-    const uint32_t k1 = (uint32_t)(p.seed >> 32);
-    Shots<TW> sc;
-#pragma unroll
-    for (int t = 0; t < TW; t++) sc.s[t] = shot_const(p.shot0 + trel + 32u * t + lane, k1);
-    // own parts start from their constants
-    for (int64_t j = tid; j < p.n_meas; j += blockDim.x) Rs[j] = p.cflag[j] ? TWd::ones() : TWd::zero();
-    __syncthreads();
-    // ---- phase 1 + 2A: draw; fired symbols flip the own parts holding them --
+// The per-channel Philox stream (the default draw): warp w of the CTA owns
+// the channel blocks [b0, b1) of an even split.
+struct DrawPerChannel {
+    __device__ static uint32_t shot_key(uint64_t seed) { return (uint32_t)(seed >> 32); }
+    template <int TW, typename Apply>
+    __device__ static void run(const FusedParams &p, const Keys &K, const Shots<TW> &sc, uint64_t shot_base, int warp,
+                               int nwarps, int lane, uint32_t *q, const Apply &apply)
     {
         const uint32_t b0 = (uint32_t)((uint64_t)warp * (uint64_t)p.n_blk / (uint64_t)nwarps);
         const uint32_t b1 = (uint32_t)((uint64_t)(warp + 1) * (uint64_t)p.n_blk / (uint64_t)nwarps);
-        const uint32_t *colOff = p.colOff, *colRows = p.colRows;
-        uint32_t *Rw = sm;
-        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, p.blkFilt, b0, b1, sc, p.shot0 + trel, K, k1, lane,
-                         aux + warp * FUSED_QCAP,
-                         [=](uint32_t sym, int t, uint32_t word) { xor_column<TW>(colOff, colRows, sym, t, word, Rw); });
+        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, p.blkFilt, b0, b1, sc, shot_base, K, (uint32_t)(p.seed >> 32),
+                         lane, q, apply);
     }
-    __syncthreads();
-    // ---- phase 2B: parent chains, m_j = own part ^ m_parent ---------------
-    // (trees are scheduled over FUSED_THREADS lists; a smaller CTA walks
-    // several lists, each independent of the others)
-    for (int th = tid; th < FUSED_THREADS; th += NT) {
-        const uint32_t e = p.bOff[th + 1];
-        for (uint32_t i = p.bOff[th]; i < e; i++) {
-            const uint2 rp = p.bItem[i];
-            Rs[rp.x] = xorw(Rs[rp.x], Rs[rp.y]);
-        }
-    }
-    __syncthreads();
-    // ---- phase 2C: detectors and observables from measurement records ------
-    for (int64_t t = tid; t < p.n_det + p.n_obs; t += blockDim.x) {
-        W acc = TWd::zero();
-        for (uint32_t k = p.cOff[t]; k < p.cOff[t + 1]; k++) acc = xorw(acc, Rs[p.cRefs[k]]);
-        Rs[p.n_meas + t] = acc;
-    }
-    __syncthreads();
-    // ---- phase 3: emit shot-major records (stage aliases the queues) -------
-    uint32_t *stage = aux;
-#pragma unroll
-    for (int sg = 0; sg < 3; sg++) {
-        uint64_t *dst = p.out[sg];
-        const int64_t n = p.nrow[sg];
-        if (!dst || n == 0) continue;
-        const int64_t row0 = p.rows0[sg];
-        const int words32 = (int)(2 * ((n + 63) / 64));
-        const int stride = words32 + 1;
-        for (int g = warp; g < words32; g += nwarps) {
-            const int64_t r = 32 * (int64_t)g + lane;
-#pragma unroll
-            for (int t = 0; t < TW; t++) {
-                const uint32_t x = r < n ? TWd::get(Rs[row0 + r], t) : 0u;
-                stage[(32 * t + lane) * stride + g] = __any_sync(FM, x != 0u) ? transpose32(x, lane) : 0u;
-            }
-        }
-        __syncthreads();
-        uint32_t *o32 = reinterpret_cast<uint32_t *>(dst);
-        for (int sh = warp; sh < 32 * TW; sh += nwarps) {
-            const uint64_t shot = trel + (uint64_t)sh;
-            if (shot >= p.nshots) continue;
-            uint32_t *o = o32 + shot * (uint64_t)words32;
-            for (int g = lane; g < words32; g += 32) o[g] = stage[sh * stride + g];
-        }
-        __syncthreads();
-    }
-    // phase 3 may have been skipped (no outputs): keep the tile boundary
-    __syncthreads();
-}
-
-// Launch shapes: 32- and 64-shot tiles at 512 threads and two CTAs per SM
-// (64 registers); U = 2 marks the 64-shot variant compiled for one CTA per
-// SM with more registers, U = 3 the 64-shot variant at 256 threads and four
-// CTAs per SM.  128-shot tiles (four independent Philox streams
-// per thread) run at 256 threads and two CTAs per SM (U = 1) or 512 threads
-// and one CTA per SM (U = 2), 128 registers either way.
-__host__ __device__ constexpr int fused_threads(int tw, int u) { return (tw == 4 && u == 1) || u == 3 ? 256 : FUSED_THREADS; }
-__host__ __device__ constexpr int fused_minb(int tw, int u) { return u == 3 ? 4 : (u == 2 && tw != 1 ? 1 : 2); }
+};
 
 template <int TW, int U>
 __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fused(FusedParams p)
@@ -640,7 +387,7 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fus
     const uint64_t per_tile = 32u * TW;
     const uint64_t ntiles = (p.nshots + per_tile - 1) / per_tile;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        fused_tile<TW, fused_threads(TW, U)>(p, p.keys, tile, sm);
+        fused_tile<TW, fused_threads(TW, U), DrawPerChannel>(p, p.keys, tile, sm);
 }
 
 // Batched form: many programs in one persistent launch per launch shape.
@@ -671,7 +418,7 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U))
         // parameters in global memory: the round keys are computed into registers
         const uint64_t seed = progs[lo].seed;
         const Keys K = make_keys((uint32_t)seed, (uint32_t)(seed >> 32));
-        fused_tile<TW, fused_threads(TW, U)>(progs[lo], K, item - (lo ? tileEnd[lo - 1] : 0ull), sm);
+        fused_tile<TW, fused_threads(TW, U), DrawPerChannel>(progs[lo], K, item - (lo ? tileEnd[lo - 1] : 0ull), sm);
     }
 }
 
@@ -1064,10 +811,11 @@ sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0,
     return SP_OK;
 }
 
-static FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint64_t shot0, uint64_t nshots,
-                                uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs)
+FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint64_t shot0, uint64_t nshots,
+                         uint64_t *d_meas, uint64_t *d_det, uint64_t *d_obs)
 {
     FusedParams fp;
+    memset(&fp, 0, sizeof fp);
     fp.blkT = P->d_blkT; fp.blkMeta = P->d_blkMeta; fp.blkSym0 = P->d_blkSym0; fp.blkFilt = P->d_blkFilt;
     fp.colOff = P->d_colOff; fp.colRows = P->d_colRows;
     fp.n_blk = P->n_blk; fp.n_rows = P->n_rows; fp.n_meas = P->n_meas; fp.n_det = P->n_det; fp.n_obs = P->n_obs;
@@ -1082,6 +830,8 @@ static FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint
         fp.keys.k0[r] = (uint32_t)seed + (uint32_t)r * PH_W0;
         fp.keys.k1[r] = (uint32_t)(seed >> 32) + (uint32_t)r * PH_W1;
     }
+    fp.s2Ch = P->d_s2Ch; fp.s2G = P->d_s2G; fp.s2Rand = P->d_s2Rand;
+    fp.n_fault = (uint32_t)P->s2_nfault; fp.n_grp = (uint32_t)P->s2_ngrp; fp.n_rnd = (uint32_t)P->s2_nrnd;
     return fp;
 }
 
@@ -1090,6 +840,7 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
 {
     if (nshots == 0) return SP_OK;
     if (!P->fused_tw) return set_error(SP_ERR_INVALID_ARG, "fused path unavailable for this program");
+    if (P->stream == 2) return grouped_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     const FusedParams fp = fused_params(P, P->fused_tw, seed, shot0, nshots, d_meas, d_det, d_obs);
     const uint64_t per_tile = 32u * (uint64_t)P->fused_tw;
     const uint64_t ntiles = (nshots + per_tile - 1) / per_tile;
@@ -1240,7 +991,7 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
             const sp_program *P = progs[i];
             np->progs.push_back(P);
             if (nshots[i] == 0) continue;
-            if (P->path == SP_PATH_FUSED && P->fused_tw) {
+            if (P->path == SP_PATH_FUSED && P->fused_tw && P->stream == 1) {
                 BatchGroup &g = by_shape[std::make_tuple(P->fused_tw, P->fused_unroll, P->fused_ctas_per_sm)];
                 g.tw = P->fused_tw;
                 g.unroll = P->fused_unroll;

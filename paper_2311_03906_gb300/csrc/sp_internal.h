@@ -133,6 +133,14 @@ struct sp_program {
     uint32_t *d_blkMeta = nullptr;
     uint32_t *d_blkSym0 = nullptr;
     uint32_t *d_blkFilt = nullptr;  // per block: all-thresholds-large flag or the largest threshold
+    // grouped draw (stream 2, sp_grouped.cu): built on the first sp_set_stream(prog, 2)
+    int stream = 1;
+    std::vector<double> h_fault_p;    // probability of each channel other than random outcomes, in order
+    uint4 *d_s2Ch = nullptr;
+    uint4 *d_s2G = nullptr;
+    uint32_t *d_s2Rand = nullptr;
+    int64_t s2_nfault = 0, s2_ngrp = 0, s2_nrnd = 0;
+    int s2_ctas_per_sm = 0, s2_cfg = 0;   // occupancy of the grouped kernel for launch shape s2_cfg
     // fused product program (see sp_fused.cu)
     uint8_t *d_fCflag = nullptr;      // step 0: constant bit of each measurement row's own part
     uint2 *d_fChain = nullptr;        // step B items (row, parent), per thread, parents first
@@ -224,6 +232,10 @@ void batch_forget(const sp_program *P);
 size_t batch_plan_count();
 constexpr size_t BATCH_MAX_PLANS = 8;
 sp_status fused_select(sp_program *P, int tw, int unroll);
+// grouped draw (sp_grouped.cu)
+sp_status ensure_grouped(sp_program *P, cudaStream_t s);
+sp_status grouped_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
+                        uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
 sp_status autotune(sp_program *P, cudaStream_t s);
 sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *B,
                              int64_t pitch, cudaStream_t s);

@@ -71,6 +71,8 @@ extern "C" sp_status sp_sample_static(sp_program *P, uint64_t seed, uint64_t sho
         return set_error(SP_ERR_TOO_LARGE,
                          "program needs " + std::to_string(rows * 4) + " bytes per 32 shots; the static scratch holds " +
                              std::to_string(STATIC_SCRATCH_BYTES) + " bytes");
+    if (P->stream != 1)
+        return set_error(SP_ERR_INVALID_ARG, "the static-scratch entry point draws the per-channel stream (stream 1) only");
     if (nshots == 0) return SP_OK;
     // the program's tables and the scratch must live on the same GPU
     int dev = -1;
