@@ -51,17 +51,23 @@ __device__ __forceinline__ void philox_tagged(const ShotConst &s, uint32_t ctr2,
 }
 
 // Symbol bits of a channel decided by threshold U: 1 for a one-symbol
-// channel, k+1 with k = min(floor(u m / U), m - 1) for a depolarizing one.
+// channel, k+1 with k = min(floor(u m / U), m - 1) for a depolarizing one
+// (cat_index is exact for u < U; u >= U happens only for a group's last
+// channel with p > 0, which fires regardless, and gives k = m - 1).
 __device__ __forceinline__ uint32_t grouped_outcome(uint32_t kind, uint32_t u, uint32_t U)
 {
     if (kind != CK_DEP1 && kind != CK_DEP2) return 1u;
-    const uint64_t m = kind == CK_DEP1 ? 3u : 15u;
-    const uint64_t k = ((uint64_t)u * m) / (uint64_t)(U ? U : 1u);
-    return (uint32_t)(k < m - 1 ? k : m - 1) + 1u;
+    const uint32_t m = kind == CK_DEP1 ? 3u : 15u;
+    return (u < U ? cat_index(u, U, m) : m - 1u) + 1u;
 }
 
 // Walk the queued (group, shot) events e = lane, lane+32, ... < n; event =
-// group - g0 above bit 5 + TB, tile word t, lane.
+// group - g0 above bit 5 + TB, tile word t, lane.  The loops have the same
+// trip counts in every lane (lanes without an event, or past a group's last
+// channel, are masked) and the warp reconverges after each block of four
+// channel words: a lane leaving a divergent apply loop early would
+// otherwise run ahead into the next block's Philox rounds, and the warp
+// would execute them in several partial passes.
 template <int TW, typename Apply>
 __device__ __forceinline__ void grouped_drain(const uint32_t *q, uint32_t n, const FusedParams &p, const Keys &K,
                                               uint32_t g0, uint64_t shot_base, int lane, const Apply &apply)
@@ -69,35 +75,55 @@ __device__ __forceinline__ void grouped_drain(const uint32_t *q, uint32_t n, con
     __syncwarp();
     constexpr int TB = event_tbits(TW);
     const uint32_t k1 = (uint32_t)(p.seed >> 32);
-    for (uint32_t e = lane; e < n; e += 32) {
-        const uint32_t ev = q[e];
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t e = base + (uint32_t)lane;
+        const bool live = e < n;
+        const uint32_t ev = live ? q[e] : 0u;
         const uint32_t g = g0 + (ev >> (5 + TB));
         const int t = (ev >> 5) & ((1u << TB) - 1u);
         const uint32_t ln = ev & 31u;
         const ShotConst s = shot_const(shot_base + 32u * (uint32_t)t + ln, k1 ^ S2_TAG_CHANNEL);
         const uint32_t first = g * S2_GROUP;
-        const uint32_t nch = min(S2_GROUP, p.n_fault - first);
+        const uint32_t nch = live ? min(S2_GROUP, p.n_fault - first) : 0u;
         bool searching = true;
-        for (uint32_t j = 0; 4 * j < nch; j++) {
+        // the walk's first two fired channels wait in registers (first
+        // symbol, symbol bits) and are applied after it, by every lane at
+        // the same point; a third or later one (rare) is applied at once
+        uint32_t s_a = 0, v_a = 0, s_b = 0, v_b = 0;
+        auto apply_bits = [&](uint32_t sym, uint32_t val) {
+            while (val) {
+                const int b = __ffs(val) - 1;
+                val &= val - 1;
+                apply(sym + (uint32_t)b, t, 1u << ln);
+            }
+        };
+#pragma unroll 1
+        for (uint32_t j = 0; j < S2_GROUP / 4; j++) {
+            uint4 c[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                c[i] = 4 * j + (uint32_t)i < nch ? p.s2Ch[first + 4 * j + (uint32_t)i] : make_uint4(0u, 0u, 0u, 0u);
             uint32_t r[4];
             philox_tagged(s, 8u * g + j, K, r[0], r[1], r[2], r[3]);
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                if (4 * j + (uint32_t)i >= nch) break;
-                const uint4 c = p.s2Ch[first + 4 * j + (uint32_t)i];
                 const uint32_t u = r[i];
-                const uint32_t U = searching ? c.x : c.y;
-                const bool fired = searching ? ((c.w & S2_LAST) != 0u || u < U) : u < U;
-                if (!fired) continue;
-                searching = false;
-                uint32_t val = grouped_outcome(c.w & 3u, u, U);
-                while (val) {
-                    const int b = __ffs(val) - 1;
-                    val &= val - 1;
-                    apply(c.z + (uint32_t)b, t, 1u << ln);
+                const uint32_t U = searching ? c[i].x : c[i].y;
+                const bool valid = 4 * j + (uint32_t)i < nch;
+                const bool fired = valid && (searching ? ((c[i].w & S2_LAST) != 0u || u < U) : u < U);
+                if (fired) {
+                    searching = false;
+                    const uint32_t val = grouped_outcome(c[i].w & 3u, u, U);
+                    if (!v_a) { s_a = c[i].z; v_a = val; }
+                    else if (!v_b) { s_b = c[i].z; v_b = val; }
+                    else apply_bits(c[i].z, val);
                 }
             }
+            __syncwarp();
         }
+        apply_bits(s_a, v_a);
+        apply_bits(s_b, v_b);
+        __syncwarp();
     }
     __syncwarp();
 }
