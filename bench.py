@@ -36,9 +36,10 @@ UNIT = "shots/s"
 # the first timed 1,000,000-shot launch. The figure belongs to the kernel
 # source it was taken on; when the hash of that source differs, it is dropped
 # (reported as null) until a new capture replaces it.
-FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 1_020_000 + 300_970_000,
-                 "sources_sha256": "a8808867e4aabe5c74ebf48eec83518928132dec1dcf33584241907bd620ebb9"}
-FUSED_SOURCES = ("paper_2311_03906_gb300/csrc/sp_fused.cu", "paper_2311_03906_gb300/csrc/sp_internal.h")
+FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 698_112 + 301_691_392,
+                 "sources_sha256": "06c3bedc9a57393255bde5b4008d841ad1624e4e6a6bf2ced220ffc166e04d07"}
+FUSED_SOURCES = ("paper_2311_03906_gb300/csrc/sp_fused.cu", "paper_2311_03906_gb300/csrc/sp_fused_dev.cuh",
+                 "paper_2311_03906_gb300/csrc/sp_internal.h")
 
 
 def _sources_sha256(paths=FUSED_SOURCES):

@@ -322,6 +322,8 @@ SP_API sp_status sp_set_chunk(sp_program *prog, uint64_t chunk_shots);
  *      groups of 32 channels; stream 1 stays preferable where channels fire
  *      often.  Runs on the fused path only (the path is set to it);
  *      sp_sample_static and the staged and dense paths draw stream 1.
+ * Switching streams re-runs the build's launch-shape autotuner for the new
+ * stream (cached per circuit shape), replacing a sp_set_fused_config choice.
  * Errors: INVALID_ARG (stream not 1 or 2; stream 2 without the fused path),
  * OOM, CUDA.
  */
@@ -355,6 +357,7 @@ enum {
     SP_KERNEL_EMIT = 2,      /* bit-sliced -> shot-major record transpose */
     SP_KERNEL_FUSED = 3,     /* fused draw + product */
     SP_KERNEL_TENSOR = 4,    /* tensor-core (tcgen05) product */
+    SP_KERNEL_CONSTS = 5,    /* per-launch channel-block constants of the fused draw */
     SP_KERNEL_CLASSES = 8
 };
 

@@ -31,7 +31,7 @@ EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_stat
            "sp_set_chunk", "sp_set_stream", "sp_device_status", "sp_set_wait_limit",
            "sp_profile_enable", "sp_profile_read", "sp_batch_plans", "sp_debug_fail_alloc",
            "sp_debug_live_allocs", "sp_free", "sp_last_error")
-KERNEL_CLASSES = ("draw", "product", "emit", "fused", "tensor")
+KERNEL_CLASSES = ("draw", "product", "emit", "fused", "tensor", "consts")
 
 
 class SymPhaseError(RuntimeError):

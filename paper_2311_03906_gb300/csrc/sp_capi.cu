@@ -66,7 +66,7 @@ static void release(sp_program *P)
     if (cur != P->device) cudaSetDevice(P->device);
     void *bufs[] = {P->d_A, P->d_chT, P->d_chKind, P->d_chP, P->d_chSym0, P->d_rowOff, P->d_idx,
                     P->d_parent, P->d_cflag, P->d_A64, P->d_const, P->d_inc, P->d_incT, P->d_kappa,
-                    P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta, P->d_blkFilt,
+                    P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta, P->d_blkFilt, P->d_blkConst,
                     P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs,
                     P->d_colOff, P->d_colRows, P->d_AT, P->d_tc_coef[0], P->d_tc_coef[1], P->d_tc_coef[2],
                     P->d_tc_status, P->d_s2Ch, P->d_s2G, P->d_s2Rand};
@@ -394,8 +394,17 @@ sp_status sp_set_stream(sp_program *P, int32_t stream)
         if (st != SP_OK) return st;
         P->path = SP_PATH_FUSED;
     }
+    const int old = P->stream;
     P->stream = stream;
     reconfigured(P);
+    // the launch shape is tuned per stream (cached per circuit shape)
+    if (stream != old && P->fused_tw) {
+        const sp_status st = autotune(P, nullptr);
+        if (st != SP_OK) {
+            P->stream = old;
+            return st;
+        }
+    }
     return SP_OK;
 }
 

@@ -225,10 +225,12 @@ __device__ __forceinline__ void drain_fired(const uint32_t *q, uint32_t n, const
 // The queue is drained by all 32 lanes together when it fills and at the end.
 // UHI: every shot of the tile has the same high counter word c1u, so round
 // 2's M0 product is the same in all lanes and tile words.
-template <int TW, bool UHI, typename Apply>
+// BC: the launch supplies blkConst (every shot shares the high word c1u).
+template <int TW, bool UHI, bool BC, typename Apply>
 __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
                                                 const uint32_t *__restrict__ blkSym0,
-                                                const uint32_t *__restrict__ blkFilt, uint32_t b0, uint32_t b1,
+                                                const uint32_t *__restrict__ blkFilt,
+                                                const uint4 *__restrict__ blkConst, uint32_t b0, uint32_t b1,
                                                 const Shots<TW> sc, uint64_t shot_base, const Keys &K, uint32_t k1,
                                                 int lane, uint32_t *q, const Apply &apply)
 {
@@ -257,6 +259,17 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
                 if ((uint32_t)lane < cnt) q[lane] = rest;
                 __syncwarp();
             }
+        }
+    };
+    // rare block g+kk from its launch constants: one uniform load
+    auto step_rare_bc = [&](uint32_t g, uint32_t kk, uint32_t (&word)[TW]) {
+        const uint4 bc = blkConst[g + kk];
+        const uint64_t p = ((uint64_t)bc.z << 32) | bc.y;
+#pragma unroll
+        for (int t = 0; t < TW; t++) {
+            uint32_t r0, r1, r2, r3;
+            philox_from_p(sc.s[t], p, bc.x, K, r0, r1, r2, r3);
+            if (min(min(r0, r1), min(r2, r3)) < bc.w) word[t] |= 1u << kk;
         }
     };
     // rare block g+kk: bit kk of word[t] = the least of the shot's four
@@ -300,7 +313,10 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
 #pragma unroll
         for (int t = 0; t < TW; t++) word[t] = 0u;
         if (!__any_sync(FM, filt == FREQUENT)) {
-            if (nb == DRAW_GROUP) {
+            if (BC && nb == DRAW_GROUP) {
+#pragma unroll
+                for (uint32_t kk = 0; kk < DRAW_GROUP; kk++) step_rare_bc(g, kk, word);
+            } else if (nb == DRAW_GROUP) {
 #pragma unroll
                 for (uint32_t kk = 0; kk < DRAW_GROUP; kk++)
                     step_rare(kk, ug + (uint64_t)kk * PH_M1, __shfl_sync(FM, filt, kk), word);
@@ -355,14 +371,32 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
 template <int TW, typename Apply>
 __device__ __forceinline__ void draw_scatter(const uint4 *__restrict__ blkT, const uint32_t *__restrict__ blkMeta,
                                              const uint32_t *__restrict__ blkSym0, const uint32_t *__restrict__ blkFilt,
-                                             uint32_t b0, uint32_t b1, const Shots<TW> sc, uint64_t shot_base,
-                                             const Keys &K, uint32_t k1, int lane, uint32_t *q, const Apply &apply)
+                                             const uint4 *__restrict__ blkConst, uint32_t b0, uint32_t b1,
+                                             const Shots<TW> sc, uint64_t shot_base, const Keys &K, uint32_t k1,
+                                             int lane, uint32_t *q, const Apply &apply)
 {
-    // a tile straddles a multiple of 2^32 shots only if shot0 is unaligned
-    if ((shot_base >> 32) == ((shot_base + 32u * TW - 1u) >> 32))
-        draw_group_impl<TW, true>(blkT, blkMeta, blkSym0, blkFilt, b0, b1, sc, shot_base, K, k1, lane, q, apply);
+    // a tile straddles a multiple of 2^32 shots only if shot0 is unaligned;
+    // blkConst is given only when no tile of the launch does
+    if (blkConst)
+        draw_group_impl<TW, true, true>(blkT, blkMeta, blkSym0, blkFilt, blkConst, b0, b1, sc, shot_base, K, k1, lane,
+                                        q, apply);
+    else if ((shot_base >> 32) == ((shot_base + 32u * TW - 1u) >> 32))
+        draw_group_impl<TW, true, false>(blkT, blkMeta, blkSym0, blkFilt, blkConst, b0, b1, sc, shot_base, K, k1,
+                                         lane, q, apply);
     else
-        draw_group_impl<TW, false>(blkT, blkMeta, blkSym0, blkFilt, b0, b1, sc, shot_base, K, k1, lane, q, apply);
+        draw_group_impl<TW, false, false>(blkT, blkMeta, blkSym0, blkFilt, blkConst, b0, b1, sc, shot_base, K, k1,
+                                          lane, q, apply);
+}
+
+// The launch constants of every channel block (see FusedParams::blkConst).
+__global__ void __launch_bounds__(256) k_block_consts(int64_t n_blk, uint32_t k0, uint32_t c1u,
+                                                      const uint32_t *__restrict__ blkFilt, uint4 *__restrict__ out)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_blk) return;
+    const uint64_t ub = (uint64_t)PH_M1 * (uint32_t)b;
+    const uint64_t p = (uint64_t)PH_M0 * ((uint32_t)(ub >> 32) ^ c1u ^ k0);
+    out[b] = make_uint4((uint32_t)ub, (uint32_t)p, (uint32_t)(p >> 32), blkFilt[b]);
 }
 
 // The per-channel Philox stream (the default draw): warp w of the CTA owns
@@ -375,8 +409,8 @@ struct DrawPerChannel {
     {
         const uint32_t b0 = (uint32_t)((uint64_t)warp * (uint64_t)p.n_blk / (uint64_t)nwarps);
         const uint32_t b1 = (uint32_t)((uint64_t)(warp + 1) * (uint64_t)p.n_blk / (uint64_t)nwarps);
-        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, p.blkFilt, b0, b1, sc, shot_base, K, (uint32_t)(p.seed >> 32),
-                         lane, q, apply);
+        draw_scatter<TW>(p.blkT, p.blkMeta, p.blkSym0, p.blkFilt, p.blkConst, b0, b1, sc, shot_base, K,
+                         (uint32_t)(p.seed >> 32), lane, q, apply);
     }
 };
 
@@ -386,8 +420,9 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fus
     extern __shared__ __align__(16) uint32_t sm[];
     const uint64_t per_tile = 32u * TW;
     const uint64_t ntiles = (p.nshots + per_tile - 1) / per_tile;
+    const FusedTables tab = stage_tables(p, sm);
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        fused_tile<TW, fused_threads(TW, U), DrawPerChannel>(p, p.keys, tile, sm);
+        fused_tile<TW, fused_threads(TW, U), DrawPerChannel>(p, p.keys, tab, tile, sm);
 }
 
 // Batched form: many programs in one persistent launch per launch shape.
@@ -418,7 +453,8 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U))
         // parameters in global memory: the round keys are computed into registers
         const uint64_t seed = progs[lo].seed;
         const Keys K = make_keys((uint32_t)seed, (uint32_t)(seed >> 32));
-        fused_tile<TW, fused_threads(TW, U), DrawPerChannel>(progs[lo], K, item - (lo ? tileEnd[lo - 1] : 0ull), sm);
+        fused_tile<TW, fused_threads(TW, U), DrawPerChannel>(progs[lo], K, global_tables(progs[lo]),
+                                                             item - (lo ? tileEnd[lo - 1] : 0ull), sm);
     }
 }
 
@@ -475,7 +511,8 @@ __global__ void __launch_bounds__(256, 4) k_draw_dense(const uint4 *__restrict__
     uint32_t *base = Bd + (size_t)(2 * gw) * (size_t)bpitch * 32u;
     const bool has2 = 2 * gw + 1 < ngroups;
     const Keys K = make_keys(k0, k1);
-    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, 0u, (uint32_t)n_blk, sc, shot_base, K, k1, lane, q + warp * FUSED_QCAP,
+    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, nullptr, 0u, (uint32_t)n_blk, sc, shot_base, K, k1, lane,
+                    q + warp * FUSED_QCAP,
                     [=](uint32_t sym, int t, uint32_t word) {
                         if (t == 1 && !has2) return;
                         const uint32_t e = sym + 1u;
@@ -593,6 +630,11 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     if ((st = upload(&P->d_blkT, bT, s)) || (st = upload(&P->d_blkMeta, bMeta, s)) || (st = upload(&P->d_blkSym0, bSym0, s)) ||
         (st = upload(&P->d_blkFilt, bFilt, s)))
         return st;
+    if (dev_alloc((void **)&P->d_blkConst, (size_t)std::max<int64_t>(nb, 1) * sizeof(uint4)) != cudaSuccess) {
+        cudaGetLastError();
+        P->d_blkConst = nullptr;
+        return set_error(SP_ERR_OOM, "cudaMalloc of the block constants failed");
+    }
 
     // ---- product program: the measurement rows' own parts by symbol -------
     const int64_t R = P->n_rows;
@@ -648,6 +690,7 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
         for (int64_t j = 0; j < M; j++)   // increasing j: parents before children
             if (parent[j] >= 0) bItem[pos[ownerT[root[j]]]++] = make_uint2((uint32_t)j, (uint32_t)parent[j]);
     }
+    P->fused_items = (int64_t)bItem.size();
     if ((st = upload(&P->d_fCflag, cf, s)) || (st = upload(&P->d_fChain, bItem, s)) || (st = upload(&P->d_fBOff, bOff, s)) ||
         (st = upload(&P->d_fCOff, P->h_xoff, s)) || (st = upload(&P->d_fCRefs, P->h_xrefs, s)))
         return st;
@@ -670,19 +713,33 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
     return SP_OK;
 }
 
-// Shared-memory words of a tile of 32*tw shots: the records R_s (n_rows x tw
-// words), then a region used by the warps' event queues in phase 1 and by
-// the emit stage in phase 3.
 static uint32_t aux_offset(const sp_program *P, int tw) { return (uint32_t)((P->n_rows * tw + 3) / 4 * 4); }
 
-size_t fused_words(const sp_program *P, int tw)
+// Words of the phase-2 tables when staged in shared memory (a multiple of 4).
+static size_t table_words(const sp_program *P)
 {
-    int64_t max_words32 = 0;
-    for (int64_t n : {P->n_meas, P->n_det, P->n_obs}) max_words32 = std::max<int64_t>(max_words32, 2 * ((n + 63) / 64));
-    const int64_t stage_words = 32 * tw * (max_words32 + 1);
+    const size_t w = 2 * (size_t)P->fused_items + (FUSED_THREADS + 1) + (size_t)(P->n_det + P->n_obs + 1) +
+                     (size_t)P->h_xrefs.size();
+    return (w + 3) / 4 * 4;
+}
+
+// Shared-memory words of a tile of 32*tw shots: the records R_s (n_rows x tw
+// words), then a region used by the warps' event queues in phase 1 and by
+// the emit stage in phase 3 (one record kind at a time, or all three side
+// by side when emit_once).
+size_t fused_words(const sp_program *P, int tw, bool emit_once)
+{
+    int64_t max_words = 0, sum_words = 0;
+    for (int64_t n : {P->n_meas, P->n_det, P->n_obs}) {
+        max_words = std::max<int64_t>(max_words, 2 * ((n + 63) / 64) + 1);
+        sum_words += 2 * ((n + 63) / 64) + 1;
+    }
+    const int64_t stage_words = 32 * tw * (emit_once ? sum_words : max_words);
     const int64_t queue_words = (FUSED_THREADS / 32) * (int64_t)FUSED_QCAP;
     return (size_t)aux_offset(P, tw) + (size_t)std::max(stage_words, queue_words);
 }
+
+size_t fused_words(const sp_program *P, int tw) { return fused_words(P, tw, false); }
 
 typedef void (*FusedFn)(FusedParams);
 
@@ -710,27 +767,50 @@ sp_status fused_select(sp_program *P, int tw, int unroll)
     SP_CUDA(max_dynamic_smem(fn));
     int occ = 0;
     SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, bytes));
+    // the one-pass emit and the phase-2 tables in shared memory, each where
+    // it keeps the CTAs per SM of the plain layout (both, else the emit, else
+    // the tables)
+    struct Opt { bool once, tab; };
+    Opt pick{false, false};
+    size_t pick_bytes = bytes;
+    int pick_occ = occ;
+    for (Opt o : {Opt{true, true}, Opt{true, false}, Opt{false, true}}) {
+        const size_t b = (fused_words(P, tw, o.once) + (o.tab ? table_words(P) : 0)) * 4;
+        if (b > (size_t)P->smem_max) continue;
+        int oc = 0;
+        SP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, fn, threads, b));
+        if (oc >= occ && oc > 0) {
+            pick = o;
+            pick_bytes = b;
+            pick_occ = oc;
+            break;
+        }
+    }
     P->fused_tw = tw;
     P->fused_unroll = unroll;
     P->fused_threads = threads;
-    P->fused_smem = bytes;
+    P->fused_smem_base = bytes;
+    P->fused_smem = pick_bytes;
+    P->fused_emit_once = pick.once;
+    P->fused_tab_off = pick.tab ? (uint32_t)fused_words(P, tw, pick.once) : 0u;
     P->fused_aux_off = aux_offset(P, tw);
-    P->fused_ctas_per_sm = std::max(occ, 1);
+    P->fused_ctas_per_sm = std::max(pick_occ, 1);
     return SP_OK;
 }
 
 // Autotuner: time the fused variants that fit -- 64-shot tiles at two CTAs
 // per SM, 32-shot tiles, 64-shot tiles at one CTA per SM with more registers,
 // 128-shot tiles at 256 threads x two CTAs or 512 threads x one CTA per SM --
-// on a few tiles per SM and keep the fastest.  The choice is cached per
-// circuit shape for the process.
+// on a few tiles per SM, drawing with the program's current fault-draw
+// stream, and keep the fastest.  The choice is cached per circuit shape and
+// stream for the process.
 sp_status autotune(sp_program *P, cudaStream_t s)
 {
     if (!P->fused_tw) return SP_OK;
-    typedef std::tuple<int, int64_t, int64_t, int64_t, int64_t, int64_t> Key;
+    typedef std::tuple<int, int64_t, int64_t, int64_t, int64_t, int64_t, int> Key;
     static std::mutex mu;
     static std::map<Key, std::pair<int, int>> cache;
-    const Key key{P->device, P->n_sym, P->n_rows, P->n_blk, P->nnz_delta, P->n_meas};
+    const Key key{P->device, P->n_sym, P->n_rows, P->n_blk, P->nnz_delta, P->n_meas, P->stream};
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
@@ -832,6 +912,10 @@ FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint64_t sh
     }
     fp.s2Ch = P->d_s2Ch; fp.s2G = P->d_s2G; fp.s2Rand = P->d_s2Rand;
     fp.n_fault = (uint32_t)P->s2_nfault; fp.n_grp = (uint32_t)P->s2_ngrp; fp.n_rnd = (uint32_t)P->s2_nrnd;
+    fp.tab_off_words = tw == P->fused_tw ? P->fused_tab_off : 0u;
+    fp.emit_once = tw == P->fused_tw && P->fused_emit_once ? 1u : 0u;
+    fp.n_items = (uint32_t)P->fused_items;
+    fp.n_refs = (uint32_t)P->h_xrefs.size();
     return fp;
 }
 
@@ -841,7 +925,16 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
     if (nshots == 0) return SP_OK;
     if (!P->fused_tw) return set_error(SP_ERR_INVALID_ARG, "fused path unavailable for this program");
     if (P->stream == 2) return grouped_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
-    const FusedParams fp = fused_params(P, P->fused_tw, seed, shot0, nshots, d_meas, d_det, d_obs);
+    FusedParams fp = fused_params(P, P->fused_tw, seed, shot0, nshots, d_meas, d_det, d_obs);
+    // one launch's block constants when its shots share a high word
+    if (P->d_blkConst && (shot0 >> 32) == ((shot0 + nshots - 1) >> 32)) {
+        ProfScope pc(P, SP_KERNEL_CONSTS, s);
+        k_block_consts<<<(unsigned)ceil_div(P->n_blk, 256), 256, 0, s>>>(P->n_blk, (uint32_t)seed,
+                                                                        (uint32_t)(shot0 >> 32), P->d_blkFilt,
+                                                                        P->d_blkConst);
+        SP_CUDA(cudaGetLastError());
+        fp.blkConst = P->d_blkConst;
+    }
     const uint64_t per_tile = 32u * (uint64_t)P->fused_tw;
     const uint64_t ntiles = (nshots + per_tile - 1) / per_tile;
     const uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)P->num_sms * (uint64_t)P->fused_ctas_per_sm);
@@ -935,6 +1028,8 @@ void fill_params(const BatchPlan &plan, sp_program *const *progs, const uint64_t
             const uint32_t i = g.members[k];
             out[g.param0 + k] = fused_params(progs[i], g.tw, seeds[i], 0, nshots[i], d_meas ? d_meas[i] : nullptr,
                                              d_det ? d_det[i] : nullptr, d_obs ? d_obs[i] : nullptr);
+            out[g.param0 + k].tab_off_words = 0;   // the batch reads phase-2 tables from global memory
+            out[g.param0 + k].emit_once = 0;       // and emits one record kind per pass
         }
 }
 
@@ -997,7 +1092,7 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
                 g.unroll = P->fused_unroll;
                 g.threads = P->fused_threads;
                 g.ctas = P->fused_ctas_per_sm;
-                g.smem = std::max(g.smem, P->fused_smem);
+                g.smem = std::max(g.smem, P->fused_smem_base);
                 g.members.push_back(i);
             } else {
                 np->others.push_back(i);

@@ -175,7 +175,52 @@ struct FusedParams {
     const uint4 *s2G;          // per 4 groups of 32 such channels: the groups' thresholds
     const uint32_t *s2Rand;    // per random-outcome channel: its symbol - 1
     uint32_t n_fault, n_grp, n_rnd;
+    // phase-2 tables staged in shared memory at this word offset (0 = read
+    // from global memory): bItem, bOff, cOff, cRefs, with these counts
+    uint32_t tab_off_words, n_items, n_refs;
+    uint32_t emit_once;        // 1: phase 3 stages all three record kinds before one copy-out
+    // per channel block, for this launch's seed and shot high word (NULL when
+    // the launch's shots straddle a multiple of 2^32): {lo(M1 b), lo(p),
+    // hi(p), blkFilt[b]} with p = M0 (hi(M1 b) ^ shot hi ^ k0), round 2's
+    // product shared by every shot of the launch
+    const uint4 *blkConst;
 };
+
+// Where phase 2 reads its tables: shared memory when the launch staged them
+// (once per persistent CTA), else global memory.
+struct FusedTables {
+    const uint2 *bItem;
+    const uint32_t *bOff, *cOff, *cRefs;
+};
+
+__device__ __forceinline__ FusedTables global_tables(const FusedParams &p)
+{
+    FusedTables t;
+    t.bItem = p.bItem; t.bOff = p.bOff; t.cOff = p.cOff; t.cRefs = p.cRefs;
+    return t;
+}
+
+// Copy the phase-2 tables into shared memory (the whole CTA, then a barrier)
+// if the launch asked for it.  Layout from word tab_off_words on: bItem
+// (2 words each), bOff (FUSED_THREADS + 1), cOff (targets + 1), cRefs.
+__device__ __forceinline__ FusedTables stage_tables(const FusedParams &p, uint32_t *sm)
+{
+    if (!p.tab_off_words) return global_tables(p);
+    uint32_t *base = sm + p.tab_off_words;
+    uint2 *bi = reinterpret_cast<uint2 *>(base);
+    uint32_t *bo = base + 2 * p.n_items;
+    uint32_t *co = bo + FUSED_THREADS + 1;
+    const uint32_t ntgt = (uint32_t)(p.n_det + p.n_obs);
+    uint32_t *cr = co + ntgt + 1;
+    for (uint32_t i = threadIdx.x; i < p.n_items; i += blockDim.x) bi[i] = p.bItem[i];
+    for (uint32_t i = threadIdx.x; i <= (uint32_t)FUSED_THREADS; i += blockDim.x) bo[i] = p.bOff[i];
+    for (uint32_t i = threadIdx.x; i <= ntgt; i += blockDim.x) co[i] = p.cOff[i];
+    for (uint32_t i = threadIdx.x; i < p.n_refs; i += blockDim.x) cr[i] = p.cRefs[i];
+    __syncthreads();
+    FusedTables t;
+    t.bItem = bi; t.bOff = bo; t.cOff = co; t.cRefs = cr;
+    return t;
+}
 
 // The parameters of one fused launch (host side, sp_fused.cu).
 FusedParams fused_params(const sp_program *P, int tw, uint64_t seed, uint64_t shot0, uint64_t nshots,
@@ -215,7 +260,8 @@ __device__ __forceinline__ uint4 xorw(uint4 a, uint4 b)
 // nwarps, lane, queue, apply), which hands every fired (symbol, tile word,
 // shot bits) to apply.
 template <int TW, int NT, typename Draw>
-__device__ __forceinline__ void fused_tile(const FusedParams &p, const Keys &K, uint64_t tile, uint32_t *sm)
+__device__ __forceinline__ void fused_tile(const FusedParams &p, const Keys &K, const FusedTables &tab, uint64_t tile,
+                                           uint32_t *sm)
 {
     typedef TileWord<TW> TWd;
     typedef typename TWd::T W;
@@ -241,9 +287,9 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, const Keys &K, 
     // (trees are scheduled over FUSED_THREADS lists; a smaller CTA walks
     // several lists, each independent of the others)
     for (int th = tid; th < FUSED_THREADS; th += NT) {
-        const uint32_t e = p.bOff[th + 1];
-        for (uint32_t i = p.bOff[th]; i < e; i++) {
-            const uint2 rp = p.bItem[i];
+        const uint32_t e = tab.bOff[th + 1];
+        for (uint32_t i = tab.bOff[th]; i < e; i++) {
+            const uint2 rp = tab.bItem[i];
             Rs[rp.x] = xorw(Rs[rp.x], Rs[rp.y]);
         }
     }
@@ -251,37 +297,65 @@ __device__ __forceinline__ void fused_tile(const FusedParams &p, const Keys &K, 
     // ---- phase 2C: detectors and observables from measurement records ------
     for (int64_t t = tid; t < p.n_det + p.n_obs; t += blockDim.x) {
         W acc = TWd::zero();
-        for (uint32_t k = p.cOff[t]; k < p.cOff[t + 1]; k++) acc = xorw(acc, Rs[p.cRefs[k]]);
+        for (uint32_t k = tab.cOff[t]; k < tab.cOff[t + 1]; k++) acc = xorw(acc, Rs[tab.cRefs[k]]);
         Rs[p.n_meas + t] = acc;
     }
     __syncthreads();
     // ---- phase 3: emit shot-major records (stage aliases the queues) -------
+    // Record kind sg is transposed into the stage, then copied out as
+    // contiguous per-shot segments; with emit_once all three kinds share one
+    // pass (their stages side by side, one barrier pair), else one pass each.
     uint32_t *stage = aux;
+    int soff[3];
+    {
+        int acc = 0;
+#pragma unroll
+        for (int sg = 0; sg < 3; sg++) {
+            soff[sg] = p.emit_once ? acc : 0;
+            acc += 32 * TW * (int)(2 * ((p.nrow[sg] + 63) / 64) + 1);
+        }
+    }
 #pragma unroll
     for (int sg = 0; sg < 3; sg++) {
-        uint64_t *dst = p.out[sg];
-        const int64_t n = p.nrow[sg];
-        if (!dst || n == 0) continue;
-        const int64_t row0 = p.rows0[sg];
-        const int words32 = (int)(2 * ((n + 63) / 64));
-        const int stride = words32 + 1;
-        for (int g = warp; g < words32; g += nwarps) {
-            const int64_t r = 32 * (int64_t)g + lane;
+        {
+            uint64_t *dst = p.out[sg];
+            const int64_t n = p.nrow[sg];
+            if (dst && n) {
+                const int64_t row0 = p.rows0[sg];
+                const int words32 = (int)(2 * ((n + 63) / 64));
+                const int stride = words32 + 1;
+                uint32_t *st = stage + soff[sg];
+                for (int g = warp; g < words32; g += nwarps) {
+                    const int64_t r = 32 * (int64_t)g + lane;
 #pragma unroll
-            for (int t = 0; t < TW; t++) {
-                const uint32_t x = r < n ? TWd::get(Rs[row0 + r], t) : 0u;
-                stage[(32 * t + lane) * stride + g] = __any_sync(FM, x != 0u) ? transpose32(x, lane) : 0u;
+                    for (int t = 0; t < TW; t++) {
+                        const uint32_t x = r < n ? TWd::get(Rs[row0 + r], t) : 0u;
+                        st[(32 * t + lane) * stride + g] = __any_sync(FM, x != 0u) ? transpose32(x, lane) : 0u;
+                    }
+                }
             }
         }
-        __syncthreads();
-        uint32_t *o32 = reinterpret_cast<uint32_t *>(dst);
-        for (int sh = warp; sh < 32 * TW; sh += nwarps) {
-            const uint64_t shot = trel + (uint64_t)sh;
-            if (shot >= p.nshots) continue;
-            uint32_t *o = o32 + shot * (uint64_t)words32;
-            for (int g = lane; g < words32; g += 32) o[g] = stage[sh * stride + g];
+        if (!p.emit_once || sg == 2) {
+            __syncthreads();
+#pragma unroll
+            for (int sc2 = 0; sc2 < 3; sc2++) {
+                if (p.emit_once ? sc2 > sg : sc2 != sg) continue;
+                uint64_t *dst = p.out[sc2];
+                const int64_t n = p.nrow[sc2];
+                if (!dst || n == 0) continue;
+                const int words32 = (int)(2 * ((n + 63) / 64));
+                const int stride = words32 + 1;
+                const uint32_t *st = stage + soff[sc2];
+                uint32_t *o32 = reinterpret_cast<uint32_t *>(dst);
+                for (int sh = warp; sh < 32 * TW; sh += nwarps) {
+                    const uint64_t shot = trel + (uint64_t)sh;
+                    if (shot >= p.nshots) continue;
+                    uint32_t *o = o32 + shot * (uint64_t)words32;
+                    for (int g = lane; g < words32; g += 32) o[g] = st[sh * stride + g];
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     // phase 3 may have been skipped (no outputs): keep the tile boundary
     __syncthreads();

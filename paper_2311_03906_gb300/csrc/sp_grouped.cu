@@ -210,8 +210,9 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U)) k_fus
     extern __shared__ __align__(16) uint32_t sm[];
     const uint64_t per_tile = 32u * TW;
     const uint64_t ntiles = (p.nshots + per_tile - 1) / per_tile;
+    const FusedTables tab = stage_tables(p, sm);
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        fused_tile<TW, fused_threads(TW, U), DrawGrouped>(p, p.keys, tile, sm);
+        fused_tile<TW, fused_threads(TW, U), DrawGrouped>(p, p.keys, tab, tile, sm);
 }
 
 namespace {

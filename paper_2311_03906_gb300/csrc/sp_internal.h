@@ -133,6 +133,7 @@ struct sp_program {
     uint32_t *d_blkMeta = nullptr;
     uint32_t *d_blkSym0 = nullptr;
     uint32_t *d_blkFilt = nullptr;  // per block: all-thresholds-large flag or the largest threshold
+    uint4 *d_blkConst = nullptr;    // per block: a launch's Philox constants (rewritten by every fused launch)
     // grouped draw (stream 2, sp_grouped.cu): built on the first sp_set_stream(prog, 2)
     int stream = 1;
     std::vector<double> h_fault_p;    // probability of each channel other than random outcomes, in order
@@ -154,7 +155,11 @@ struct sp_program {
     int fused_tw = 0;                 // shots per tile / 32 (0 = fused path off)
     int fused_unroll = 1;             // 2: the 64- or 128-shot variant with one CTA per SM
     int fused_threads = 512;          // threads per CTA of the selected variant
-    size_t fused_smem = 0;
+    size_t fused_smem = 0;            // dynamic shared memory of a launch (with the staged tables, if any)
+    size_t fused_smem_base = 0;       // the same without the staged phase-2 tables
+    uint32_t fused_tab_off = 0;       // word offset of the staged phase-2 tables (0 = not staged)
+    bool fused_emit_once = false;     // phase 3 stages all record kinds before one copy-out
+    int64_t fused_items = 0;          // parent-chain items (phase 2B)
     uint32_t fused_aux_off = 0;       // shared-memory words before the queue/stage region
     bool tuned = false;
     int autotune_launches = 0;        // fused-kernel launches made by the autotuner
