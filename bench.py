@@ -354,8 +354,11 @@ def _fault_probabilities(circuit):
 
 def _batched_vs_plain(args):
     """64 uneven circuits (rotated surface codes d = 3..15, p in {5e-4, 1e-3,
-    2e-3}, seeds 0..63), 1e5 shots each: one graph-captured batched enqueue
-    vs 64 separate sp_sample calls, identical records."""
+    2e-3}, seeds 0..63) at several shot counts per circuit: one
+    graph-captured batched enqueue vs 64 separate sp_sample calls, identical
+    records.  The batch pays off where a single circuit's launch does not
+    fill the GPU (few shots per circuit, small codes); at 1e5 shots each
+    the separate calls already run several waves per launch."""
     import torch
     import paper_2311_03906_gb300 as sp
     from workloads import batch_suite
@@ -364,47 +367,51 @@ def _batched_vs_plain(args):
     progs = [sp.build(c) for c, _ in suite]
     build_s = time.perf_counter() - t0
     seeds = [s for _, s in suite]
-    shots = [args.batch_shots] * len(progs)
-    outs = [p.alloc_outputs(n) for p, n in zip(progs, shots)]
-    outs_plain = [p.alloc_outputs(n) for p, n in zip(progs, shots)]
     stream = torch.cuda.current_stream()
+    sweep = []
+    for nshots in args.batch_shots:
+        shots = [nshots] * len(progs)
+        outs = [p.alloc_outputs(n) for p, n in zip(progs, shots)]
+        outs_plain = [p.alloc_outputs(n) for p, n in zip(progs, shots)]
 
-    def batched():
-        sp.sample_batch(progs, seeds, shots, outs=outs)
+        def batched():
+            sp.sample_batch(progs, seeds, shots, outs=outs)
 
-    def plain():
-        for p, s, n, o in zip(progs, seeds, shots, outs_plain):
-            p.sample(n, seed=s, out=o)
+        def plain():
+            for p, s, n, o in zip(progs, seeds, shots, outs_plain):
+                p.sample(n, seed=s, out=o)
 
-    res = {}
-    for name, fn in (("batched", batched), ("plain", plain)):
-        for _ in range(2):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        reps = 5
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        res[name] = {"ms": ms, "shots_per_s": sum(shots) / (ms / 1e3)}
-    res["speedup"] = res["plain"]["ms"] / res["batched"]["ms"]
-    res["identical"] = all(torch.equal(a, b) for oa, ob in zip(outs, outs_plain) for a, b in zip(oa, ob))
+        res = {"shots_per_circuit": nshots}
+        for name, fn in (("batched", batched), ("plain", plain)):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reps = 5
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[name] = {"ms": ms, "shots_per_s": sum(shots) / (ms / 1e3)}
+        res["speedup"] = res["plain"]["ms"] / res["batched"]["ms"]
+        res["identical"] = all(torch.equal(a, b) for oa, ob in zip(outs, outs_plain) for a, b in zip(oa, ob))
+        sweep.append(res)
+        del outs, outs_plain
     shapes = {}
     for p in progs:
         k = f"{p.info['fused_tile_shots']}-shot tiles, variant {p.info['fused_variant']}"
         shapes[k] = shapes.get(k, 0) + 1
-    res["config"] = {"workload": "64 rotated surface codes d=3+2*(i mod 7), p=(5e-4,1e-3,2e-3)[(i//7) mod 3], seed i",
-                     "shots_per_circuit": args.batch_shots, "build_s": build_s,
-                     "paths": {"fused": sum(p.info["path"] == 3 for p in progs),
-                               "staged": sum(p.info["path"] == 1 for p in progs)},
-                     "launch_shapes": shapes,
-                     "identical": "torch.equal of every record tensor, batched vs 64 separate sp_sample calls"}
+    config = {"workload": "64 rotated surface codes d=3+2*(i mod 7), p=(5e-4,1e-3,2e-3)[(i//7) mod 3], seed i",
+              "build_s": build_s,
+              "paths": {"fused": sum(p.info["path"] == 3 for p in progs),
+                        "staged": sum(p.info["path"] == 1 for p in progs)},
+              "launch_shapes": shapes,
+              "identical": "torch.equal of every record tensor, batched vs 64 separate sp_sample calls"}
     for p in progs:
         p.close()
-    return res
+    return {"sweep": sweep, "identical": all(r["identical"] for r in sweep), "config": config}
 
 
 def _dense_paths(args):
@@ -769,7 +776,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--batch-shots", type=int, default=100_000)
+    ap.add_argument("--batch-shots", type=int, nargs="*", default=[10_000, 100_000])
     ap.add_argument("--no-dense", action="store_true", help="skip the dense-row (mirror circuit) section")
     ap.add_argument("--dense-shots", type=int, default=262_144)
     ap.add_argument("--dense-p", type=float, nargs="*", default=[1e-3, 1e-2, 3e-2, 1e-1],

@@ -152,6 +152,44 @@ SP_API sp_status sp_build(const sp_circuit_desc *circuit, void *cuda_stream, sp_
 SP_API sp_status sp_info(const sp_program *prog, sp_info_t *out);
 
 /*
+ * sp_save -- write a built program to a host buffer, so that sp_load can
+ * restore it without repeating the traversal of Algorithm 1
+ * "Initialization".  The blob holds what that traversal produces: the
+ * channel table (Sec. 3.1 distributions: threshold, kind, probability and
+ * first symbol of each channel), the detector and observable definitions,
+ * and the coefficient rows of Eq. sampling in the sampler's parent-delta
+ * form (each row = an earlier row XOR its own symbols, plus its constant).
+ * Format: a 128-byte header (magic "SYMPHASE", version 1, byte-order mark,
+ * counts, payload size, FNV-1a-64 checksum of the payload), then the
+ * sections, each 8-byte aligned; little-endian.
+ *   buf   host buffer of cap bytes, or NULL to ask for the size only.
+ *   size  receives the blob's size in bytes (may be NULL when buf is set).
+ * Synchronous (copies the tables back from the program's device); the
+ * program is unchanged.  Errors: INVALID_ARG (NULL prog, buf and size both
+ * NULL, cap smaller than the blob), CUDA.
+ */
+SP_API sp_status sp_save(const sp_program *prog, void *buf, size_t cap, size_t *size);
+
+/*
+ * sp_load -- rebuild a program written by sp_save on the current device.
+ * Every field of the blob is checked on the host before any device call:
+ * magic, version, byte order, counts against the buffer size, checksum,
+ * the channel table (symbols 1..n in order, each threshold equal to
+ * floor(p * 2^32) of its probability, random outcomes at 1/2), detector
+ * references, parent distances (<= 512 rows back), symbol ranges and
+ * order.  Then the coefficient rows are rebuilt on the device and the
+ * sampler program, expectation tables, fused-kernel program and launch
+ * shapes are derived from them as sp_build does; the rebuilt sampler
+ * program is compared with the saved one.  Records sampled from the loaded
+ * program equal those of the saved program for every seed and shot.
+ *   buf, size    the blob (read only during the call).
+ *   cuda_stream  stream for the rebuild; sp_load synchronises it.
+ *   out          receives a program to release with sp_free.
+ * Errors: INVALID_ARG (a malformed or inconsistent blob), OOM, CUDA.
+ */
+SP_API sp_status sp_load(const void *buf, size_t size, void *cuda_stream, sp_program **out);
+
+/*
  * sp_sample -- Algorithm 1 "Sampling" (Eq. sampling) for shots
  * shot0 .. shot0+nshots-1: draw every symbol (Sec. 3.1 distributions,
  * Philox keyed by (seed, shot, channel)), then evaluate all forms.

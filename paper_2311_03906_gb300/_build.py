@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsymphase.so")
 SOURCES = ["sp_build.cu", "sp_sample.cu", "sp_expect.cu", "sp_capi.cu", "sp_static.cu", "sp_fused.cu",
-           "sp_grouped.cu", "sp_dense.cu"]
+           "sp_grouped.cu", "sp_dense.cu", "sp_serial.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

@@ -25,7 +25,7 @@ OPCODES = {"H": 0, "S": 1, "CX": 2, "X": 3, "Y": 4, "Z": 5, "M": 6, "MR": 7, "R"
 PATH_AUTO, PATH_SPARSE, PATH_DENSE, PATH_FUSED, PATH_TENSOR = 0, 1, 2, 3, 4
 
 # every entry point declared in include/symphase.h
-EXPORTS = ("sp_build", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",
+EXPORTS = ("sp_build", "sp_save", "sp_load", "sp_info", "sp_sample", "sp_sample_host", "sp_sample_static",
            "sp_sample_batch", "sp_expect", "sp_expect_sign",
            "sp_expect_grad", "sp_export_rows", "sp_export_channels", "sp_set_path", "sp_set_fused_config",
            "sp_set_chunk", "sp_set_stream", "sp_device_status", "sp_set_wait_limit",
@@ -78,6 +78,8 @@ def load() -> C.CDLL:
     lib = C.CDLL(path)
     vp, u64, u32, i32 = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int32
     lib.sp_build.argtypes = [C.POINTER(sp_circuit_desc), vp, C.POINTER(vp)]
+    lib.sp_save.argtypes = [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+    lib.sp_load.argtypes = [vp, C.c_size_t, vp, C.POINTER(vp)]
     lib.sp_info.argtypes = [vp, C.POINTER(sp_info_t)]
     lib.sp_sample.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
     lib.sp_sample_host.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp]
@@ -148,15 +150,19 @@ def _circuit_struct(circuit):
 class Program:
     """A circuit built by ``sp_build`` on the current CUDA device."""
 
-    def __init__(self, circuit, stream=None):
+    def __init__(self, circuit=None, stream=None, saved: Optional[bytes] = None):
         import torch  # noqa: F401  (CUDA context through torch)
         lib = load()
-        desc, keep = _circuit_struct(circuit)
         h = C.c_void_p()
-        _check(lib.sp_build(C.byref(desc), C.c_void_p(_stream_handle(stream)), C.byref(h)))
+        if saved is not None:
+            buf = bytes(saved)
+            _check(lib.sp_load(buf, len(buf), C.c_void_p(_stream_handle(stream)), C.byref(h)))
+        else:
+            desc, keep = _circuit_struct(circuit)
+            _check(lib.sp_build(C.byref(desc), C.c_void_p(_stream_handle(stream)), C.byref(h)))
+            del keep
         self._h = h
         self._lib = lib
-        del keep
         info = sp_info_t()
         _check(lib.sp_info(h, C.byref(info)))
         self.info = {f: (list(getattr(info, f)) if f == "path_probe_ms" else getattr(info, f))
@@ -170,6 +176,18 @@ class Program:
     @property
     def handle(self):
         return self._h
+
+    def save(self, path: Optional[str] = None) -> bytes:
+        """The program as sp_save's blob; also written to `path` if given."""
+        size = C.c_size_t(0)
+        _check(self._lib.sp_save(self._h, None, 0, C.byref(size)))
+        buf = C.create_string_buffer(size.value)
+        _check(self._lib.sp_save(self._h, buf, size.value, C.byref(size)))
+        data = buf.raw[:size.value]
+        if path is not None:
+            with open(path, "wb") as f:
+                f.write(data)
+        return data
 
     def close(self):
         if getattr(self, "_h", None):
@@ -314,6 +332,14 @@ class Program:
 
 def build(circuit, stream=None) -> Program:
     return Program(circuit, stream=stream)
+
+
+def load_program(saved, stream=None) -> Program:
+    """Restore a program from sp_save's blob (bytes) or a file holding it."""
+    if isinstance(saved, (str, os.PathLike)):
+        with open(saved, "rb") as f:
+            saved = f.read()
+    return Program(saved=saved, stream=stream)
 
 
 def sample_batch(progs: Sequence[Program], seeds: Sequence[int], shots: Sequence[int], outs=None,

@@ -32,7 +32,6 @@ namespace sp {
 
 constexpr int TRAV_THREADS = 1024;
 constexpr uint32_t FULL = 0xffffffffu;
-constexpr int PARENT_LOOKBACK = 512;
 constexpr int REPLAY_SPLIT_MIN_N = 256;   // qubits from which k_replay runs 8 warps per CTA
 
 __device__ __forceinline__ int gcount(uint32_t x1, uint32_t z1, uint32_t x2, uint32_t z2)
@@ -808,18 +807,6 @@ __global__ void k_xor_rows(uint32_t *A, int64_t apitch, const uint32_t *__restri
     }
 }
 
-__global__ void k_random_mask(const uint8_t *sym_random, uint32_t nsym, uint32_t *mask, int64_t apitch)
-{
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= apitch) return;
-    uint32_t m = 0;
-    for (int b = 0; b < 32; b++) {
-        const int64_t s = w * 32 + b;
-        if (s >= 1 && s <= (int64_t)nsym && sym_random[s]) m |= 1u << b;
-    }
-    mask[w] = m;
-}
-
 __global__ void k_check_random(const uint32_t *A, int64_t apitch, int64_t row0, int64_t nrows,
                                const uint32_t *mask, int *bad)
 {
@@ -975,6 +962,15 @@ __global__ void k_transpose_bits(const uint32_t *__restrict__ in, int64_t inPitc
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Threshold of a channel with probability p: a 32-bit draw u fires when
+// u < T, T = floor(p * 2^32) clamped to 2^32 - 1.
+uint32_t threshold_of(double p)
+{
+    if (!(p > 0.0)) return 0u;
+    const double t = floor(p * 4294967296.0);
+    return t >= 4294967295.0 ? 4294967295u : (uint32_t)t;
+}
+
 namespace {
 
 struct Flat {
@@ -987,13 +983,6 @@ struct Flat {
     int64_t nmeasfam = 0;
     int64_t nff = 0;         // feed-forward instructions
 };
-
-uint32_t threshold_of(double p)
-{
-    if (!(p > 0.0)) return 0u;
-    const double t = floor(p * 4294967296.0);
-    return t >= 4294967295.0 ? 4294967295u : (uint32_t)t;
-}
 
 sp_status flatten(const sp_circuit_desc *d, Flat &F)
 {
@@ -1177,8 +1166,6 @@ struct Temp {
 
 }  // namespace
 
-#define SP_TRY(x) do { sp_status _s = (x); if (_s != SP_OK) return _s; } while (0)
-
 sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_program *P)
 {
     const auto t0 = std::chrono::steady_clock::now();
@@ -1345,29 +1332,50 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
             SP_CUDA(cudaMemcpyAsync(d_xrefs, xrefs.data(), xrefs.size() * 4, cudaMemcpyHostToDevice, stream));
         k_xor_rows<<<(unsigned)ntgt, 128, 0, stream>>>(P->d_A, P->apitch, d_xoff, d_xrefs, ntgt, P->n_meas);
         SP_CUDA(cudaGetLastError());
-        // a detector or observable with a random-measurement symbol is rejected
-        uint32_t *d_mask; int *d_bad;
-        SP_TRY(tmp.alloc(&d_mask, (size_t)P->apitch));
-        SP_TRY(tmp.alloc(&d_bad, 1));
-        const int big = 0x7fffffff;
-        SP_CUDA(cudaMemcpyAsync(d_bad, &big, 4, cudaMemcpyHostToDevice, stream));
-        k_random_mask<<<(unsigned)ceil_div(P->apitch, 128), 128, 0, stream>>>(d_symrand, hc.nsym, d_mask, P->apitch);
-        k_check_random<<<(unsigned)ntgt, 128, 0, stream>>>(P->d_A, P->apitch, P->n_meas, ntgt, d_mask, d_bad);
-        SP_CUDA(cudaGetLastError());
-        int bad;
-        SP_CUDA(cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, stream));
-        SP_CUDA(cudaStreamSynchronize(stream));
-        if (bad != big) {
-            std::string what = bad < P->n_det ? "detector " + std::to_string(bad)
-                                              : "observable " + std::to_string(bad - P->n_det);
-            return set_error(SP_ERR_NONDETERMINISTIC_DETECTOR, what + " depends on a random measurement outcome");
-        }
     }
+    SP_TRY(finish_program(P, stream));
+    P->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return SP_OK;
+}
+
+// Everything the sampler and the expectations derive from the coefficient
+// rows (P->d_A) and the channel table: run after the traversal by
+// build_program and after the rows are restored by sp_load.
+sp_status finish_program(sp_program *P, cudaStream_t stream)
+{
+    Temp tmp;
+    const int64_t ntgt = P->n_det + P->n_obs;
     // number of random symbols
     {
         std::vector<uint8_t> hk((size_t)P->n_ch);
-        if (P->n_ch) SP_CUDA(cudaMemcpy(hk.data(), P->d_chKind, (size_t)P->n_ch, cudaMemcpyDeviceToHost));
+        std::vector<uint32_t> hs((size_t)P->n_ch);
+        if (P->n_ch) {
+            SP_CUDA(cudaMemcpy(hk.data(), P->d_chKind, (size_t)P->n_ch, cudaMemcpyDeviceToHost));
+            SP_CUDA(cudaMemcpy(hs.data(), P->d_chSym0, (size_t)P->n_ch * 4, cudaMemcpyDeviceToHost));
+        }
         P->n_rand = std::count(hk.begin(), hk.end(), (uint8_t)CK_RANDOM);
+        // a detector or observable with a random-measurement symbol is rejected
+        if (ntgt > 0 && P->n_rand > 0) {
+            std::vector<uint32_t> mask((size_t)P->apitch, 0u);
+            for (int64_t c = 0; c < P->n_ch; c++)
+                if (hk[c] == CK_RANDOM) mask[hs[c] >> 5] |= 1u << (hs[c] & 31);
+            uint32_t *d_mask; int *d_bad;
+            SP_TRY(tmp.alloc(&d_mask, (size_t)P->apitch));
+            SP_TRY(tmp.alloc(&d_bad, 1));
+            const int big = 0x7fffffff;
+            SP_CUDA(cudaMemcpyAsync(d_mask, mask.data(), (size_t)P->apitch * 4, cudaMemcpyHostToDevice, stream));
+            SP_CUDA(cudaMemcpyAsync(d_bad, &big, 4, cudaMemcpyHostToDevice, stream));
+            k_check_random<<<(unsigned)ntgt, 128, 0, stream>>>(P->d_A, P->apitch, P->n_meas, ntgt, d_mask, d_bad);
+            SP_CUDA(cudaGetLastError());
+            int bad;
+            SP_CUDA(cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, stream));
+            SP_CUDA(cudaStreamSynchronize(stream));
+            if (bad != big) {
+                std::string what = bad < P->n_det ? "detector " + std::to_string(bad)
+                                                  : "observable " + std::to_string(bad - P->n_det);
+                return set_error(SP_ERR_NONDETERMINISTIC_DETECTOR, what + " depends on a random measurement outcome");
+            }
+        }
         std::vector<float> kap((size_t)std::max<int64_t>(P->n_ch, 1), 0.f);
         for (int64_t c = 0; c < P->n_ch; c++)
             kap[c] = hk[c] == CK_DEP1 ? 2.0f / 3.0f : hk[c] == CK_DEP2 ? 8.0f / 15.0f : hk[c] == CK_BERN ? 1.0f : 0.0f;
@@ -1442,7 +1450,6 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
     SP_TRY(autotune(P, stream));
     P->chunk_shots = default_chunk(P);
     SP_TRY(choose_path(P, stream));
-    P->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return SP_OK;
 }
 

@@ -1,6 +1,7 @@
 // sp_capi.cu -- the extern "C" entry points declared in include/symphase.h.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -171,6 +172,41 @@ sp_status sp_build(const sp_circuit_desc *circuit, void *cuda_stream, sp_program
         release(P);
         return st;
     }
+    *out = P;
+    return SP_OK;
+}
+
+sp_status sp_save(const sp_program *P, void *buf, size_t cap, size_t *size)
+{
+    if (!P) return set_error(SP_ERR_INVALID_ARG, "prog is NULL");
+    if (!buf && !size) return set_error(SP_ERR_INVALID_ARG, "buf and size are both NULL");
+    int cur = -1;
+    if (buf) {
+        SP_CUDA(cudaGetDevice(&cur));
+        if (cur != P->device) SP_CUDA(cudaSetDevice(P->device));
+    }
+    const sp_status st = save_program(P, buf, cap, size);
+    if (buf && cur != P->device) cudaSetDevice(cur);
+    return st;
+}
+
+sp_status sp_load(const void *buf, size_t size, void *cuda_stream, sp_program **out)
+{
+    if (!out) return set_error(SP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    SP_TRY(check_saved(buf, size));
+    sp_program *P = host_alloc_fails() ? nullptr : new (std::nothrow) sp_program();
+    if (!P) return set_error(SP_ERR_OOM, "host allocation of the program failed");
+    g_live_host++;
+    const auto t0 = std::chrono::steady_clock::now();
+    sp_status st = load_program(buf, size, (cudaStream_t)cuda_stream, P);
+    if (st != SP_OK) {
+        cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        cudaGetLastError();
+        release(P);
+        return st;
+    }
+    P->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = P;
     return SP_OK;
 }

@@ -388,6 +388,26 @@ __device__ __forceinline__ void draw_scatter(const uint4 *__restrict__ blkT, con
                                           lane, q, apply);
 }
 
+// The launch constants of every channel block of every batch member (shots
+// from 0, so the high word is 0): thread i is block i - blkStart[m] of member
+// m, found by binary search over the members' cumulative block counts.
+__global__ void __launch_bounds__(256) k_block_consts_batch(const FusedParams *__restrict__ params, int nprog,
+                                                            const uint64_t *__restrict__ blkEnd)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= blkEnd[nprog - 1]) return;
+    int lo = 0, hi = nprog - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (blkEnd[mid] > i) hi = mid; else lo = mid + 1;
+    }
+    const FusedParams &p = params[lo];
+    const uint32_t b = (uint32_t)(i - (lo ? blkEnd[lo - 1] : 0ull));
+    const uint64_t ub = (uint64_t)PH_M1 * b;
+    const uint64_t pp = (uint64_t)PH_M0 * ((uint32_t)(ub >> 32) ^ (uint32_t)p.seed);
+    const_cast<uint4 *>(p.blkConst)[b] = make_uint4((uint32_t)ub, (uint32_t)pp, (uint32_t)(pp >> 32), p.blkFilt[b]);
+}
+
 // The launch constants of every channel block (see FusedParams::blkConst).
 __global__ void __launch_bounds__(256) k_block_consts(int64_t n_blk, uint32_t k0, uint32_t c1u,
                                                       const uint32_t *__restrict__ blkFilt, uint4 *__restrict__ out)
@@ -926,8 +946,11 @@ sp_status fused_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nsh
     if (!P->fused_tw) return set_error(SP_ERR_INVALID_ARG, "fused path unavailable for this program");
     if (P->stream == 2) return grouped_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     FusedParams fp = fused_params(P, P->fused_tw, seed, shot0, nshots, d_meas, d_det, d_obs);
-    // one launch's block constants when its shots share a high word
-    if (P->d_blkConst && (shot0 >> 32) == ((shot0 + nshots - 1) >> 32)) {
+    // one launch's block constants when its shots share a high word and it
+    // runs at least two waves of tiles (a short launch would pay the extra
+    // kernel's latency for little)
+    const uint64_t wave = 32u * (uint64_t)P->fused_tw * (uint64_t)P->num_sms * (uint64_t)P->fused_ctas_per_sm;
+    if (P->d_blkConst && nshots >= 2 * wave && (shot0 >> 32) == ((shot0 + nshots - 1) >> 32)) {
         ProfScope pc(P, SP_KERNEL_CONSTS, s);
         k_block_consts<<<(unsigned)ceil_div(P->n_blk, 256), 256, 0, s>>>(P->n_blk, (uint32_t)seed,
                                                                         (uint32_t)(shot0 >> 32), P->d_blkFilt,
@@ -988,6 +1011,8 @@ struct BatchPlan {
     size_t nparams = 0;
     FusedParams *d_params = nullptr;           // [nparams], refreshed by every call
     uint64_t *d_tileEnd = nullptr;             // [nparams]
+    uint64_t *d_blkEnd = nullptr;              // [nparams] cumulative channel blocks, parameter order
+    uint64_t nblk_total = 0;
     unsigned long long *d_counter = nullptr;   // [groups]
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1003,6 +1028,7 @@ struct BatchPlan {
         if (graph) cudaGraphDestroy(graph);
         dev_free(d_params);
         dev_free(d_tileEnd);
+        dev_free(d_blkEnd);
         dev_free(d_counter);
         if (cur >= 0 && cur != device) cudaSetDevice(cur);
         cudaGetLastError();
@@ -1030,6 +1056,7 @@ void fill_params(const BatchPlan &plan, sp_program *const *progs, const uint64_t
                                              d_det ? d_det[i] : nullptr, d_obs ? d_obs[i] : nullptr);
             out[g.param0 + k].tab_off_words = 0;   // the batch reads phase-2 tables from global memory
             out[g.param0 + k].emit_once = 0;       // and emits one record kind per pass
+            out[g.param0 + k].blkConst = progs[i]->d_blkConst;   // written by the plan's first node
         }
 }
 
@@ -1098,7 +1125,7 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
                 np->others.push_back(i);
             }
         }
-        std::vector<uint64_t> tileEnd;
+        std::vector<uint64_t> tileEnd, blkEnd;
         // the group with the most work first: the others' CTAs fill its tail
         std::vector<BatchGroup> shapes;
         for (auto &kv : by_shape) shapes.push_back(kv.second);
@@ -1117,6 +1144,8 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
             for (uint32_t i : g.members) {
                 acc += (nshots[i] + 32u * g.tw - 1) / (32u * g.tw);
                 tileEnd.push_back(acc);
+                np->nblk_total += (uint64_t)progs[i]->n_blk;
+                blkEnd.push_back(np->nblk_total);
             }
             BatchFn fn = batch_kernel(g.tw, g.unroll);
             SP_CUDA(max_dynamic_smem(fn));
@@ -1131,11 +1160,13 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
         if (np->nparams) {
             if (dev_alloc((void **)&np->d_params, np->nparams * sizeof(FusedParams)) != cudaSuccess ||
                 dev_alloc((void **)&np->d_tileEnd, np->nparams * 8) != cudaSuccess ||
+                dev_alloc((void **)&np->d_blkEnd, np->nparams * 8) != cudaSuccess ||
                 dev_alloc((void **)&np->d_counter, np->groups.size() * 8) != cudaSuccess) {
                 cudaGetLastError();
                 return set_error(SP_ERR_OOM, "cudaMalloc of the batch plan failed");
             }
             SP_CUDA(cudaMemcpy(np->d_tileEnd, tileEnd.data(), tileEnd.size() * 8, cudaMemcpyHostToDevice));
+            SP_CUDA(cudaMemcpy(np->d_blkEnd, blkEnd.data(), blkEnd.size() * 8, cudaMemcpyHostToDevice));
             // ---- capture on library streams, replay on the caller's --------
             // counter reset, then one branch per launch shape (the shapes'
             // persistent kernels may overlap), then a join
@@ -1155,6 +1186,11 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
                 if (e != cudaSuccess && st == SP_OK) st = cuda_error(e, what);
             };
             ok(cudaMemsetAsync(np->d_counter, 0, ng * 8, cs), "counter reset during capture");
+            if (np->nblk_total) {
+                k_block_consts_batch<<<(unsigned)ceil_div((int64_t)np->nblk_total, 256), 256, 0, cs>>>(
+                    np->d_params, (int)np->nparams, np->d_blkEnd);
+                ok(cudaGetLastError(), "batch block constants during capture");
+            }
             ok(cudaEventRecord(g_capture_event[dev][MAX_SHAPES], cs), "fork during capture");
             for (size_t k = 0; k < ng && st == SP_OK; k++) {
                 const BatchGroup &g = np->groups[k];

@@ -177,6 +177,8 @@ namespace sp {
 sp_status set_error(sp_status st, const std::string &msg);
 sp_status cuda_error(cudaError_t e, const char *what);
 
+#define SP_TRY(x) do { sp_status _s = (x); if (_s != SP_OK) return _s; } while (0)
+
 #define SP_CUDA(call)                                                  \
     do {                                                               \
         cudaError_t _e = (call);                                       \
@@ -192,8 +194,23 @@ cudaError_t dev_alloc(void **p, size_t bytes);
 void dev_free(void *p);
 bool host_alloc_fails();
 
-// build (sp_build.cu)
+// build (sp_build.cu).  finish_program derives the sampler program, the
+// expectation tables, the fused-kernel program and the path choice from
+// P->d_A and the channel table (the traversal's output).
 sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_program *P);
+sp_status finish_program(sp_program *P, cudaStream_t stream);
+uint32_t threshold_of(double p);
+
+// A row's parent (the earlier row its own part is coded against) lies at
+// most PARENT_LOOKBACK rows before it.
+constexpr int PARENT_LOOKBACK = 512;
+
+// saved programs (sp_serial.cu): save_program writes the blob (size only
+// when buf is NULL), check_saved validates one on the host, load_program
+// validates and rebuilds it on the current device.
+sp_status save_program(const sp_program *P, void *buf, size_t cap, size_t *size);
+sp_status check_saved(const void *buf, size_t size);
+sp_status load_program(const void *buf, size_t size, cudaStream_t stream, sp_program *P);
 
 // profiling: bracket one kernel launch with events when enabled
 struct ProfScope {
