@@ -402,6 +402,7 @@ __global__ void __launch_bounds__(256) k_block_consts_batch(const FusedParams *_
         if (blkEnd[mid] > i) hi = mid; else lo = mid + 1;
     }
     const FusedParams &p = params[lo];
+    if (!p.blkConst) return;   // this member draws without launch constants
     const uint32_t b = (uint32_t)(i - (lo ? blkEnd[lo - 1] : 0ull));
     const uint64_t ub = (uint64_t)PH_M1 * b;
     const uint64_t pp = (uint64_t)PH_M0 * ((uint32_t)(ub >> 32) ^ (uint32_t)p.seed);
@@ -1002,11 +1003,22 @@ struct BatchGroup {
 };
 
 
+// A member with at least one full wave of tiles runs as its own k_fused
+// node (its launch shape, launch-constant node, staged tables); the graph's
+// branches of such nodes fill each other's last waves.
+struct SoloMember {
+    uint32_t member = 0;
+    int grid = 0;
+    bool consts = false;                       // a k_block_consts node precedes the kernel
+    cudaGraphNode_t consts_node = nullptr, fused_node = nullptr;
+};
+
 struct BatchPlan {
     int device = 0;
     std::vector<uint64_t> key;
     std::vector<const sp_program *> progs;
     std::vector<BatchGroup> groups;
+    std::vector<SoloMember> solo;
     std::vector<uint32_t> others;              // members sampled through their own path
     size_t nparams = 0;
     FusedParams *d_params = nullptr;           // [nparams], refreshed by every call
@@ -1044,11 +1056,18 @@ cudaStream_t g_capture_stream[64][MAX_SHAPES] = {};
 cudaEvent_t g_capture_event[64][MAX_SHAPES + 1] = {};
 
 // The per-call part of the members' parameters: seeds and output pointers.
+// A member's launch constants live in its program's buffer, written by the
+// plan's first node; a program that appears more than once in the call
+// (its members would share the buffer with different seeds), or a member
+// whose shots cross a multiple of 2^32 (the constants hold one high word),
+// draws without them.
 void fill_params(const BatchPlan &plan, sp_program *const *progs, const uint64_t *seeds, const uint64_t *nshots,
                  uint64_t *const *d_meas, uint64_t *const *d_det, uint64_t *const *d_obs,
                  std::vector<FusedParams> &out)
 {
     out.resize(plan.nparams);
+    std::map<const sp_program *, int> uses;
+    for (const sp_program *P : plan.progs) uses[P]++;
     for (const BatchGroup &g : plan.groups)
         for (size_t k = 0; k < g.members.size(); k++) {
             const uint32_t i = g.members[k];
@@ -1056,7 +1075,8 @@ void fill_params(const BatchPlan &plan, sp_program *const *progs, const uint64_t
                                              d_det ? d_det[i] : nullptr, d_obs ? d_obs[i] : nullptr);
             out[g.param0 + k].tab_off_words = 0;   // the batch reads phase-2 tables from global memory
             out[g.param0 + k].emit_once = 0;       // and emits one record kind per pass
-            out[g.param0 + k].blkConst = progs[i]->d_blkConst;   // written by the plan's first node
+            const bool own = uses[progs[i]] == 1 && nshots[i] <= (1ull << 32);
+            out[g.param0 + k].blkConst = own ? progs[i]->d_blkConst : nullptr;
         }
 }
 
@@ -1114,6 +1134,17 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
             np->progs.push_back(P);
             if (nshots[i] == 0) continue;
             if (P->path == SP_PATH_FUSED && P->fused_tw && P->stream == 1) {
+                const uint64_t tiles = (nshots[i] + 32u * P->fused_tw - 1) / (32u * P->fused_tw);
+                const uint64_t slots = (uint64_t)P->num_sms * (uint64_t)P->fused_ctas_per_sm;
+                if (slots && tiles >= slots) {
+                    SoloMember m;
+                    m.member = i;
+                    m.grid = (int)slots;
+                    m.consts = P->d_blkConst && tiles >= 2 * slots && nshots[i] <= (1ull << 32) &&
+                               std::count(progs, progs + n, progs[i]) == 1;
+                    np->solo.push_back(m);
+                    continue;
+                }
                 BatchGroup &g = by_shape[std::make_tuple(P->fused_tw, P->fused_unroll, P->fused_ctas_per_sm)];
                 g.tw = P->fused_tw;
                 g.unroll = P->fused_unroll;
@@ -1212,8 +1243,53 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
             }
             if (ec != cudaSuccess) return cuda_error(ec, "cudaStreamEndCapture");
             np->graph = graph;
-            SP_CUDA(cudaGraphInstantiate(&np->exec, graph, 0));
         }
+        if (!np->solo.empty()) {
+            if (!np->graph) SP_CUDA(cudaGraphCreate(&np->graph, 0));
+            // heaviest first, each to the least loaded of up to four branches
+            std::stable_sort(np->solo.begin(), np->solo.end(), [&](const SoloMember &a, const SoloMember &b) {
+                return (double)progs[a.member]->n_blk * (double)nshots[a.member] >
+                       (double)progs[b.member]->n_blk * (double)nshots[b.member];
+            });
+            const int nb = (int)std::min<size_t>(4, np->solo.size());
+            std::vector<double> load((size_t)nb, 0.0);
+            std::vector<cudaGraphNode_t> tail((size_t)nb, nullptr);
+            for (SoloMember &m : np->solo) {
+                const int br = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                load[br] += (double)progs[m.member]->n_blk * (double)nshots[m.member];
+                const sp_program *P = progs[m.member];
+                // parameters of the first call; every call sets its own
+                FusedParams fp = fused_params(P, P->fused_tw, seeds[m.member], 0, nshots[m.member], nullptr,
+                                              nullptr, nullptr);
+                uint32_t k0 = (uint32_t)seeds[m.member], c1u = 0u;
+                int64_t nblk = P->n_blk;
+                const uint32_t *filt = P->d_blkFilt;
+                uint4 *bconst = P->d_blkConst;
+                if (m.consts) {
+                    void *args[] = {&nblk, &k0, &c1u, &filt, &bconst};
+                    cudaKernelNodeParams kp = {};
+                    kp.func = (void *)k_block_consts;
+                    kp.gridDim = dim3((unsigned)ceil_div(P->n_blk, 256));
+                    kp.blockDim = dim3(256);
+                    kp.kernelParams = args;
+                    SP_CUDA(cudaGraphAddKernelNode(&m.consts_node, np->graph, tail[br] ? &tail[br] : nullptr,
+                                                   tail[br] ? 1 : 0, &kp));
+                    tail[br] = m.consts_node;
+                    fp.blkConst = P->d_blkConst;
+                }
+                void *args[] = {&fp};
+                cudaKernelNodeParams kp = {};
+                kp.func = (void *)fused_kernel(P->fused_tw, P->fused_unroll);
+                kp.gridDim = dim3((unsigned)m.grid);
+                kp.blockDim = dim3((unsigned)P->fused_threads);
+                kp.sharedMemBytes = (unsigned)P->fused_smem;
+                kp.kernelParams = args;
+                SP_CUDA(cudaGraphAddKernelNode(&m.fused_node, np->graph, tail[br] ? &tail[br] : nullptr,
+                                               tail[br] ? 1 : 0, &kp));
+                tail[br] = m.fused_node;
+            }
+        }
+        if (np->graph) SP_CUDA(cudaGraphInstantiate(&np->exec, np->graph, 0));
         // bounded cache: drop the least recently used plan
         if (g_plans.size() >= BATCH_MAX_PLANS) {
             auto lru = std::min_element(g_plans.begin(), g_plans.end(),
@@ -1227,9 +1303,41 @@ sp_status sample_batch(sp_program *const *progs, uint32_t n, const uint64_t *see
     }
     plan->last_use = ++g_batch_clock;
     if (plan->exec) {
-        fill_params(*plan, progs, seeds, nshots, d_meas, d_det, d_obs, hp);
-        // pageable source: staged by the runtime before the call returns
-        SP_CUDA(cudaMemcpyAsync(plan->d_params, hp.data(), hp.size() * sizeof(FusedParams), cudaMemcpyHostToDevice, s));
+        if (plan->nparams) {
+            fill_params(*plan, progs, seeds, nshots, d_meas, d_det, d_obs, hp);
+            // pageable source: staged by the runtime before the call returns
+            SP_CUDA(cudaMemcpyAsync(plan->d_params, hp.data(), hp.size() * sizeof(FusedParams), cudaMemcpyHostToDevice, s));
+        }
+        // the solo members' seeds and outputs go into their nodes (a launch
+        // already enqueued keeps the parameters it was launched with)
+        for (const SoloMember &m : plan->solo) {
+            const uint32_t i = m.member;
+            const sp_program *P = progs[i];
+            FusedParams fp = fused_params(P, P->fused_tw, seeds[i], 0, nshots[i], d_meas ? d_meas[i] : nullptr,
+                                          d_det ? d_det[i] : nullptr, d_obs ? d_obs[i] : nullptr);
+            if (m.consts) {
+                int64_t nblk = P->n_blk;
+                uint32_t k0 = (uint32_t)seeds[i], c1u = 0u;
+                const uint32_t *filt = P->d_blkFilt;
+                uint4 *bconst = P->d_blkConst;
+                void *args[] = {&nblk, &k0, &c1u, &filt, &bconst};
+                cudaKernelNodeParams kp = {};
+                kp.func = (void *)k_block_consts;
+                kp.gridDim = dim3((unsigned)ceil_div(P->n_blk, 256));
+                kp.blockDim = dim3(256);
+                kp.kernelParams = args;
+                SP_CUDA(cudaGraphExecKernelNodeSetParams(plan->exec, m.consts_node, &kp));
+                fp.blkConst = P->d_blkConst;
+            }
+            void *args[] = {&fp};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void *)fused_kernel(P->fused_tw, P->fused_unroll);
+            kp.gridDim = dim3((unsigned)m.grid);
+            kp.blockDim = dim3((unsigned)P->fused_threads);
+            kp.sharedMemBytes = (unsigned)P->fused_smem;
+            kp.kernelParams = args;
+            SP_CUDA(cudaGraphExecKernelNodeSetParams(plan->exec, m.fused_node, &kp));
+        }
         SP_CUDA(cudaGraphLaunch(plan->exec, s));
     }
     const std::vector<uint32_t> others = plan->others;

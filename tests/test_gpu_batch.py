@@ -177,3 +177,47 @@ def test_every_launch_shape_in_one_batch():
     outs = sp.sample_batch(progs, seeds, shots)
     torch.cuda.synchronize()
     _check_members(progs, seeds, shots, outs)
+
+
+def test_same_program_twice_in_one_batch():
+    """One program listed twice with different seeds (and a third entry of
+    another program): each member's records equal its own sp_sample call.
+    The repeated program's members share one launch-constant buffer, so
+    they draw without it. With these shot counts the repeated program's
+    members run as their own kernel nodes and the other one inside the
+    persistent batch kernel; three calls with new seeds and new output
+    buffers replay one plan."""
+    a = sp.build(surface_code(7, 7, 1e-3))
+    b = sp.build(surface_code(5, 5, 2e-3))
+    progs, shots = [a, b, a], [50_000, 9_000, 40_000]
+    before = sp.batch_plans()[0]
+    for rep in range(3):
+        seeds = [11 + 10 * rep, 12 + 10 * rep, 13 + 10 * rep]
+        outs = sp.sample_batch(progs, seeds, shots)
+        torch.cuda.synchronize()
+        _check_members(progs, seeds, shots, outs)
+    assert sp.batch_plans()[0] <= before + 1
+
+
+def test_large_members_as_kernel_nodes_against_oracle():
+    """Members with at least a full wave of tiles run as separate kernel
+    nodes on parallel branches of the plan's graph (with their own launch
+    constants); records equal sp_sample and the oracle on sampled shots,
+    over two calls with new seeds."""
+    specs = [surface_code(9, 9, 1e-3), surface_code(11, 11, 5e-4), repetition_code(5, 5, 0.01),
+             surface_code(3, 3, 2e-3)]
+    progs = [sp.build(c) for c in specs]
+    shots = [120_000, 100_003, 150_000, 70_000]
+    for rep in range(2):
+        seeds = [100 * rep + k for k in range(len(progs))]
+        outs = sp.sample_batch(progs, seeds, shots)
+        torch.cuda.synchronize()
+        _check_members(progs, seeds, shots, outs)
+    for c, s, n, (m, d, o) in zip(specs, seeds, shots, outs):
+        ref = oracle.Program(c)
+        pick = np.array([0, n // 3, n - 1])
+        rm, rd, ro = ref.sample_shots(s, pick)
+        idx = torch.as_tensor(pick, device="cuda")
+        np.testing.assert_array_equal(_u64(m[idx]), rm)
+        np.testing.assert_array_equal(_u64(d[idx]), rd)
+        np.testing.assert_array_equal(_u64(o[idx]), ro)

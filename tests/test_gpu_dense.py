@@ -89,6 +89,29 @@ def test_tensor_path_chunked_equals_unchunked():
     assert prog.device_status() == 0
 
 
+def test_tensor_path_large_count_equals_fused():
+    """700,001 shots from an unaligned start (a ragged last 128-shot tile,
+    more than a million-row fault-bit buffer) on the tensor path, twice in
+    a row on the same buffers: records equal the fused path's bit for bit,
+    and a few shots are recomputed by the oracle."""
+    c = mirror_circuit(48, 16, p=0.02, seed=4)
+    prog, ref = sp.build(c), oracle.Program(c)
+    n, shot0 = 700_001, 12_345
+    prog.set_path(sp.PATH_FUSED)
+    fm, fd, fo = prog.sample(n, seed=5, shot0=shot0)
+    prog.set_path(sp.PATH_TENSOR)
+    for _ in range(2):
+        m, d, o = prog.sample(n, seed=5, shot0=shot0)
+        torch.cuda.synchronize()
+        assert prog.device_status() == 0
+        for a, b in ((m, fm), (d, fd), (o, fo)):
+            assert torch.equal(a, b)
+    pick = np.array([0, 1, 127, 128, 350_000, n - 129, n - 128, n - 1])
+    rm, rd, ro = ref.sample_shots(5, shot0 + pick)
+    np.testing.assert_array_equal(_u64(m)[pick], rm)
+    np.testing.assert_array_equal(_u64(d)[pick], rd)
+
+
 def test_path_choice_is_measured_where_rows_are_dense():
     """Mirror circuits have dense rows: the build times the sparse and both
     dense forms and keeps the fastest; the surface code (0.3 % dense) is
