@@ -36,8 +36,8 @@ UNIT = "shots/s"
 # the first timed 1,000,000-shot launch. The figure belongs to the kernel
 # source it was taken on; when the hash of that source differs, it is dropped
 # (reported as null) until a new capture replaces it.
-FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 698_112 + 301_691_392,
-                 "sources_sha256": "06c3bedc9a57393255bde5b4008d841ad1624e4e6a6bf2ced220ffc166e04d07"}
+FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 584_448 + 301_245_184,
+                 "sources_sha256": "35c1e3e44d077f4ff2fceef5523052662b1b8ce161c045f3c29ad84419e23818"}
 FUSED_SOURCES = ("paper_2311_03906_gb300/csrc/sp_fused.cu", "paper_2311_03906_gb300/csrc/sp_fused_dev.cuh",
                  "paper_2311_03906_gb300/csrc/sp_internal.h")
 
@@ -475,11 +475,21 @@ def _dense_paths(args):
                     "achieved_set_coefficients": flops_set / sec / 1e12, "frac_set_coefficients": flops_set / sec / 1e12 / peak,
                     "traffic": None,
                     "peak_source": f"MEASURED_PEAKS.json bf16_tflops x 2 (nominal FP8:BF16 ratio; {peaks['source']})"}
+        pp = res["dense"]["kernels"].get("product")
+        popc = None
+        if pp:
+            # one LOP3 (acc ^= a & b) per (record row, 32-position word of b, shot)
+            lops = rows * -(-(info["num_symbols"] + 1) // 32) * shots
+            achieved = lops / (pp["ms_per_step"] / 1e3) / 1e12
+            lpeak = 152 * 64 * peaks["sm_max_mhz"] * 1e6 / 1e12
+            popc = {"kernel": "k_popc_product", "bound": "alu", "achieved": achieved, "peak": lpeak,
+                    "unit": "T LOP3/s", "frac": achieved / lpeak,
+                    "peak_source": "152 SMs x 64 int32 logic ops/clk x max SM clock (derived)"}
         fastest = min(res, key=lambda k: res[k]["ms"])
         sweep.append({"p": p, "symbols": info["num_symbols"], "record_rows": rows, "density": info["density"],
                       "build_s": build_s, "auto_path": names.get(auto, str(auto)), "fastest": fastest,
                       "build_probe_ms": {names[k]: v for k, v in enumerate(info["path_probe_ms"]) if v > 0 and k in names},
-                      "paths": res, "tensor_roofline": roof, "device_status": status})
+                      "paths": res, "tensor_roofline": roof, "popc_roofline": popc, "device_status": status})
         prog.close()
     return {"config": {"workload": "mirror_circuit(n=512, layers=16, p, seed=1)", "shots_per_step": args.dense_shots},
             "sweep": sweep}
