@@ -592,23 +592,45 @@ def _fit(args):
             "loss_last": losses[-1], "mean_abs_p_error_first": err0, "mean_abs_p_error_last": err1}
 
 
-def run_profile_case():
-    """Small case for ncu: build the d=11 program, then sample 65536 shots
-    once. The autotuner's timing launches of the fused kernel come first;
-    their number is printed so a capture can skip them."""
+def run_profile_case(case="fused"):
+    """Small cases for ncu, each one process:
+    - fused: build the d=11 program, then sample 65536 shots once. The
+      autotuner's timing launches of the fused kernel come first; their
+      number is printed so a capture can skip them.
+    - grouped: the same program switched to the grouped draw (stream 2),
+      then 65536 shots once; the stream's own autotuner launches come first
+      and are printed.
+    - dense, tensor: the dense-row mirror circuit (512 qubits, 16 layers,
+      p = 0.01), then 32768 shots once on that product form. The build's
+      path probe runs each form three times first (draw and product of both
+      record kinds per run)."""
     import torch
     import paper_2311_03906_gb300 as sp
-    from workloads import surface_code
-    prog = sp.build(surface_code(WORKLOAD["distance"], WORKLOAD["rounds"], WORKLOAD["p"]))
-    i = prog.info
-    shots = 65536
+    from workloads import mirror_circuit, surface_code
+    if case in ("fused", "grouped"):
+        prog = sp.build(surface_code(WORKLOAD["distance"], WORKLOAD["rounds"], WORKLOAD["p"]))
+        a0 = 0
+        if case == "grouped":
+            # the grouped stream's autotuner runs at the switch: count only its launches
+            a0 = prog.info["autotune_launches"]
+            prog.set_stream(2)
+        shots = 65536
+        name = WORKLOAD["name"]
+    else:
+        prog = sp.build(mirror_circuit(512, 16, p=0.01, seed=1))
+        a0 = 0
+        prog.set_path(sp.PATH_DENSE if case == "dense" else sp.PATH_TENSOR)
+        shots = 32768
+        name = "mirror_circuit(512, 16, p=0.01, seed=1)"
+    i = prog.refresh_info()
     out = prog.alloc_outputs(shots)
     prog.sample(shots, seed=1, out=out)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": WORKLOAD["name"], "shots": shots, "path": i["path"],
+    print(json.dumps({"profile_case": name, "case": case, "shots": shots, "path": i["path"], "stream": i["stream"],
                       "fused_tile_shots": i["fused_tile_shots"], "fused_ctas_per_sm": i["fused_ctas_per_sm"],
                       "fused_variant": i["fused_variant"],
-                      "autotune_fused_launches": i["autotune_launches"]}))
+                      "autotune_fused_launches": i["autotune_launches"] - a0,
+                      "device_status": prog.device_status()}))
 
 
 def run_ours(args):
@@ -799,14 +821,16 @@ def main():
     ap.add_argument("--no-c1", action="store_true", help="skip the repetition-code configuration")
     ap.add_argument("--no-grouped", action="store_true", help="skip the grouped fault-draw stream")
     ap.add_argument("--profile", action="store_true",
-                    help="build, then one 65536-shot sample only (the case captured by ncu)")
+                    help="build, then one small sample only (the case captured by ncu)")
+    ap.add_argument("--profile-case", default="fused", choices=["fused", "grouped", "dense", "tensor"],
+                    help="which small case --profile runs")
     args = ap.parse_args()
     if args.cpu_baseline_child:
         print(json.dumps(_cpu_baseline_child(args.cpu_seconds)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     elif args.profile:
-        run_profile_case()
+        run_profile_case(args.profile_case)
     else:
         run_ours(args)
 

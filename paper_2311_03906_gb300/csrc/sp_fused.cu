@@ -502,8 +502,10 @@ __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ b
 // 32w..32w+31 of (s_0, s_1, ...), b_0 = 1 of Eq. sampling) is stored at
 // Bd[(g * bpitch + w) * 32 + l].  k_dense_fill writes the constant bit and
 // zeroes the rest; k_draw_dense runs the grouped draw for 64 shots per warp
-// over every channel block and sets the bit of each fired symbol in the
-// shots that drew it (global atomics: faults are rare).
+// over one range of channel blocks (blockIdx.y of gridDim.y even ranges, so
+// that small shot counts still fill the GPU) and sets the bit of each fired
+// symbol in the shots that drew it (global atomics: faults are rare, and
+// warps of other ranges may share a word).
 __global__ void __launch_bounds__(256) k_dense_fill(uint32_t *__restrict__ Bd, int64_t bpitch, int64_t nvec)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -532,7 +534,13 @@ __global__ void __launch_bounds__(256, 4) k_draw_dense(const uint4 *__restrict__
     uint32_t *base = Bd + (size_t)(2 * gw) * (size_t)bpitch * 32u;
     const bool has2 = 2 * gw + 1 < ngroups;
     const Keys K = make_keys(k0, k1);
-    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, nullptr, 0u, (uint32_t)n_blk, sc, shot_base, K, k1, lane,
+    // this CTA's range of channel blocks, in whole groups of DRAW_GROUP
+    const uint64_t ngrp = ((uint64_t)n_blk + DRAW_GROUP - 1) / DRAW_GROUP;
+    const uint32_t b0 = (uint32_t)(ngrp * blockIdx.y / gridDim.y) * DRAW_GROUP;
+    const uint64_t e1 = ngrp * (blockIdx.y + 1) / gridDim.y * DRAW_GROUP;
+    const uint32_t b1 = (uint32_t)(e1 < (uint64_t)n_blk ? e1 : (uint64_t)n_blk);
+    if (b0 >= b1) return;
+    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, nullptr, b0, b1, sc, shot_base, K, k1, lane,
                     q + warp * FUSED_QCAP,
                     [=](uint32_t sym, int t, uint32_t word) {
                         if (t == 1 && !has2) return;
@@ -555,11 +563,18 @@ sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, 
     k_dense_fill<<<(unsigned)ceil_div(nvec, 256), 256, 0, s>>>(Bd, bpitch, nvec);
     SP_CUDA(cudaGetLastError());
     if (P->n_blk == 0) return SP_OK;
-    // one warp covers every channel block: queued events must address them all
+    // a warp's queued events address the blocks of its range (at most all)
     if ((uint64_t)P->n_blk >= event_max_blocks(2))
         return set_error(SP_ERR_INVALID_ARG, "too many channel blocks for the dense draw");
-    k_draw_dense<<<(unsigned)ceil_div(ceil_div(ngroups, 2), 8), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->d_blkSym0,
-                                                                            P->d_blkFilt, P->n_blk, seed, shot0, ngroups, Bd, bpitch);
+    // split the channel blocks so that about four waves of warps run (4
+    // CTAs of 8 warps per SM), each range keeping at least 64 groups
+    const int64_t ctas = ceil_div(ceil_div(ngroups, 2), 8);
+    const int64_t want = 4 * 4 * (int64_t)std::max(P->num_sms, 1);
+    const int64_t ngrp = ceil_div(P->n_blk, (int64_t)DRAW_GROUP);
+    const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, ctas), ngrp / 64, 65535}));
+    k_draw_dense<<<dim3((unsigned)ctas, (unsigned)ranges), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->d_blkSym0,
+                                                                        P->d_blkFilt, P->n_blk, seed, shot0, ngroups,
+                                                                        Bd, bpitch);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
