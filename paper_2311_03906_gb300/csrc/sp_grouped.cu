@@ -156,14 +156,61 @@ struct DrawGrouped {
                 }
             }
         }
+        // ---- the CTA's walk queue: the part of the shared region behind the
+        // warps' own queues that phase 3's emit stage uses and phase 1 does
+        // not (the same sizes as the host's layout, clamped to the staged
+        // tables or the end of the launch's shared memory).  Fired groups
+        // go there in sets of 32 and all warps walk them after a barrier,
+        // so that the warps that drew more fired groups do not keep the
+        // others waiting; what does not fit is walked by its own warp.
+        uint32_t *aux = q - warp * (int)FUSED_QCAP;
+        uint32_t *cq = aux + nwarps * (int)FUSED_QCAP;
+        uint32_t ccap = 0;
+        {
+            uint32_t mx = 0, sum = 0;
+#pragma unroll
+            for (int sg = 0; sg < 3; sg++) {
+                const uint32_t w = 2u * (uint32_t)((p.nrow[sg] + 63) / 64) + 1u;
+                mx = max(mx, w);
+                sum += w;
+            }
+            uint32_t aux_words = max(32u * TW * (p.emit_once ? sum : mx), (FUSED_THREADS / 32) * FUSED_QCAP);
+            uint32_t dyn;
+            asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+            const uint32_t end = p.tab_off_words ? p.tab_off_words : dyn / 4u;
+            aux_words = min(aux_words, end - p.aux_off_words);
+            const uint32_t used = (uint32_t)nwarps * FUSED_QCAP + 4u;   // own queues, two counters, padding
+            ccap = aux_words > used + 32u ? aux_words - used : 0u;
+        }
+        uint32_t *cfill = cq, *ctake = cq + 1, *cev = cq + 4;
+        if (ccap && threadIdx.x == 0) {
+            *cfill = 0u;
+            *ctake = 0u;
+        }
+        __syncthreads();
         // ---- group words: quads [q0, q1) of this warp, 8 quads (32 groups)
         // gathered per queueing step
         const uint32_t nq = (p.n_grp + 3u) / 4u;
         const uint32_t q0 = (uint32_t)((uint64_t)warp * nq / (uint64_t)nwarps);
         const uint32_t q1 = (uint32_t)((uint64_t)(warp + 1) * nq / (uint64_t)nwarps);
-        const uint32_t g0 = 4u * q0;
+        const uint32_t g0 = ccap ? 0u : 4u * q0;   // events hold groups relative to g0
         const uint32_t lt = (1u << lane) - 1u;
         uint32_t cnt = 0;
+        // move the first n (<= 32) queued events to the CTA queue; the ones
+        // that do not fit stay at the front of the warp's queue (returned)
+        auto push = [&](uint32_t n) -> uint32_t {
+            __syncwarp();
+            uint32_t pos = 0u;
+            if (lane == 0) pos = atomicAdd(cfill, n);
+            pos = __shfl_sync(FM, pos, 0);
+            const uint32_t fit = pos >= ccap ? 0u : min(n, ccap - pos);
+            const uint32_t ev = (uint32_t)lane < n ? q[lane] : 0u;
+            __syncwarp();
+            if ((uint32_t)lane < fit) cev[pos + lane] = ev;
+            if ((uint32_t)lane >= fit && (uint32_t)lane < n) q[lane - fit] = ev;
+            __syncwarp();
+            return n - fit;
+        };
         for (uint32_t qq = q0; qq < q1; qq += 8u) {
             const uint32_t nqq = min(8u, q1 - qq);
             uint32_t word[TW];
@@ -190,7 +237,8 @@ struct DrawGrouped {
                     cnt += __popc(bal);
                     m &= m - 1u;
                     if (cnt >= 32u) {
-                        grouped_drain<TW>(q, 32u, p, K, g0, shot_base, lane, apply);
+                        const uint32_t left = ccap ? push(32u) : 32u;
+                        if (left) grouped_drain<TW>(q, left, p, K, g0, shot_base, lane, apply);
                         cnt -= 32u;
                         const uint32_t rest = (uint32_t)lane < cnt ? q[32 + lane] : 0u;
                         __syncwarp();
@@ -200,7 +248,21 @@ struct DrawGrouped {
                 }
             }
         }
-        grouped_drain<TW>(q, cnt, p, K, g0, shot_base, lane, apply);
+        if (!ccap) {
+            grouped_drain<TW>(q, cnt, p, K, g0, shot_base, lane, apply);
+            return;
+        }
+        const uint32_t left = cnt ? push(cnt) : 0u;
+        if (left) grouped_drain<TW>(q, left, p, K, g0, shot_base, lane, apply);
+        __syncthreads();   // every warp's events are in the CTA queue
+        const uint32_t total = min(*cfill, ccap);
+        for (;;) {
+            uint32_t b = 0u;
+            if (lane == 0) b = atomicAdd(ctake, 32u);
+            b = __shfl_sync(FM, b, 0);
+            if (b >= total) break;
+            grouped_drain<TW>(cev + b, min(32u, total - b), p, K, 0u, shot_base, lane, apply);
+        }
     }
 };
 
