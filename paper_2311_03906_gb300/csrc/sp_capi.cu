@@ -262,11 +262,15 @@ sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t 
     // pipeline granularity: at most the sampling chunk, at most 64 MiB of records
     int64_t piece = std::min<int64_t>(P->chunk_shots, std::max<int64_t>(1024, (64 << 20) / std::max<int64_t>(per_shot * 8, 8)));
     piece = std::max<int64_t>(1024, (piece / 1024) * 1024);
+    // the copy of the last piece is the one nothing overlaps: keep it short
+    // (one wave of the fused kernel's tiles, else 1/8 of a piece)
+    int64_t tail = std::max<int64_t>(1024, piece / 8);
     if (P->path == SP_PATH_FUSED && P->fused_tw) {
         // whole waves of the fused kernel's tiles, so that no piece ends in a
         // partly filled wave
         const int64_t wave = (int64_t)P->num_sms * P->fused_ctas_per_sm * 32 * P->fused_tw;
         if (wave > 0 && piece > wave) piece = (piece / wave) * wave;
+        if (wave > 0) tail = std::min<int64_t>(piece, wave);
     }
     sp_status st = SP_OK;
     if (uses_staged_scratch(P)) {
@@ -291,8 +295,10 @@ sp_status sp_sample_host(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t 
     // ev[0..1]: chunk i computed in stage i%2; ev[2..3]: stage i%2 copied out
     bool used[2] = {false, false};
     int64_t i = 0;
-    for (uint64_t done = 0; done < nshots; done += (uint64_t)piece, i++) {
-        const int64_t n = (int64_t)std::min<uint64_t>(nshots - done, (uint64_t)piece);
+    for (uint64_t done = 0, n = 0; done < nshots; done += n, i++) {
+        const uint64_t left = nshots - done;
+        // full pieces; the last one that would exceed 2 tails leaves one tail behind
+        n = left > (uint64_t)piece ? (uint64_t)piece : left > 2 * (uint64_t)tail ? left - (uint64_t)tail : left;
         const int b = (int)(i & 1);
         uint64_t *dm = P->d_out_stage + (size_t)b * stage_words;
         uint64_t *dd = dm + (size_t)piece * wm;

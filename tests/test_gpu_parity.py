@@ -176,6 +176,19 @@ def test_chunking_and_host_path_give_identical_records():
     assert torch.equal(m2, m0[5000:5100])
 
 
+def test_host_path_with_a_short_last_piece():
+    """300,001 shots into host buffers: the records come back in pieces and
+    the last piece is cut short (one wave of the fused kernel's tiles) so
+    that its copy is brief; every record equals sp_sample's."""
+    prog = sp.build(surface_code(5, 5, 2e-3))
+    shots = 300_001
+    m0, d0, o0 = prog.sample(shots, seed=4, shot0=7)
+    hm, hd, ho = prog.sample_host(shots, seed=4, shot0=7)
+    torch.cuda.synchronize()
+    for a, h in ((m0, hm), (d0, hd), (o0, ho)):
+        assert torch.equal(a.cpu(), h)
+
+
 def test_full_size_d11_sampled_shots(d11):
     """The d=11 r=11 p=1e-3 configuration at 1e6 shots in the launch
     configuration the benchmark times; 300 shots spread over the range are
