@@ -495,6 +495,51 @@ def _dense_paths(args):
             "sweep": sweep}
 
 
+def _layered_sampling(args):
+    """The paper's first measure (Sec. 5, Fig. 3): the time to generate
+    10,000 samples of the random layered circuits, n qubits x n layers, with
+    the three noise and entangling settings of Fig. 3a-c (5 CX pairs per
+    layer; floor(n/2) pairs; floor(n/2) pairs and DEPOLARIZE1(0.01) on every
+    qubit per layer), 5 % of the qubits measured per layer and all at the
+    end. Reported per circuit: the product form the build chose and the
+    density that decided it, the build time, and the sampling time of 10,000
+    shots into device buffers (best of three after a warm-up)."""
+    import torch
+    import paper_2311_03906_gb300 as sp
+    from workloads import random_layered
+    names = {sp.PATH_TENSOR: "tensor", sp.PATH_DENSE: "dense", sp.PATH_FUSED: "fused", sp.PATH_SPARSE: "staged-sparse"}
+    shots = 10_000
+    rows = []
+    for panel, kw in (("3a", dict(cnot_pairs=5)), ("3b", dict()), ("3c", dict(depolarize=0.01))):
+        for n in args.layered_sizes:
+            c = random_layered(n, n, seed=1, **kw)
+            t0 = time.perf_counter()
+            prog = sp.build(c)
+            build_s = time.perf_counter() - t0
+            info = prog.info
+            out = prog.alloc_outputs(shots)
+            prog.sample(shots, seed=1, out=out)
+            torch.cuda.synchronize()
+            best = 1e30
+            for r in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                prog.sample(shots, seed=1, shot0=(r + 1) * shots, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            nrec = info["num_measurements"] + info["num_detectors"] + info["num_observables"]
+            rows.append({"panel": panel, "n": n, "symbols": info["num_symbols"], "measurements": info["num_measurements"],
+                         "density": info["density"], "path": names.get(info["path"], str(info["path"])),
+                         "build_s": build_s, "sample_ms": best, "shots_per_s": shots / (best / 1e3),
+                         "record_gbit_s": nrec * shots / (best / 1e3) / 1e9})
+            del out
+            prog.close()
+    return {"workload": "random_layered(n, n, seed=1): Fig. 3a (5 CX pairs/layer), 3b (floor(n/2) pairs), "
+                        "3c (floor(n/2) pairs + DEPOLARIZE1(0.01)); 5 % of qubits measured per layer",
+            "shots": shots, "rows": rows}
+
+
 def _build_times(args):
     """Time to initialize a sampler (the paper's second measure, Sec. 5): sp_build
     (GPU traversal, replay, detector rows, sampler program, autotuner) against
@@ -789,6 +834,8 @@ def run_ours(args):
         line["dense_rows"] = _dense_paths(args)
     if world == 1 and not args.no_build_times:
         line["build_times"] = _build_times(args)
+    if world == 1 and args.layered_sizes:
+        line["layered_sampling"] = _layered_sampling(args)
     if world == 1 and not args.no_fit:
         line["fit"] = _fit(args)
     if world == 1 and not args.no_cpu_baseline:
@@ -816,6 +863,8 @@ def main():
     ap.add_argument("--no-build-times", action="store_true", help="skip the sampler-initialization timings")
     ap.add_argument("--no-fit", action="store_true", help="skip the noise-model fit (config 5)")
     ap.add_argument("--build-sizes", type=int, nargs="*", default=[100, 200, 300, 500])
+    ap.add_argument("--layered-sizes", type=int, nargs="*", default=[100, 500, 1000],
+                    help="n of the random layered circuits sampled for the paper's Fig. 3 measure (none: skip)")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-d17", action="store_true", help="skip the d=17 configuration")
     ap.add_argument("--no-c1", action="store_true", help="skip the repetition-code configuration")

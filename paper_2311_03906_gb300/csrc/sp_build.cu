@@ -907,6 +907,26 @@ __global__ void k_parent(const uint32_t *__restrict__ A, int64_t apitch, int64_t
     }
 }
 
+// Symbol -> rows index of the full rows (counting sort by symbol; the order
+// of the rows within one symbol's list is not fixed, and XOR does not need
+// it): pass 1 counts, pass 2 places each (row, symbol) at its symbol's next
+// free slot.  One warp per row.
+__global__ void k_col_count(const uint32_t *__restrict__ off, const uint32_t *__restrict__ idx, int64_t nrows,
+                            uint32_t *cnt)
+{
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= nrows) return;
+    for (uint32_t k = off[j] + (threadIdx.x & 31); k < off[j + 1]; k += 32) atomicAdd(&cnt[idx[k]], 1u);
+}
+
+__global__ void k_col_fill(const uint32_t *__restrict__ off, const uint32_t *__restrict__ idx, int64_t nrows,
+                           uint32_t *next, uint32_t *rows)
+{
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= nrows) return;
+    for (uint32_t k = off[j] + (threadIdx.x & 31); k < off[j + 1]; k += 32) rows[atomicAdd(&next[idx[k]], 1u)] = (uint32_t)j;
+}
+
 __global__ void k_cflag(const uint32_t *A, int64_t apitch, int64_t nrows, const int32_t *parent,
                         uint8_t *cflag, uint8_t *cst)
 {
@@ -1404,7 +1424,17 @@ sp_status finish_program(sp_program *P, cudaStream_t stream)
         off[R] = (uint32_t)tot;
         if (tot >= 0xffffffffull) return set_error(SP_ERR_TOO_LARGE, "more than 2^32 nonzero coefficients");
         P->nnz_rows = (int64_t)tot;
-        SP_TRY(tmp.alloc(&d_fidx, (size_t)tot));
+        // the full rows stay with the program where they are small: the
+        // staged product gathers them row-parallel when few shots leave the
+        // parent chains too little parallelism
+        if (tot <= FULL_ROWS_KEEP) {
+            SP_TRY(dalloc(&P->d_fullIdx, (size_t)std::max<uint64_t>(tot, 1)));
+            SP_TRY(dalloc(&P->d_fullOff, (size_t)R + 1));
+            d_fidx = P->d_fullIdx;
+            SP_CUDA(cudaMemcpyAsync(P->d_fullOff, off.data(), ((size_t)R + 1) * 4, cudaMemcpyHostToDevice, stream));
+        } else {
+            SP_TRY(tmp.alloc(&d_fidx, (size_t)tot));
+        }
         SP_CUDA(cudaMemcpyAsync(d_off, off.data(), ((size_t)R + 1) * 4, cudaMemcpyHostToDevice, stream));
         k_row_csr<<<rb, 256, 0, stream>>>(P->d_A, P->apitch, R, nullptr, nullptr, d_off, d_fidx);
         k_parent<<<(unsigned)R, 128, 0, stream>>>(P->d_A, P->apitch, R, d_cnt, d_off, d_fidx,
@@ -1422,6 +1452,28 @@ sp_status finish_program(sp_program *P, cudaStream_t stream)
         k_row_csr<<<rb, 256, 0, stream>>>(P->d_A, P->apitch, R, P->d_parent, nullptr, P->d_rowOff, P->d_idx);
         k_cflag<<<(unsigned)ceil_div(R, 256), 256, 0, stream>>>(P->d_A, P->apitch, R, P->d_parent, P->d_cflag, P->d_const);
         SP_CUDA(cudaGetLastError());
+        // the rows of each symbol (transpose of the kept full rows), for the
+        // staged product that pushes fired symbols into L2-resident records
+        if (P->d_fullIdx && P->n_sym > 0) {
+            uint32_t *d_ccnt;
+            SP_TRY(tmp.alloc(&d_ccnt, (size_t)P->n_sym));
+            SP_CUDA(cudaMemsetAsync(d_ccnt, 0, (size_t)P->n_sym * 4, stream));
+            k_col_count<<<rb, 256, 0, stream>>>(P->d_fullOff, P->d_fullIdx, R, d_ccnt);
+            SP_CUDA(cudaGetLastError());
+            std::vector<uint32_t> cc((size_t)P->n_sym), coff((size_t)P->n_sym + 1, 0);
+            SP_CUDA(cudaMemcpyAsync(cc.data(), d_ccnt, (size_t)P->n_sym * 4, cudaMemcpyDeviceToHost, stream));
+            SP_CUDA(cudaStreamSynchronize(stream));
+            uint64_t acc = 0;
+            for (int64_t q = 0; q < P->n_sym; q++) { coff[q] = (uint32_t)acc; acc += cc[q]; }
+            coff[P->n_sym] = (uint32_t)acc;
+            SP_TRY(dalloc(&P->d_colFullOff, (size_t)P->n_sym + 1));
+            SP_TRY(dalloc(&P->d_colFullRows, (size_t)std::max<uint64_t>(acc, 1)));
+            SP_CUDA(cudaMemcpyAsync(P->d_colFullOff, coff.data(), ((size_t)P->n_sym + 1) * 4, cudaMemcpyHostToDevice, stream));
+            SP_CUDA(cudaMemcpyAsync(d_ccnt, coff.data(), (size_t)P->n_sym * 4, cudaMemcpyHostToDevice, stream));
+            k_col_fill<<<rb, 256, 0, stream>>>(P->d_fullOff, P->d_fullIdx, R, d_ccnt, P->d_colFullRows);
+            SP_CUDA(cudaGetLastError());
+            SP_CUDA(cudaStreamSynchronize(stream));
+        }
     } else {
         const uint32_t z = 0;
         SP_CUDA(cudaMemcpyAsync(P->d_rowOff, &z, 4, cudaMemcpyHostToDevice, stream));

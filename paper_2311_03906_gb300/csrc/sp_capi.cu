@@ -65,7 +65,7 @@ static void release(sp_program *P)
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != P->device) cudaSetDevice(P->device);
-    void *bufs[] = {P->d_A, P->d_chT, P->d_chKind, P->d_chP, P->d_chSym0, P->d_rowOff, P->d_idx,
+    void *bufs[] = {P->d_A, P->d_chT, P->d_chKind, P->d_chP, P->d_chSym0, P->d_rowOff, P->d_idx, P->d_fullOff, P->d_fullIdx, P->d_colFullOff, P->d_colFullRows,
                     P->d_parent, P->d_cflag, P->d_A64, P->d_const, P->d_inc, P->d_incT, P->d_kappa,
                     P->d_wbuf, P->d_B, P->d_recT, P->d_Bd, P->d_out_stage, P->d_blkT, P->d_blkMeta, P->d_blkFilt, P->d_blkConst,
                     P->d_blkSym0, P->d_fCflag, P->d_fChain, P->d_fBOff, P->d_fCOff, P->d_fCRefs,

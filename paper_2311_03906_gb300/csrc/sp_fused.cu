@@ -481,21 +481,78 @@ __global__ void __launch_bounds__(fused_threads(TW, U), fused_minb(TW, U))
 
 // Staged draw: fault bits to global memory, bit-sliced [symbol][32-shot word].
 // Block = 8 warps; warp = one 32-shot word over all channel blocks.
+// Block = 8 warps; warp = one 32-shot word over the channel blocks of range
+// blockIdx.y (gridDim.y even ranges, so that few shots still fill the GPU).
+// A range writes only its own symbols' rows of B: its last, partial set of
+// 32 stops at the next range's first symbol.
 __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ blkT,
-                                                     const uint32_t *__restrict__ blkMeta, int64_t n_blk,
+                                                     const uint32_t *__restrict__ blkMeta,
+                                                     const uint32_t *__restrict__ blkSym0, int64_t n_blk,
                                                      int64_t n_sym, uint64_t seed, uint64_t shot0, int64_t nwords,
                                                      uint32_t *__restrict__ B, int64_t bpitch)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (w >= nwords) return;
+    const uint32_t b0 = (uint32_t)((uint64_t)n_blk * blockIdx.y / gridDim.y);
+    const uint32_t b1 = (uint32_t)((uint64_t)n_blk * (blockIdx.y + 1) / gridDim.y);
+    if (b0 >= b1) return;
+    const uint32_t s_begin = blkSym0[b0];
+    const int64_t s_end = b1 < (uint64_t)n_blk ? (int64_t)blkSym0[b1] : n_sym;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     Shots<1> sc;
     sc.s[0] = shot_const(shot0 + (uint64_t)w * 32u + (uint64_t)lane, k1);
-    draw_blocks<1, 2>(blkT, blkMeta, 0u, (uint32_t)n_blk, 0u, sc, k0, k1, lane,
+    draw_blocks<1, 2>(blkT, blkMeta, b0, b1, s_begin, sc, k0, k1, lane,
                    [=](uint32_t base, const Cols<1> col) {
-                       if ((int64_t)base + lane < n_sym) B[(size_t)(base + lane) * bpitch + w] = col.v[0];
+                       if ((int64_t)base + lane < s_end) B[(size_t)(base + lane) * bpitch + w] = col.v[0];
                    });
+}
+
+// The staged draw fused with the sparse product, for records that fit in
+// L2: the same warps and channel-block ranges as k_draw_staged, but each
+// flushed set of 32 symbol words goes straight into the records (every row
+// holding the symbol, from the full rows by symbol; recT pre-filled with
+// the rows' constants) by atomic XOR, instead of into the fault-bit table.
+__global__ void __launch_bounds__(256) k_draw_push(const uint4 *__restrict__ blkT,
+                                                   const uint32_t *__restrict__ blkMeta,
+                                                   const uint32_t *__restrict__ blkSym0, int64_t n_blk,
+                                                   int64_t n_sym, uint64_t seed, uint64_t shot0, int64_t nwords,
+                                                   const uint32_t *__restrict__ colOff,
+                                                   const uint32_t *__restrict__ colRows, uint32_t *recT,
+                                                   int64_t rpitch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (w >= nwords) return;
+    const uint32_t b0 = (uint32_t)((uint64_t)n_blk * blockIdx.y / gridDim.y);
+    const uint32_t b1 = (uint32_t)((uint64_t)n_blk * (blockIdx.y + 1) / gridDim.y);
+    if (b0 >= b1) return;
+    const uint32_t s_begin = blkSym0[b0];
+    const int64_t s_end = b1 < (uint64_t)n_blk ? (int64_t)blkSym0[b1] : n_sym;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    Shots<1> sc;
+    sc.s[0] = shot_const(shot0 + (uint64_t)w * 32u + (uint64_t)lane, k1);
+    draw_blocks<1, 2>(blkT, blkMeta, b0, b1, s_begin, sc, k0, k1, lane,
+                   [=](uint32_t base, const Cols<1> col) {
+                       const uint32_t sym = base + (uint32_t)lane, x = col.v[0];
+                       if (x && (int64_t)sym < s_end) {
+                           const uint32_t e = colOff[sym + 1];
+                           for (uint32_t k = colOff[sym]; k < e; k++) atomicXor(&recT[(size_t)colRows[k] * rpitch + w], x);
+                       }
+                   });
+}
+
+sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *recT,
+                           int64_t pitch, cudaStream_t s)
+{
+    if (P->n_sym == 0 || nwords == 0) return SP_OK;
+    const int64_t want = 4 * 32 * (int64_t)std::max(P->num_sms, 1);
+    const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, nwords), P->n_blk / 256, 65535}));
+    k_draw_push<<<dim3((unsigned)ceil_div(nwords, 8), (unsigned)ranges), 256, 0, s>>>(
+        P->d_blkT, P->d_blkMeta, P->d_blkSym0, P->n_blk, P->n_sym, seed, shot0, nwords, P->d_colFullOff,
+        P->d_colFullRows, recT, pitch);
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
 }
 
 // Shot-major draw for the dense products.  Word w of shot 32g+l (entries
@@ -921,8 +978,11 @@ sp_status launch_draw_staged(const sp_program *P, uint64_t seed, uint64_t shot0,
                              int64_t pitch, cudaStream_t s)
 {
     if (P->n_sym == 0 || nwords == 0) return SP_OK;
-    k_draw_staged<<<(unsigned)ceil_div(nwords, 8), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->n_blk, P->n_sym, seed,
-                                                                 shot0, nwords, B, pitch);
+    // about four waves of warps, each range keeping at least 256 channel blocks
+    const int64_t want = 4 * 32 * (int64_t)std::max(P->num_sms, 1);
+    const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, nwords), P->n_blk / 256, 65535}));
+    k_draw_staged<<<dim3((unsigned)ceil_div(nwords, 8), (unsigned)ranges), 256, 0, s>>>(
+        P->d_blkT, P->d_blkMeta, P->d_blkSym0, P->n_blk, P->n_sym, seed, shot0, nwords, B, pitch);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -81,6 +81,13 @@ struct sp_program {
     // sparse sampler program: row j = parent (or none) XOR const XOR sum of B rows
     uint32_t *d_rowOff = nullptr;   // [n_rows+1]
     uint32_t *d_idx = nullptr;      // symbol-1 indices
+    // full rows (symbol-1 indices of A_j, constant excluded), kept when at
+    // most FULL_ROWS_KEEP entries: the row-parallel product for few shots
+    uint32_t *d_fullOff = nullptr;  // [n_rows+1]
+    uint32_t *d_fullIdx = nullptr;
+    // the same full rows by symbol: rows d_colFullRows[off[s] .. off[s+1]) hold symbol s+1
+    uint32_t *d_colFullOff = nullptr;   // [n_sym+1]
+    uint32_t *d_colFullRows = nullptr;
     int32_t *d_parent = nullptr;    // [n_rows]
     uint8_t *d_cflag = nullptr;     // [n_rows]
     int64_t nnz_rows = 0, nnz_delta = 0;
@@ -204,6 +211,8 @@ uint32_t threshold_of(double p);
 // A row's parent (the earlier row its own part is coded against) lies at
 // most PARENT_LOOKBACK rows before it.
 constexpr int PARENT_LOOKBACK = 512;
+// Largest full-row index list a program keeps (1 GiB of indices).
+constexpr uint64_t FULL_ROWS_KEEP = 1ull << 28;
 
 // saved programs (sp_serial.cu): save_program writes the blob (size only
 // when buf is NULL), check_saved validates one on the host, load_program
@@ -242,6 +251,8 @@ sp_status choose_path(sp_program *P, cudaStream_t s);
 bool tensor_path_available(const sp_program *P);
 sp_status dense_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
                       uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
+sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *recT,
+                           int64_t pitch, cudaStream_t s);
 sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t ngroups, uint32_t *Bd,
                             int64_t bpitch, cudaStream_t s);
 // fused path (sp_fused.cu)

@@ -11,7 +11,8 @@
 //                 32-shot word is c'_j ^ rec[parent(j)] ^ XOR_{s in delta_j}
 //                 B[s-1], lane = 32-shot word, so every index load is shared
 //                 by 1024 shots and every B load is a coalesced 128-byte row
-//                 segment.
+//                 segment; with few shots, k_gather_full takes each row
+//                 from its full symbol list instead, all rows at once.
 //   K6 k_emit     32x32 bit transposes from the bit-sliced records to the
 //                 shot-major packed output.
 #include <algorithm>
@@ -21,6 +22,8 @@
 namespace sp {
 
 constexpr uint32_t FULLM = 0xffffffffu;
+// Largest record block the push path keeps (it must stay in L2 for the atomics).
+constexpr uint64_t PUSH_MAX_BYTES = 96ull << 20;
 
 
 // K5.  Warp = 1024 shots (lane = 32-shot word); rows in order so a parent
@@ -56,6 +59,36 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t *__restrict__ B, 
             recT[(size_t)j * rpitch + w] = acc ^ a1 ^ a2 ^ a3;
         }
     }
+}
+
+// K5 for few shots.  Warp = (record row j, 32 consecutive 32-shot words),
+// lane = word: row j from its full symbol list (not its delta against a
+// parent), so that rows are independent and all of them run at once.
+__global__ void __launch_bounds__(256) k_gather_full(const uint32_t *__restrict__ B, int64_t bpitch,
+                                                     int64_t nwords, const uint32_t *__restrict__ fullOff,
+                                                     const uint32_t *__restrict__ fullIdx,
+                                                     const uint8_t *__restrict__ cst, int64_t nrows,
+                                                     uint32_t *recT, int64_t rpitch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wgroups = (nwords + 31) / 32;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t j = gw / wgroups;
+    if (j >= nrows) return;
+    const int64_t w = (gw % wgroups) * 32 + lane;
+    if (w >= nwords) return;
+    const uint32_t *Bw = B + w;
+    uint32_t acc = cst[j] ? FULLM : 0u, a1 = 0, a2 = 0, a3 = 0;
+    const uint32_t e = fullOff[j + 1];
+    uint32_t k = fullOff[j];
+    for (; k + 4 <= e; k += 4) {
+        acc ^= Bw[(size_t)fullIdx[k] * bpitch];
+        a1 ^= Bw[(size_t)fullIdx[k + 1] * bpitch];
+        a2 ^= Bw[(size_t)fullIdx[k + 2] * bpitch];
+        a3 ^= Bw[(size_t)fullIdx[k + 3] * bpitch];
+    }
+    for (; k < e; k++) acc ^= Bw[(size_t)fullIdx[k] * bpitch];
+    recT[(size_t)j * rpitch + w] = acc ^ a1 ^ a2 ^ a3;
 }
 
 // K6.  Block = 256 threads; tile = 256 record rows x 8 words (256 shots).
@@ -96,6 +129,36 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ recT,
     }
 }
 
+// Records start from their rows' constants (the push path XORs into them).
+__global__ void __launch_bounds__(256) k_rec_init(const uint8_t *__restrict__ cst, int64_t nrows, int64_t nwords,
+                                                  uint32_t *recT, int64_t rpitch)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows * nwords) return;
+    const int64_t j = i / nwords, w = i % nwords;
+    recT[(size_t)j * rpitch + w] = cst[j] ? FULLM : 0u;
+}
+
+// K5 for nwords 32-shot words: the parent chains (one warp per 1024 shots
+// walking every row in order) where there are enough such warps to fill the
+// GPU, else every row at once from its full symbol list (when the program
+// kept it).
+static sp_status launch_gather(const sp_program *P, const uint32_t *B, int64_t pitch, int64_t nwords, uint32_t *recT,
+                               cudaStream_t s)
+{
+    const int64_t warps = ceil_div(nwords, 32);
+    if (P->d_fullIdx && warps < 4 * 152) {
+        const int64_t all = warps * P->n_rows;
+        k_gather_full<<<(unsigned)ceil_div(all, 8), 256, 0, s>>>(B, pitch, nwords, P->d_fullOff, P->d_fullIdx,
+                                                                 P->d_const, P->n_rows, recT, pitch);
+    } else {
+        k_gather<<<(unsigned)ceil_div(warps, 4), 128, 0, s>>>(B, pitch, nwords, P->d_rowOff, P->d_idx, P->d_parent,
+                                                                P->d_cflag, P->n_rows, recT, pitch);
+    }
+    SP_CUDA(cudaGetLastError());
+    return SP_OK;
+}
+
 // The same three launches as sample_chunk, on caller-provided scratch:
 // B (n_sym rows) and recT (n_rows rows), both with `pitch` 32-shot words per
 // row; nshots must not exceed 32 * pitch.  Used by the entry point that
@@ -111,12 +174,7 @@ sp_status sample_chunk_into(const sp_program *P, uint32_t *B, uint32_t *recT, in
         sp_status st = launch_draw_staged(P, seed, shot0, nwords, B, pitch, s);
         if (st != SP_OK) return st;
     }
-    if (P->n_rows > 0) {
-        const int64_t warps = ceil_div(nwords, 32);
-        k_gather<<<(unsigned)ceil_div(warps, 4), 128, 0, s>>>(B, pitch, nwords, P->d_rowOff, P->d_idx,
-                                                                P->d_parent, P->d_cflag, P->n_rows, recT, pitch);
-        SP_CUDA(cudaGetLastError());
-    }
+    if (P->n_rows > 0) SP_TRY(launch_gather(P, B, pitch, nwords, recT, s));
     struct Seg { uint64_t *dst; int64_t row0, n; } segs[3] = {
         {d_meas, 0, P->n_meas}, {d_det, P->n_meas, P->n_det}, {d_obs, P->n_meas + P->n_det, P->n_obs}};
     for (const Seg &g : segs) {
@@ -177,18 +235,25 @@ sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t ns
         return fused_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     if (P->path == SP_PATH_DENSE || P->path == SP_PATH_TENSOR)
         return dense_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
-    if (P->n_sym > 0) {
+    const int64_t warps = ceil_div(nwords, 32);
+    if (P->d_colFullRows && warps < 4 * 152 && (uint64_t)P->n_rows * (uint64_t)nwords * 4u <= PUSH_MAX_BYTES) {
+        // few shots and records that fit in L2: fired symbols go straight
+        // into the records (no fault-bit table)
         ProfScope ps(P, SP_KERNEL_DRAW, s);
-        sp_status st = launch_draw_staged(P, seed, shot0, nwords, P->d_B, pitch, s);
-        if (st != SP_OK) return st;
-    }
-    if (P->n_rows > 0) {
-        const int64_t warps = ceil_div(nwords, 32);
-        ProfScope ps(P, SP_KERNEL_PRODUCT, s);
-        k_gather<<<(unsigned)ceil_div(warps, 4), 128, 0, s>>>(P->d_B, pitch, nwords, P->d_rowOff, P->d_idx,
-                                                                P->d_parent, P->d_cflag, P->n_rows,
-                                                                P->d_recT, pitch);
+        k_rec_init<<<(unsigned)ceil_div(P->n_rows * nwords, 256), 256, 0, s>>>(P->d_const, P->n_rows, nwords,
+                                                                               P->d_recT, pitch);
         SP_CUDA(cudaGetLastError());
+        SP_TRY(launch_draw_push(P, seed, shot0, nwords, P->d_recT, pitch, s));
+    } else {
+        if (P->n_sym > 0) {
+            ProfScope ps(P, SP_KERNEL_DRAW, s);
+            sp_status st = launch_draw_staged(P, seed, shot0, nwords, P->d_B, pitch, s);
+            if (st != SP_OK) return st;
+        }
+        if (P->n_rows > 0) {
+            ProfScope ps(P, SP_KERNEL_PRODUCT, s);
+            SP_TRY(launch_gather(P, P->d_B, pitch, nwords, P->d_recT, s));
+        }
     }
     struct Seg { uint64_t *dst; int64_t row0, n; } segs[3] = {
         {d_meas, 0, P->n_meas}, {d_det, P->n_meas, P->n_det}, {d_obs, P->n_meas + P->n_det, P->n_obs}};
