@@ -508,48 +508,61 @@ __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ b
                    });
 }
 
-// The staged draw fused with the sparse product, for records that fit in
-// L2: the same warps and channel-block ranges as k_draw_staged, but each
-// flushed set of 32 symbol words goes straight into the records (every row
-// holding the symbol, from the full rows by symbol; recT pre-filled with
-// the rows' constants) by atomic XOR, instead of into the fault-bit table.
-__global__ void __launch_bounds__(256) k_draw_push(const uint4 *__restrict__ blkT,
-                                                   const uint32_t *__restrict__ blkMeta,
-                                                   const uint32_t *__restrict__ blkSym0, int64_t n_blk,
-                                                   int64_t n_sym, uint64_t seed, uint64_t shot0, int64_t nwords,
-                                                   const uint32_t *__restrict__ colOff,
-                                                   const uint32_t *__restrict__ colRows, uint32_t *recT,
-                                                   int64_t rpitch)
+// The draw fused with the sparse product in global memory, for records
+// that fit in L2: warp = 64 shots (two 32-shot words) over one range of
+// channel blocks (blockIdx.y), with the fused kernel's draw (least-word
+// filter, events resolved 32 at a time); every fired symbol's shot word is
+// XORed straight into the records of the rows holding it (the full rows by
+// symbol; recT pre-filled with the rows' constants), by atomics in L2.
+__global__ void __launch_bounds__(256, 4) k_draw_push(const uint4 *__restrict__ blkT,
+                                                      const uint32_t *__restrict__ blkMeta,
+                                                      const uint32_t *__restrict__ blkSym0,
+                                                      const uint32_t *__restrict__ blkFilt, int64_t n_blk,
+                                                      uint64_t seed, uint64_t shot0, int64_t nwords,
+                                                      const uint32_t *__restrict__ colOff,
+                                                      const uint32_t *__restrict__ colRows, uint32_t *recT,
+                                                      int64_t rpitch)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (w >= nwords) return;
-    const uint32_t b0 = (uint32_t)((uint64_t)n_blk * blockIdx.y / gridDim.y);
-    const uint32_t b1 = (uint32_t)((uint64_t)n_blk * (blockIdx.y + 1) / gridDim.y);
-    if (b0 >= b1) return;
-    const uint32_t s_begin = blkSym0[b0];
-    const int64_t s_end = b1 < (uint64_t)n_blk ? (int64_t)blkSym0[b1] : n_sym;
+    __shared__ uint32_t q[8 * FUSED_QCAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * 8 + warp;      // words 2gw and 2gw+1
+    if (2 * gw >= nwords) return;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    Shots<1> sc;
-    sc.s[0] = shot_const(shot0 + (uint64_t)w * 32u + (uint64_t)lane, k1);
-    draw_blocks<1, 2>(blkT, blkMeta, b0, b1, s_begin, sc, k0, k1, lane,
-                   [=](uint32_t base, const Cols<1> col) {
-                       const uint32_t sym = base + (uint32_t)lane, x = col.v[0];
-                       if (x && (int64_t)sym < s_end) {
-                           const uint32_t e = colOff[sym + 1];
-                           for (uint32_t k = colOff[sym]; k < e; k++) atomicXor(&recT[(size_t)colRows[k] * rpitch + w], x);
-                       }
-                   });
+    const uint64_t shot_base = shot0 + 64u * (uint64_t)gw;
+    Shots<2> sc;
+#pragma unroll
+    for (int t = 0; t < 2; t++) sc.s[t] = shot_const(shot_base + 32u * t + lane, k1);
+    const bool has2 = 2 * gw + 1 < nwords;
+    const Keys K = make_keys(k0, k1);
+    const uint64_t ngrp = ((uint64_t)n_blk + DRAW_GROUP - 1) / DRAW_GROUP;
+    const uint32_t b0 = (uint32_t)(ngrp * blockIdx.y / gridDim.y) * DRAW_GROUP;
+    const uint64_t e1 = ngrp * (blockIdx.y + 1) / gridDim.y * DRAW_GROUP;
+    const uint32_t b1 = (uint32_t)(e1 < (uint64_t)n_blk ? e1 : (uint64_t)n_blk);
+    if (b0 >= b1) return;
+    uint32_t *rec = recT + 2 * gw;
+    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, nullptr, b0, b1, sc, shot_base, K, k1, lane,
+                    q + warp * FUSED_QCAP,
+                    [=](uint32_t sym, int t, uint32_t word) {
+                        if (t == 1 && !has2) return;
+                        const uint32_t e = colOff[sym + 1];
+                        for (uint32_t k = colOff[sym]; k < e; k++) atomicXor(&rec[(size_t)colRows[k] * rpitch + t], word);
+                    });
 }
 
 sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *recT,
                            int64_t pitch, cudaStream_t s)
 {
-    if (P->n_sym == 0 || nwords == 0) return SP_OK;
-    const int64_t want = 4 * 32 * (int64_t)std::max(P->num_sms, 1);
-    const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, nwords), P->n_blk / 256, 65535}));
-    k_draw_push<<<dim3((unsigned)ceil_div(nwords, 8), (unsigned)ranges), 256, 0, s>>>(
-        P->d_blkT, P->d_blkMeta, P->d_blkSym0, P->n_blk, P->n_sym, seed, shot0, nwords, P->d_colFullOff,
+    if (P->n_blk == 0 || nwords == 0) return SP_OK;
+    // a warp's queued events address the blocks of its range (at most all)
+    if ((uint64_t)P->n_blk >= event_max_blocks(2))
+        return set_error(SP_ERR_INVALID_ARG, "too many channel blocks for the staged draw");
+    // about four waves of warps (4 CTAs of 8 warps per SM), each range keeping at least 64 groups
+    const int64_t ctas = ceil_div(ceil_div(nwords, 2), 8);
+    const int64_t want = 4 * 4 * (int64_t)std::max(P->num_sms, 1);
+    const int64_t ngrp = ceil_div(P->n_blk, (int64_t)DRAW_GROUP);
+    const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, ctas), ngrp / 64, 65535}));
+    k_draw_push<<<dim3((unsigned)ctas, (unsigned)ranges), 256, 0, s>>>(
+        P->d_blkT, P->d_blkMeta, P->d_blkSym0, P->d_blkFilt, P->n_blk, seed, shot0, nwords, P->d_colFullOff,
         P->d_colFullRows, recT, pitch);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
