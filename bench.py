@@ -36,8 +36,8 @@ UNIT = "shots/s"
 # the first timed 1,000,000-shot launch. The figure belongs to the kernel
 # source it was taken on; when the hash of that source differs, it is dropped
 # (reported as null) until a new capture replaces it.
-FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 584_448 + 301_245_184,
-                 "sources_sha256": "35c1e3e44d077f4ff2fceef5523052662b1b8ce161c045f3c29ad84419e23818"}
+FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 855_296 + 301_372_672,
+                 "sources_sha256": "37c081d302df1409de9a23893100290419bc45a893d657a818e61ceb78c23b6a"}
 FUSED_SOURCES = ("paper_2311_03906_gb300/csrc/sp_fused.cu", "paper_2311_03906_gb300/csrc/sp_fused_dev.cuh",
                  "paper_2311_03906_gb300/csrc/sp_internal.h")
 

@@ -176,6 +176,32 @@ def test_chunking_and_host_path_give_identical_records():
     assert torch.equal(m2, m0[5000:5100])
 
 
+def test_fig3c_circuit_staged_forms_equal_fused():
+    """The paper's Fig. 3c circuit at n = 300 (300 qubits x 300 layers,
+    DEPOLARIZE1(0.01), 184,584 symbols): the staged product with few shots
+    (fired symbols pushed into L2-resident records) and with many shots
+    (a fault-bit table gathered row by row) equals the fused kernel's records
+    bit for bit, and sampled shots equal the oracle's."""
+    c = random_layered(300, 300, depolarize=0.01, seed=1)
+    prog = sp.build(c)
+    assert prog.info["path"] == sp.PATH_FUSED
+    ref = oracle.Program(c)
+    for shots, shot0 in ((5_001, 77), (650_000, 1 << 32)):
+        prog.set_path(sp.PATH_FUSED)
+        fm, fd, fo = prog.sample(shots, seed=9, shot0=shot0)
+        prog.set_path(sp.PATH_SPARSE)
+        m, d, o = prog.sample(shots, seed=9, shot0=shot0)
+        torch.cuda.synchronize()
+        for a, b in ((m, fm), (d, fd), (o, fo)):
+            assert torch.equal(a, b)
+        pick = np.array([0, 1, 31, 32, shots // 2, shots - 1])
+        rm, rd, ro = ref.sample_shots(9, shot0 + pick)
+        idx = torch.as_tensor(pick, device="cuda")
+        np.testing.assert_array_equal(_u64(m[idx]), rm)
+        np.testing.assert_array_equal(_u64(d[idx]), rd)
+    prog.set_path(sp.PATH_AUTO)
+
+
 def test_host_path_with_a_short_last_piece():
     """300,001 shots into host buffers: the records come back in pieces and
     the last piece is cut short (one wave of the fused kernel's tiles) so
