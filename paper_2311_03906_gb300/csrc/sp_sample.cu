@@ -24,6 +24,8 @@ namespace sp {
 constexpr uint32_t FULLM = 0xffffffffu;
 // Largest record block the push path keeps (it must stay in L2 for the atomics).
 constexpr uint64_t PUSH_MAX_BYTES = 96ull << 20;
+// The push draw's queued events address a warp's channel blocks in 25 bits.
+constexpr int64_t PUSH_MAX_BLOCKS = (int64_t)1 << 25;
 
 
 // K5.  Warp = 1024 shots (lane = 32-shot word); rows in order so a parent
@@ -236,7 +238,8 @@ sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t ns
     if (P->path == SP_PATH_DENSE || P->path == SP_PATH_TENSOR)
         return dense_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     const int64_t warps = ceil_div(nwords, 32);
-    if (P->d_colFullRows && warps < 4 * 152 && (uint64_t)P->n_rows * (uint64_t)nwords * 4u <= PUSH_MAX_BYTES) {
+    if (P->d_colFullRows && warps < 4 * 152 && (uint64_t)P->n_rows * (uint64_t)nwords * 4u <= PUSH_MAX_BYTES &&
+        P->n_blk < PUSH_MAX_BLOCKS) {
         // few shots and records that fit in L2: fired symbols go straight
         // into the records (no fault-bit table)
         ProfScope ps(P, SP_KERNEL_DRAW, s);
