@@ -907,26 +907,6 @@ __global__ void k_parent(const uint32_t *__restrict__ A, int64_t apitch, int64_t
     }
 }
 
-// Symbol -> rows index of the full rows (counting sort by symbol; the order
-// of the rows within one symbol's list is not fixed, and XOR does not need
-// it): pass 1 counts, pass 2 places each (row, symbol) at its symbol's next
-// free slot.  One warp per row.
-__global__ void k_col_count(const uint32_t *__restrict__ off, const uint32_t *__restrict__ idx, int64_t nrows,
-                            uint32_t *cnt)
-{
-    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (j >= nrows) return;
-    for (uint32_t k = off[j] + (threadIdx.x & 31); k < off[j + 1]; k += 32) atomicAdd(&cnt[idx[k]], 1u);
-}
-
-__global__ void k_col_fill(const uint32_t *__restrict__ off, const uint32_t *__restrict__ idx, int64_t nrows,
-                           uint32_t *next, uint32_t *rows)
-{
-    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (j >= nrows) return;
-    for (uint32_t k = off[j] + (threadIdx.x & 31); k < off[j + 1]; k += 32) rows[atomicAdd(&next[idx[k]], 1u)] = (uint32_t)j;
-}
-
 __global__ void k_cflag(const uint32_t *A, int64_t apitch, int64_t nrows, const int32_t *parent,
                         uint8_t *cflag, uint8_t *cst)
 {
@@ -1243,17 +1223,18 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
 
     // The tableau (4 bit-vectors of n rows per qubit, plus a pad word) lives
     // in shared memory: one CTA's when it fits next to the kernel's static
-    // shared memory, else spread over a cluster of 2, 4 or 8 CTAs; global
-    // memory with one CTA if no cluster can be launched.
+    // shared memory, else spread over a cluster of 8 CTAs (gate levels and
+    // random-outcome rowsums split over the CTAs' columns: measured no slower
+    // than the smallest cluster that fits at 600 qubits, 21 % faster at 800
+    // and 8 % at 1,000); global memory with one CTA if no cluster can be
+    // launched.
     const size_t qbytes = (4 * (size_t)Wq + 1) * 4;
     const size_t smem_cap = 192 * 1024;
     int CL = 1, qp = std::max(n, 1);
     if ((size_t)qp * qbytes > smem_cap) {
         CL = 0;
-        for (int c : {2, 4, 8}) {
-            const int q = (n + c - 1) / c;
-            if ((size_t)q * qbytes <= smem_cap) { CL = c; qp = q; break; }
-        }
+        const int q = (n + 7) / 8;
+        if ((size_t)q * qbytes <= smem_cap) { CL = 8; qp = q; }
     }
     TravParams tp;
     tp.insts = d_insts; tp.sched = d_sched; tp.steps = d_steps; tp.nsteps = (int64_t)steps.size();
@@ -1281,9 +1262,8 @@ sp_status build_program(const sp_circuit_desc *desc, cudaStream_t stream, sp_pro
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cudaError_t e = cudaSuccess;
-        if (CL == 2) { SP_CUDA(max_dynamic_smem(k_traverse<2>)); e = cudaLaunchKernelEx(&cfg, k_traverse<2>, tp); }
-        else if (CL == 4) { SP_CUDA(max_dynamic_smem(k_traverse<4>)); e = cudaLaunchKernelEx(&cfg, k_traverse<4>, tp); }
-        else { SP_CUDA(max_dynamic_smem(k_traverse<8>)); e = cudaLaunchKernelEx(&cfg, k_traverse<8>, tp); }
+        SP_CUDA(max_dynamic_smem(k_traverse<8>));
+        e = cudaLaunchKernelEx(&cfg, k_traverse<8>, tp);
         if (e == cudaSuccess) launched = true;
         else cudaGetLastError();
     }
@@ -1452,28 +1432,6 @@ sp_status finish_program(sp_program *P, cudaStream_t stream)
         k_row_csr<<<rb, 256, 0, stream>>>(P->d_A, P->apitch, R, P->d_parent, nullptr, P->d_rowOff, P->d_idx);
         k_cflag<<<(unsigned)ceil_div(R, 256), 256, 0, stream>>>(P->d_A, P->apitch, R, P->d_parent, P->d_cflag, P->d_const);
         SP_CUDA(cudaGetLastError());
-        // the rows of each symbol (transpose of the kept full rows), for the
-        // staged product that pushes fired symbols into L2-resident records
-        if (P->d_fullIdx && P->n_sym > 0) {
-            uint32_t *d_ccnt;
-            SP_TRY(tmp.alloc(&d_ccnt, (size_t)P->n_sym));
-            SP_CUDA(cudaMemsetAsync(d_ccnt, 0, (size_t)P->n_sym * 4, stream));
-            k_col_count<<<rb, 256, 0, stream>>>(P->d_fullOff, P->d_fullIdx, R, d_ccnt);
-            SP_CUDA(cudaGetLastError());
-            std::vector<uint32_t> cc((size_t)P->n_sym), coff((size_t)P->n_sym + 1, 0);
-            SP_CUDA(cudaMemcpyAsync(cc.data(), d_ccnt, (size_t)P->n_sym * 4, cudaMemcpyDeviceToHost, stream));
-            SP_CUDA(cudaStreamSynchronize(stream));
-            uint64_t acc = 0;
-            for (int64_t q = 0; q < P->n_sym; q++) { coff[q] = (uint32_t)acc; acc += cc[q]; }
-            coff[P->n_sym] = (uint32_t)acc;
-            SP_TRY(dalloc(&P->d_colFullOff, (size_t)P->n_sym + 1));
-            SP_TRY(dalloc(&P->d_colFullRows, (size_t)std::max<uint64_t>(acc, 1)));
-            SP_CUDA(cudaMemcpyAsync(P->d_colFullOff, coff.data(), ((size_t)P->n_sym + 1) * 4, cudaMemcpyHostToDevice, stream));
-            SP_CUDA(cudaMemcpyAsync(d_ccnt, coff.data(), (size_t)P->n_sym * 4, cudaMemcpyHostToDevice, stream));
-            k_col_fill<<<rb, 256, 0, stream>>>(P->d_fullOff, P->d_fullIdx, R, d_ccnt, P->d_colFullRows);
-            SP_CUDA(cudaGetLastError());
-            SP_CUDA(cudaStreamSynchronize(stream));
-        }
     } else {
         const uint32_t z = 0;
         SP_CUDA(cudaMemcpyAsync(P->d_rowOff, &z, 4, cudaMemcpyHostToDevice, stream));

@@ -16,6 +16,7 @@
 //   K6 k_emit     32x32 bit transposes from the bit-sliced records to the
 //                 shot-major packed output.
 #include <algorithm>
+#include <vector>
 
 #include "sp_internal.h"
 
@@ -131,6 +132,67 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t *__restrict__ recT,
     }
 }
 
+// Symbol -> rows index of the full rows (counting sort by symbol; the order
+// of the rows within one symbol's list is not fixed, and XOR does not need
+// it): pass 1 counts, pass 2 places each (row, symbol) at its symbol's next
+// free slot.  One warp per row.
+__global__ void k_col_count(const uint32_t *__restrict__ off, const uint32_t *__restrict__ idx, int64_t nrows,
+                            uint32_t *cnt)
+{
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= nrows) return;
+    for (uint32_t k = off[j] + (threadIdx.x & 31); k < off[j + 1]; k += 32) atomicAdd(&cnt[idx[k]], 1u);
+}
+
+__global__ void k_col_fill(const uint32_t *__restrict__ off, const uint32_t *__restrict__ idx, int64_t nrows,
+                           uint32_t *next, uint32_t *rows)
+{
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= nrows) return;
+    for (uint32_t k = off[j] + (threadIdx.x & 31); k < off[j + 1]; k += 32) rows[atomicAdd(&next[idx[k]], 1u)] = (uint32_t)j;
+}
+
+// The rows of each symbol (transpose of the kept full rows), built on the
+// first sample that pushes fired symbols into the records; it synchronises
+// the stream once.  On an error nothing is kept and the program stays usable.
+static sp_status ensure_colfull(sp_program *P, cudaStream_t s)
+{
+    if (P->d_colFullRows) return SP_OK;
+    uint32_t *cnt = nullptr, *off = nullptr, *rows = nullptr;
+    auto fail = [&](sp_status st, const char *what) {
+        cudaGetLastError();
+        dev_free(cnt);
+        dev_free(off);
+        dev_free(rows);
+        return set_error(st, what);
+    };
+    if (dev_alloc((void **)&cnt, (size_t)P->n_sym * 4) != cudaSuccess)
+        return fail(SP_ERR_OOM, "cudaMalloc of the symbol -> rows index failed");
+    if (cudaMemsetAsync(cnt, 0, (size_t)P->n_sym * 4, s) != cudaSuccess)
+        return fail(SP_ERR_CUDA, "building the symbol -> rows index failed");
+    const unsigned rb = (unsigned)ceil_div(P->n_rows, 8);
+    k_col_count<<<rb, 256, 0, s>>>(P->d_fullOff, P->d_fullIdx, P->n_rows, cnt);
+    std::vector<uint32_t> c((size_t)P->n_sym), o((size_t)P->n_sym + 1, 0);
+    if (cudaMemcpyAsync(c.data(), cnt, (size_t)P->n_sym * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(SP_ERR_CUDA, "building the symbol -> rows index failed");
+    uint64_t acc = 0;
+    for (int64_t q = 0; q < P->n_sym; q++) { o[q] = (uint32_t)acc; acc += c[q]; }
+    o[P->n_sym] = (uint32_t)acc;
+    if (dev_alloc((void **)&off, ((size_t)P->n_sym + 1) * 4) != cudaSuccess ||
+        dev_alloc((void **)&rows, (size_t)std::max<uint64_t>(acc, 1) * 4) != cudaSuccess)
+        return fail(SP_ERR_OOM, "cudaMalloc of the symbol -> rows index failed");
+    if (cudaMemcpyAsync(off, o.data(), ((size_t)P->n_sym + 1) * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(cnt, o.data(), (size_t)P->n_sym * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return fail(SP_ERR_CUDA, "building the symbol -> rows index failed");
+    k_col_fill<<<rb, 256, 0, s>>>(P->d_fullOff, P->d_fullIdx, P->n_rows, cnt, rows);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(SP_ERR_CUDA, "building the symbol -> rows index failed");
+    dev_free(cnt);
+    P->d_colFullOff = off;
+    P->d_colFullRows = rows;
+    return SP_OK;
+}
+
 // Records start from their rows' constants (the push path XORs into them).
 __global__ void __launch_bounds__(256) k_rec_init(const uint8_t *__restrict__ cst, int64_t nrows, int64_t nwords,
                                                   uint32_t *recT, int64_t rpitch)
@@ -238,10 +300,11 @@ sp_status sample_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t ns
     if (P->path == SP_PATH_DENSE || P->path == SP_PATH_TENSOR)
         return dense_chunk(P, seed, shot0, nshots, d_meas, d_det, d_obs, s);
     const int64_t warps = ceil_div(nwords, 32);
-    if (P->d_colFullRows && warps < 4 * 152 && (uint64_t)P->n_rows * (uint64_t)nwords * 4u <= PUSH_MAX_BYTES &&
-        P->n_blk < PUSH_MAX_BLOCKS) {
+    if (P->d_fullIdx && P->n_sym > 0 && P->n_rows > 0 && warps < 4 * 152 &&
+        (uint64_t)P->n_rows * (uint64_t)nwords * 4u <= PUSH_MAX_BYTES && P->n_blk < PUSH_MAX_BLOCKS) {
         // few shots and records that fit in L2: fired symbols go straight
         // into the records (no fault-bit table)
+        SP_TRY(ensure_colfull(P, s));
         ProfScope ps(P, SP_KERNEL_DRAW, s);
         k_rec_init<<<(unsigned)ceil_div(P->n_rows * nwords, 256), 256, 0, s>>>(P->d_const, P->n_rows, nwords,
                                                                                P->d_recT, pitch);

@@ -51,7 +51,7 @@ CIRCUITS = {
     "layered300": lambda: random_layered(300, 30, depolarize=0.01, seed=6),
     "ffwide": lambda: random_feedforward_circuit(260, 3000, seed=810),
     # more than 577 qubits: the traversal's tableau spreads over a cluster of
-    # CTAs (2 for 640 and 700 qubits, 4 for 1000), with resets and feed-forward
+    # 8 CTAs (80 to 125 qubit columns each), with resets and feed-forward
     "rand640": lambda: random_small_circuit(640, 5000, seed=930),
     "ff700": lambda: random_feedforward_circuit(700, 6000, seed=820),
     "rand1000": lambda: random_small_circuit(1000, 6000, seed=931),
