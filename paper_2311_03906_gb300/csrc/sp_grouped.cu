@@ -1,11 +1,11 @@
 // sp_grouped.cu -- the grouped fault draw (stream 2, opt-in) inside the fused
 // sampling kernel.
 //
-// Algorithm 1 "Sample b from P_C" with the same Sec. 3.1 distributions as the
-// per-channel stream (independent Bernoulli(p) symbols, depolarizing outcomes
-// uniform over the non-identity Paulis, random outcomes fair coins), drawn
-// with far fewer Philox words when channels rarely fire.  Counter word 3 tags
-// the words (the per-channel stream uses 0):
+// The draw of b from P_C (Algorithm 1, Sampling) with the same Sec. 3.1
+// distributions as the per-channel stream (independent Bernoulli(p) symbols,
+// depolarizing outcomes uniform over the non-identity Paulis, random outcomes
+// fair coins), drawn with far fewer Philox words when channels rarely fire.
+// Counter word 3 tags the words (the per-channel stream uses 0):
 //   - random-outcome channel of rank r: bit r%32 of word (r/32)%4 of
 //     Philox(shot lo, shot hi, r/128, 3);
 //   - the other channels, in channel order, form groups of 32.  Group g
