@@ -67,7 +67,12 @@ __device__ __forceinline__ uint32_t grouped_outcome(uint32_t kind, uint32_t u, u
 // channel, are masked) and the warp reconverges after each block of four
 // channel words: a lane leaving a divergent apply loop early would
 // otherwise run ahead into the next block's Philox rounds, and the warp
-// would execute them in several partial passes.
+// would execute them in several partial passes.  A lane's walk fires about
+// one channel, but some lane of the warp fires in most of the 32 channel
+// slots, so the walk only notes (symbol, kind, word, threshold) of its first
+// two fired channels, by selects; their outcomes are computed and applied
+// after the walk, by every lane at the same point.  A third or later fired
+// channel (rare) is applied at once.
 template <int TW, typename Apply>
 __device__ __forceinline__ void grouped_drain(const uint32_t *q, uint32_t n, const FusedParams &p, const Keys &K,
                                               uint32_t g0, uint64_t shot_base, int lane, const Apply &apply)
@@ -85,11 +90,8 @@ __device__ __forceinline__ void grouped_drain(const uint32_t *q, uint32_t n, con
         const ShotConst s = shot_const(shot_base + 32u * (uint32_t)t + ln, k1 ^ S2_TAG_CHANNEL);
         const uint32_t first = g * S2_GROUP;
         const uint32_t nch = live ? min(S2_GROUP, p.n_fault - first) : 0u;
-        bool searching = true;
-        // the walk's first two fired channels wait in registers (first
-        // symbol, symbol bits) and are applied after it, by every lane at
-        // the same point; a third or later one (rare) is applied at once
-        uint32_t s_a = 0, v_a = 0, s_b = 0, v_b = 0;
+        bool searching = true, have_a = false, have_b = false;
+        uint32_t sym_a = 0, w_a = 0, u_a = 0, U_a = 0, sym_b = 0, w_b = 0, u_b = 0, U_b = 0;
         auto apply_bits = [&](uint32_t sym, uint32_t val) {
             while (val) {
                 const int b = __ffs(val) - 1;
@@ -97,32 +99,41 @@ __device__ __forceinline__ void grouped_drain(const uint32_t *q, uint32_t n, con
                 apply(sym + (uint32_t)b, t, 1u << ln);
             }
         };
+        // M1 * (8 g + j), the channel block's counter-word product
+        uint64_t ub = (uint64_t)PH_M1 * (8u * g);
 #pragma unroll 1
-        for (uint32_t j = 0; j < S2_GROUP / 4; j++) {
+        for (uint32_t j = 0; j < S2_GROUP / 4; j++, ub += PH_M1) {
             uint4 c[4];
 #pragma unroll
             for (int i = 0; i < 4; i++)
                 c[i] = 4 * j + (uint32_t)i < nch ? p.s2Ch[first + 4 * j + (uint32_t)i] : make_uint4(0u, 0u, 0u, 0u);
             uint32_t r[4];
-            philox_tagged(s, 8u * g + j, K, r[0], r[1], r[2], r[3]);
+            philox_block(s, s.c1, (uint32_t)(ub >> 32), (uint32_t)ub, K, r[0], r[1], r[2], r[3]);
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const uint32_t u = r[i];
                 const uint32_t U = searching ? c[i].x : c[i].y;
                 const bool valid = 4 * j + (uint32_t)i < nch;
-                const bool fired = valid && (searching ? ((c[i].w & S2_LAST) != 0u || u < U) : u < U);
-                if (fired) {
-                    searching = false;
-                    const uint32_t val = grouped_outcome(c[i].w & 3u, u, U);
-                    if (!v_a) { s_a = c[i].z; v_a = val; }
-                    else if (!v_b) { s_b = c[i].z; v_b = val; }
-                    else apply_bits(c[i].z, val);
-                }
+                const bool fired = valid && (u < U || (searching && (c[i].w & S2_LAST) != 0u));
+                const bool to_a = fired && !have_a;
+                const bool to_b = fired && have_a && !have_b;
+                if (fired && have_b) apply_bits(c[i].z, grouped_outcome(c[i].w & 3u, u, U));
+                sym_a = to_a ? c[i].z : sym_a;
+                w_a = to_a ? c[i].w : w_a;
+                u_a = to_a ? u : u_a;
+                U_a = to_a ? U : U_a;
+                sym_b = to_b ? c[i].z : sym_b;
+                w_b = to_b ? c[i].w : w_b;
+                u_b = to_b ? u : u_b;
+                U_b = to_b ? U : U_b;
+                have_b = have_b || to_b;
+                have_a = have_a || fired;
+                searching = searching && !fired;
             }
             __syncwarp();
         }
-        apply_bits(s_a, v_a);
-        apply_bits(s_b, v_b);
+        if (have_a) apply_bits(sym_a, grouped_outcome(w_a & 3u, u_a, U_a));
+        if (have_b) apply_bits(sym_b, grouped_outcome(w_b & 3u, u_b, U_b));
         __syncwarp();
     }
     __syncwarp();
