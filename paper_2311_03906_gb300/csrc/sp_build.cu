@@ -820,6 +820,9 @@ __global__ void k_check_random(const uint32_t *A, int64_t apitch, int64_t row0, 
 
 // Row nonzeros (symbols only) of A_j, or of A_j ^ A_parent(j) when parent
 // is given; in fill mode the symbol indices (s-1) are written in order.
+// One warp per row, four consecutive words per lane (the row pitch is a
+// multiple of four words), so that each warp keeps 512 bytes of the row in
+// flight: the pass streams the whole coefficient matrix.
 __global__ void k_row_csr(const uint32_t *__restrict__ A, int64_t apitch, int64_t nrows,
                           const int32_t *__restrict__ parent, uint32_t *count,
                           const uint32_t *__restrict__ off, uint32_t *idx)
@@ -832,15 +835,19 @@ __global__ void k_row_csr(const uint32_t *__restrict__ A, int64_t apitch, int64_
     const uint32_t *rp = pj >= 0 ? A + (size_t)pj * apitch : nullptr;
     uint32_t base = idx ? off[j] : 0u;
     uint32_t cnt = 0;
-    for (int64_t w0 = 0; w0 < apitch; w0 += 32) {
-        const int64_t w = w0 + lane;
-        uint32_t m = 0;
+    for (int64_t w0 = 0; w0 < apitch; w0 += 128) {
+        const int64_t w = w0 + 4 * lane;
+        uint32_t m[4] = {0u, 0u, 0u, 0u};
         if (w < apitch) {
-            m = rj[w];
-            if (rp) m ^= rp[w];
-            if (w == 0) m &= ~1u;
+            const uint4 a = *reinterpret_cast<const uint4 *>(rj + w);
+            m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
+            if (rp) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(rp + w);
+                m[0] ^= x.x; m[1] ^= x.y; m[2] ^= x.z; m[3] ^= x.w;
+            }
+            if (w == 0) m[0] &= ~1u;
         }
-        const int c = __popc(m);
+        const int c = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
         int inc = c;
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(FULL, inc, o);
@@ -849,10 +856,14 @@ __global__ void k_row_csr(const uint32_t *__restrict__ A, int64_t apitch, int64_
         const int tot = __shfl_sync(FULL, inc, 31);
         if (idx) {
             uint32_t pos = base + (uint32_t)(inc - c);
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                idx[pos++] = (uint32_t)(w * 32 + b) - 1u;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                uint32_t mk = m[k];
+                while (mk) {
+                    const int b = __ffs(mk) - 1;
+                    mk &= mk - 1;
+                    idx[pos++] = (uint32_t)((w + k) * 32 + b) - 1u;
+                }
             }
         }
         base += (uint32_t)tot;
