@@ -36,8 +36,8 @@ UNIT = "shots/s"
 # the first timed 1,000,000-shot launch. The figure belongs to the kernel
 # source it was taken on; when the hash of that source differs, it is dropped
 # (reported as null) until a new capture replaces it.
-FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 855_296 + 301_372_672,
-                 "sources_sha256": "37c081d302df1409de9a23893100290419bc45a893d657a818e61ceb78c23b6a"}
+FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 900_352 + 301_310_208,
+                 "sources_sha256": "c8cb8b7adee358a3dbdf777f931ab43286da9551cfd1e3535c7ec74cacb8f810"}
 FUSED_SOURCES = ("paper_2311_03906_gb300/csrc/sp_fused.cu", "paper_2311_03906_gb300/csrc/sp_fused_dev.cuh",
                  "paper_2311_03906_gb300/csrc/sp_internal.h")
 
@@ -220,9 +220,10 @@ def run_reference(args):
 
 def _mul_roofline(info, shots, avg_ms):
     """Achieved integer multiplies of the fused kernel's Philox draw against
-    the multiply pipe: 32 multiply issues per (shot, 4-channel block)."""
+    the multiply pipe: 32 multiply issues per (shot, 4-channel block the draw
+    evaluates; blocks whose channels change no record are skipped)."""
     peaks = _peaks()
-    nblocks = -(-info["num_channels"] // 4)
+    nblocks = info["live_blocks"]
     achieved = nblocks * 32.0 * shots / (avg_ms / 1e3) / 1e12
     peak = 152 * 64 * peaks["sm_max_mhz"] * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
@@ -752,7 +753,7 @@ def run_ours(args):
     total_ms = sum(v[0] for v in prof.values()) or 1.0
     bytes_B = info["num_symbols"] * shots / 8.0
     bytes_rec = nrec * shots / 8.0
-    nblocks = -(-info["num_channels"] // 4)
+    nblocks = info["live_blocks"]   # the blocks the draw evaluates (see _mul_roofline)
     # Philox4x32-10 per (shot, 4-channel block): 16 of its 20 32x32->64-bit
     # products depend on both the shot and the block (rounds 3-10); round 1's
     # two and round 2's M1 product depend on the shot or the block alone, and

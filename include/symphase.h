@@ -130,6 +130,9 @@ typedef struct {
     double build_ms;               /* wall time of sp_build */
     double path_probe_ms[5];       /* build-time probe of 32,768 shots per SP_PATH_* (0 = not timed: the
                                       dense forms are timed only where >= 1 % of the coefficients are set) */
+    uint64_t live_blocks;          /* 4-channel blocks the per-channel draw evaluates per shot: those with a
+                                      channel that can fire and whose symbols some measurement row holds
+                                      (the others change no record and are skipped) */
 } sp_info_t;
 
 typedef struct sp_program sp_program;   /* opaque, library-owned */

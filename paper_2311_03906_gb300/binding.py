@@ -57,7 +57,8 @@ class sp_info_t(C.Structure):
                 ("log_words", C.c_uint64), ("density", C.c_double), ("path", C.c_int32),
                 ("fused_tile_shots", C.c_int32), ("fused_variant", C.c_int32),
                 ("fused_ctas_per_sm", C.c_int32), ("autotune_launches", C.c_int32), ("stream", C.c_int32),
-                ("chunk_shots", C.c_uint64), ("build_ms", C.c_double), ("path_probe_ms", C.c_double * 5)]
+                ("chunk_shots", C.c_uint64), ("build_ms", C.c_double), ("path_probe_ms", C.c_double * 5),
+                ("live_blocks", C.c_uint64)]
 
 
 _lib = None

@@ -235,6 +235,7 @@ sp_status sp_info(const sp_program *P, sp_info_t *o)
     o->chunk_shots = (uint64_t)P->chunk_shots;
     o->build_ms = P->build_ms;
     for (int k = 0; k < 5; k++) o->path_probe_ms[k] = P->path_probe_ms[k];
+    o->live_blocks = (uint64_t)P->n_blk_live;
     return SP_OK;
 }
 

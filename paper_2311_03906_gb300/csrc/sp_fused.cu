@@ -304,26 +304,35 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
             if (r3 < T.w) word[t] |= bit << 3;
         }
     };
+    constexpr uint32_t ALL = (1u << DRAW_GROUP) - 1u;
     for (uint32_t g = b0; g < b1; g += DRAW_GROUP) {
         const uint32_t nb = min(DRAW_GROUP, b1 - g);
         // lane k < nb holds block g+k's filter threshold
         const uint32_t filt = (uint32_t)lane < nb ? blkFilt[g + lane] : 0u;
+        // blocks with a channel that can fire (a zero filter entry: every
+        // threshold is zero, so no channel of the block fires in any shot and
+        // its Philox words are not needed)
+        const uint32_t act = __ballot_sync(FM, filt != 0u);
+        if (!act) continue;
         const uint64_t ug = (uint64_t)PH_M1 * g;
         uint32_t word[TW];
 #pragma unroll
         for (int t = 0; t < TW; t++) word[t] = 0u;
         if (!__any_sync(FM, filt == FREQUENT)) {
-            if (BC && nb == DRAW_GROUP) {
+            if (BC && act == ALL) {
 #pragma unroll
                 for (uint32_t kk = 0; kk < DRAW_GROUP; kk++) step_rare_bc(g, kk, word);
-            } else if (nb == DRAW_GROUP) {
+            } else if (act == ALL) {
 #pragma unroll
                 for (uint32_t kk = 0; kk < DRAW_GROUP; kk++)
                     step_rare(kk, ug + (uint64_t)kk * PH_M1, __shfl_sync(FM, filt, kk), word);
             } else {
 #pragma unroll 1
-                for (uint32_t kk = 0; kk < nb; kk++)
-                    step_rare(kk, ug + (uint64_t)kk * PH_M1, __shfl_sync(FM, filt, kk), word);
+                for (uint32_t m = act; m; m &= m - 1u) {
+                    const uint32_t kk = (uint32_t)__ffs(m) - 1u;
+                    if (BC) step_rare_bc(g, kk, word);
+                    else step_rare(kk, ug + (uint64_t)kk * PH_M1, __shfl_sync(FM, filt, kk), word);
+                }
             }
 #pragma unroll
             for (int t = 0; t < TW; t++) enqueue(g, t, word[t], 0u, 1);
@@ -335,12 +344,15 @@ __device__ __forceinline__ void draw_group_impl(const uint4 *__restrict__ blkT, 
             jmeta = blkMeta[g + (lane >> 2)];
             js0 = blkSym0[g + (lane >> 2)];
         }
-        if (nb == DRAW_GROUP) {
+        if (act == ALL) {
 #pragma unroll
             for (uint32_t kk = 0; kk < DRAW_GROUP; kk++) step_exact(g, kk, ug + (uint64_t)kk * PH_M1, word);
         } else {
 #pragma unroll 1
-            for (uint32_t kk = 0; kk < nb; kk++) step_exact(g, kk, ug + (uint64_t)kk * PH_M1, word);
+            for (uint32_t m = act; m; m &= m - 1u) {
+                const uint32_t kk = (uint32_t)__ffs(m) - 1u;
+                step_exact(g, kk, ug + (uint64_t)kk * PH_M1, word);
+            }
         }
         uint32_t any = 0;
 #pragma unroll
@@ -725,22 +737,12 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
         }
         meta |= off << 24;
         bT[b] = make_uint4(Tv[0], Tv[1], Tv[2], Tv[3]);
-        const uint64_t sumT = (uint64_t)Tv[0] + Tv[1] + Tv[2] + Tv[3];
-        bFilt[b] = sumT >= FREQUENT_SUM ? FREQUENT : std::max(std::max(Tv[0], Tv[1]), std::max(Tv[2], Tv[3]));
         bMeta[b] = meta;
         sym += off;
     }
     bSym0[nb] = sym;
     if ((int64_t)sym != P->n_sym) return set_error(SP_ERR_CUDA, "channel symbol count mismatch");
     sp_status st;
-    if ((st = upload(&P->d_blkT, bT, s)) || (st = upload(&P->d_blkMeta, bMeta, s)) || (st = upload(&P->d_blkSym0, bSym0, s)) ||
-        (st = upload(&P->d_blkFilt, bFilt, s)))
-        return st;
-    if (dev_alloc((void **)&P->d_blkConst, (size_t)std::max<int64_t>(nb, 1) * sizeof(uint4)) != cudaSuccess) {
-        cudaGetLastError();
-        P->d_blkConst = nullptr;
-        return set_error(SP_ERR_OOM, "cudaMalloc of the block constants failed");
-    }
 
     // ---- product program: the measurement rows' own parts by symbol -------
     const int64_t R = P->n_rows;
@@ -772,6 +774,39 @@ sp_status build_fused_program(sp_program *P, cudaStream_t s)
             for (uint32_t k = off[j]; k < off[j + 1]; k++) colRows[pos[own_idx[k]]++] = (uint32_t)j;
     }
     if ((st = upload(&P->d_colOff, colOff, s)) || (st = upload(&P->d_colRows, colRows, s))) return st;
+    // A channel none of whose symbols is held by a measurement row's own
+    // part changes no record (every record row is an XOR of own parts along
+    // a parent chain, and detectors and observables are XORs of measurement
+    // rows), so the sampler's copy of its threshold is zero and its block is
+    // skipped by the draws when no channel of it can fire.  The channel
+    // table keeps the circuit's thresholds.
+    int64_t live_blocks = 0;
+    for (int64_t b = 0; b < nb; b++) {
+        uint32_t Tv[4] = {bT[b].x, bT[b].y, bT[b].z, bT[b].w};
+        const uint32_t meta = bMeta[b];
+        for (int i = 0; i < 4; i++) {
+            if (4 * b + i >= nch) continue;
+            const uint32_t kd = (meta >> (2 * i)) & 3u;
+            const uint32_t k = kd == CK_DEP2 ? 4u : kd == CK_DEP1 ? 2u : 1u;
+            const uint32_t v0 = bSym0[b] + ((meta >> (8 + 4 * i)) & 15u);
+            bool held = false;
+            for (uint32_t v = v0; v < v0 + k; v++) held = held || colOff[v + 1] > colOff[v];
+            if (!held) Tv[i] = 0u;
+        }
+        bT[b] = make_uint4(Tv[0], Tv[1], Tv[2], Tv[3]);
+        const uint64_t sumT = (uint64_t)Tv[0] + Tv[1] + Tv[2] + Tv[3];
+        bFilt[b] = sumT >= FREQUENT_SUM ? FREQUENT : std::max(std::max(Tv[0], Tv[1]), std::max(Tv[2], Tv[3]));
+        live_blocks += bFilt[b] != 0u;
+    }
+    P->n_blk_live = live_blocks;
+    if ((st = upload(&P->d_blkT, bT, s)) || (st = upload(&P->d_blkMeta, bMeta, s)) || (st = upload(&P->d_blkSym0, bSym0, s)) ||
+        (st = upload(&P->d_blkFilt, bFilt, s)))
+        return st;
+    if (dev_alloc((void **)&P->d_blkConst, (size_t)std::max<int64_t>(nb, 1) * sizeof(uint4)) != cudaSuccess) {
+        cudaGetLastError();
+        P->d_blkConst = nullptr;
+        return set_error(SP_ERR_OOM, "cudaMalloc of the block constants failed");
+    }
     // step 0: constants of the own parts
     std::vector<uint8_t> cf(cflag.begin(), cflag.begin() + M);
     // step B: parent chains, whole trees per thread, parents first

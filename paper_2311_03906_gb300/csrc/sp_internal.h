@@ -136,6 +136,7 @@ struct sp_program {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // draw descriptors: blocks of 4 channels (thresholds, kinds/offsets, first symbol)
     int64_t n_blk = 0;
+    int64_t n_blk_live = 0;            // blocks with a channel that can fire and changes some record
     uint4 *d_blkT = nullptr;
     uint32_t *d_blkMeta = nullptr;
     uint32_t *d_blkSym0 = nullptr;

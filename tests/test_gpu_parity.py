@@ -90,6 +90,17 @@ def test_rows_match_oracle(name):
     np.testing.assert_array_equal(s0, ch.sym0)
     want_kind = np.select([ch.type == 3, ch.type == 4, ch.type == 5], [1, 2, 3], 0)
     np.testing.assert_array_equal(kind, want_kind)
+    # the channel table keeps every threshold; the draws evaluate only the
+    # 4-channel blocks holding a channel that can fire (T > 0) with a symbol
+    # some measurement row holds (the oracle's rows): the others change no
+    # record
+    held = np.unpackbits(np.bitwise_or.reduce(ref.rows("meas"), axis=0).view(np.uint8),
+                         bitorder="little")[: ref.num_symbols + 1].astype(bool)
+    live = np.array([ch.T[i] > 0 and held[ch.sym0[i]: ch.sym0[i] + ch.nsym[i]].any() for i in range(len(ch.T))],
+                    dtype=bool)
+    blocks = np.zeros((len(live) + 3) // 4, dtype=bool)
+    blocks[np.nonzero(live)[0] // 4] = True
+    assert prog.info["live_blocks"] == int(blocks.sum())
 
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
