@@ -36,8 +36,8 @@ UNIT = "shots/s"
 # the first timed 1,000,000-shot launch. The figure belongs to the kernel
 # source it was taken on; when the hash of that source differs, it is dropped
 # (reported as null) until a new capture replaces it.
-FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 900_352 + 301_310_208,
-                 "sources_sha256": "c8cb8b7adee358a3dbdf777f931ab43286da9551cfd1e3535c7ec74cacb8f810"}
+FUSED_TRAFFIC = {"shots": 1_000_000, "bytes": 682_496 + 301_122_816,
+                 "sources_sha256": "1a4991b81e5bc085a0f99b171807072bc063b5f72ab515f3a67257e98aa64448"}
 FUSED_SOURCES = ("paper_2311_03906_gb300/csrc/sp_fused.cu", "paper_2311_03906_gb300/csrc/sp_fused_dev.cuh",
                  "paper_2311_03906_gb300/csrc/sp_internal.h")
 

@@ -525,15 +525,16 @@ __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ b
 // channel blocks (blockIdx.y), with the fused kernel's draw (least-word
 // filter, events resolved 32 at a time); every fired symbol's shot word is
 // XORed straight into the records of the rows holding it (the full rows by
-// symbol; recT pre-filled with the rows' constants), by atomics in L2.
+// symbol; rec pre-filled with the rows' constants, word-major: word w of row
+// j at rec[w * nrows + j]), by atomics in L2.
 __global__ void __launch_bounds__(256, 4) k_draw_push(const uint4 *__restrict__ blkT,
                                                       const uint32_t *__restrict__ blkMeta,
                                                       const uint32_t *__restrict__ blkSym0,
                                                       const uint32_t *__restrict__ blkFilt, int64_t n_blk,
                                                       uint64_t seed, uint64_t shot0, int64_t nwords,
                                                       const uint32_t *__restrict__ colOff,
-                                                      const uint32_t *__restrict__ colRows, uint32_t *recT,
-                                                      int64_t rpitch)
+                                                      const uint32_t *__restrict__ colRows, uint32_t *rec,
+                                                      int64_t nrows)
 {
     __shared__ uint32_t q[8 * FUSED_QCAP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -551,18 +552,19 @@ __global__ void __launch_bounds__(256, 4) k_draw_push(const uint4 *__restrict__ 
     const uint64_t e1 = ngrp * (blockIdx.y + 1) / gridDim.y * DRAW_GROUP;
     const uint32_t b1 = (uint32_t)(e1 < (uint64_t)n_blk ? e1 : (uint64_t)n_blk);
     if (b0 >= b1) return;
-    uint32_t *rec = recT + 2 * gw;
+    uint32_t *rec0 = rec + (size_t)(2 * gw) * nrows;   // word 2gw; word 2gw+1 follows nrows later
     draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, nullptr, b0, b1, sc, shot_base, K, k1, lane,
                     q + warp * FUSED_QCAP,
                     [=](uint32_t sym, int t, uint32_t word) {
                         if (t == 1 && !has2) return;
+                        uint32_t *rw = rec0 + (size_t)t * nrows;
                         const uint32_t e = colOff[sym + 1];
-                        for (uint32_t k = colOff[sym]; k < e; k++) atomicXor(&rec[(size_t)colRows[k] * rpitch + t], word);
+                        for (uint32_t k = colOff[sym]; k < e; k++) atomicXor(&rw[colRows[k]], word);
                     });
 }
 
-sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *recT,
-                           int64_t pitch, cudaStream_t s)
+sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *rec,
+                           cudaStream_t s)
 {
     if (P->n_blk == 0 || nwords == 0) return SP_OK;
     // a warp's queued events address the blocks of its range (at most all)
@@ -575,7 +577,7 @@ sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, i
     const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, ctas), ngrp / 64, 65535}));
     k_draw_push<<<dim3((unsigned)ctas, (unsigned)ranges), 256, 0, s>>>(
         P->d_blkT, P->d_blkMeta, P->d_blkSym0, P->d_blkFilt, P->n_blk, seed, shot0, nwords, P->d_colFullOff,
-        P->d_colFullRows, recT, pitch);
+        P->d_colFullRows, rec, P->n_rows);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }

@@ -252,8 +252,9 @@ sp_status choose_path(sp_program *P, cudaStream_t s);
 bool tensor_path_available(const sp_program *P);
 sp_status dense_chunk(sp_program *P, uint64_t seed, uint64_t shot0, uint64_t nshots, uint64_t *d_meas,
                       uint64_t *d_det, uint64_t *d_obs, cudaStream_t s);
-sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *recT,
-                           int64_t pitch, cudaStream_t s);
+// rec: word-major records, word w of row j at rec[w * n_rows + j]
+sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t nwords, uint32_t *rec,
+                           cudaStream_t s);
 sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, int64_t ngroups, uint32_t *Bd,
                             int64_t bpitch, cudaStream_t s);
 // fused path (sp_fused.cu)
