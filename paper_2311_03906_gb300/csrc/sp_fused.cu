@@ -530,8 +530,9 @@ __global__ void __launch_bounds__(256) k_draw_staged(const uint4 *__restrict__ b
 __global__ void __launch_bounds__(256, 4) k_draw_push(const uint4 *__restrict__ blkT,
                                                       const uint32_t *__restrict__ blkMeta,
                                                       const uint32_t *__restrict__ blkSym0,
-                                                      const uint32_t *__restrict__ blkFilt, int64_t n_blk,
-                                                      uint64_t seed, uint64_t shot0, int64_t nwords,
+                                                      const uint32_t *__restrict__ blkFilt,
+                                                      const uint4 *__restrict__ blkConst, int64_t n_blk,
+                                                      uint64_t seed, const Keys K, uint64_t shot0, int64_t nwords,
                                                       const uint32_t *__restrict__ colOff,
                                                       const uint32_t *__restrict__ colRows, uint32_t *rec,
                                                       int64_t nrows)
@@ -540,26 +541,27 @@ __global__ void __launch_bounds__(256, 4) k_draw_push(const uint4 *__restrict__ 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * 8 + warp;      // words 2gw and 2gw+1
     if (2 * gw >= nwords) return;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t k1 = (uint32_t)(seed >> 32);
     const uint64_t shot_base = shot0 + 64u * (uint64_t)gw;
     Shots<2> sc;
 #pragma unroll
     for (int t = 0; t < 2; t++) sc.s[t] = shot_const(shot_base + 32u * t + lane, k1);
     const bool has2 = 2 * gw + 1 < nwords;
-    const Keys K = make_keys(k0, k1);
     const uint64_t ngrp = ((uint64_t)n_blk + DRAW_GROUP - 1) / DRAW_GROUP;
     const uint32_t b0 = (uint32_t)(ngrp * blockIdx.y / gridDim.y) * DRAW_GROUP;
     const uint64_t e1 = ngrp * (blockIdx.y + 1) / gridDim.y * DRAW_GROUP;
     const uint32_t b1 = (uint32_t)(e1 < (uint64_t)n_blk ? e1 : (uint64_t)n_blk);
     if (b0 >= b1) return;
-    uint32_t *rec0 = rec + (size_t)(2 * gw) * nrows;   // word 2gw; word 2gw+1 follows nrows later
-    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, nullptr, b0, b1, sc, shot_base, K, k1, lane,
+    // word 2gw of row j at rec[2gw * nrows + j], word 2gw+1 nrows later (the
+    // launcher keeps nwords * nrows below 2^32)
+    const uint32_t nr = (uint32_t)nrows, w0 = (uint32_t)(2 * gw) * nr;
+    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, blkConst, b0, b1, sc, shot_base, K, k1, lane,
                     q + warp * FUSED_QCAP,
                     [=](uint32_t sym, int t, uint32_t word) {
                         if (t == 1 && !has2) return;
-                        uint32_t *rw = rec0 + (size_t)t * nrows;
+                        const uint32_t base = w0 + (t ? nr : 0u);
                         const uint32_t e = colOff[sym + 1];
-                        for (uint32_t k = colOff[sym]; k < e; k++) atomicXor(&rw[colRows[k]], word);
+                        for (uint32_t k = colOff[sym]; k < e; k++) atomicXor(&rec[base + colRows[k]], word);
                     });
 }
 
@@ -570,14 +572,31 @@ sp_status launch_draw_push(const sp_program *P, uint64_t seed, uint64_t shot0, i
     // a warp's queued events address the blocks of its range (at most all)
     if ((uint64_t)P->n_blk >= event_max_blocks(2))
         return set_error(SP_ERR_INVALID_ARG, "too many channel blocks for the staged draw");
+    if ((uint64_t)nwords * (uint64_t)P->n_rows >= (1ull << 32))
+        return set_error(SP_ERR_INVALID_ARG, "records too large for the push draw");
     // about four waves of warps (4 CTAs of 8 warps per SM), each range keeping at least 64 groups
     const int64_t ctas = ceil_div(ceil_div(nwords, 2), 8);
     const int64_t want = 4 * 4 * (int64_t)std::max(P->num_sms, 1);
     const int64_t ngrp = ceil_div(P->n_blk, (int64_t)DRAW_GROUP);
     const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, ctas), ngrp / 64, 65535}));
+    // the round keys as launch parameters (constant-bank operands), and the
+    // launch's block constants when all its shots share a high word
+    Keys K;
+    for (int r = 0; r < 10; r++) {
+        K.k0[r] = (uint32_t)seed + (uint32_t)r * PH_W0;
+        K.k1[r] = (uint32_t)(seed >> 32) + (uint32_t)r * PH_W1;
+    }
+    const uint4 *consts = nullptr;
+    if (P->d_blkConst && (shot0 >> 32) == ((shot0 + 32u * (uint64_t)nwords - 1u) >> 32)) {
+        k_block_consts<<<(unsigned)ceil_div(P->n_blk, 256), 256, 0, s>>>(P->n_blk, (uint32_t)seed,
+                                                                        (uint32_t)(shot0 >> 32), P->d_blkFilt,
+                                                                        P->d_blkConst);
+        SP_CUDA(cudaGetLastError());
+        consts = P->d_blkConst;
+    }
     k_draw_push<<<dim3((unsigned)ctas, (unsigned)ranges), 256, 0, s>>>(
-        P->d_blkT, P->d_blkMeta, P->d_blkSym0, P->d_blkFilt, P->n_blk, seed, shot0, nwords, P->d_colFullOff,
-        P->d_colFullRows, rec, P->n_rows);
+        P->d_blkT, P->d_blkMeta, P->d_blkSym0, P->d_blkFilt, consts, P->n_blk, seed, K, shot0, nwords,
+        P->d_colFullOff, P->d_colFullRows, rec, P->n_rows);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
