@@ -621,34 +621,37 @@ __global__ void __launch_bounds__(256) k_dense_fill(uint32_t *__restrict__ Bd, i
 __global__ void __launch_bounds__(256, 4) k_draw_dense(const uint4 *__restrict__ blkT,
                                                        const uint32_t *__restrict__ blkMeta,
                                                        const uint32_t *__restrict__ blkSym0,
-                                                       const uint32_t *__restrict__ blkFilt, int64_t n_blk,
-                                                       uint64_t seed, uint64_t shot0, int64_t ngroups,
+                                                       const uint32_t *__restrict__ blkFilt,
+                                                       const uint4 *__restrict__ blkConst, int64_t n_blk,
+                                                       uint64_t seed, const Keys K, uint64_t shot0, int64_t ngroups,
                                                        uint32_t *__restrict__ Bd, int64_t bpitch)
 {
     __shared__ uint32_t q[8 * FUSED_QCAP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * 8 + warp;      // groups 2gw and 2gw+1
     if (2 * gw >= ngroups) return;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t k1 = (uint32_t)(seed >> 32);
     const uint64_t shot_base = shot0 + 64u * (uint64_t)gw;
     Shots<2> sc;
 #pragma unroll
     for (int t = 0; t < 2; t++) sc.s[t] = shot_const(shot_base + 32u * t + lane, k1);
     uint32_t *base = Bd + (size_t)(2 * gw) * (size_t)bpitch * 32u;
     const bool has2 = 2 * gw + 1 < ngroups;
-    const Keys K = make_keys(k0, k1);
     // this CTA's range of channel blocks, in whole groups of DRAW_GROUP
     const uint64_t ngrp = ((uint64_t)n_blk + DRAW_GROUP - 1) / DRAW_GROUP;
     const uint32_t b0 = (uint32_t)(ngrp * blockIdx.y / gridDim.y) * DRAW_GROUP;
     const uint64_t e1 = ngrp * (blockIdx.y + 1) / gridDim.y * DRAW_GROUP;
     const uint32_t b1 = (uint32_t)(e1 < (uint64_t)n_blk ? e1 : (uint64_t)n_blk);
     if (b0 >= b1) return;
-    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, nullptr, b0, b1, sc, shot_base, K, k1, lane,
+    // offsets within this warp's two shot groups (2 * bpitch * 32 words,
+    // below 2^32: the launcher checks)
+    const uint32_t gstride = (uint32_t)bpitch * 32u;
+    draw_scatter<2>(blkT, blkMeta, blkSym0, blkFilt, blkConst, b0, b1, sc, shot_base, K, k1, lane,
                     q + warp * FUSED_QCAP,
                     [=](uint32_t sym, int t, uint32_t word) {
                         if (t == 1 && !has2) return;
                         const uint32_t e = sym + 1u;
-                        uint32_t *wp = base + ((size_t)t * (size_t)bpitch + e / 32u) * 32u;
+                        uint32_t *wp = base + ((t ? gstride : 0u) + (e / 32u) * 32u);
                         const uint32_t bit = 1u << (e & 31u);
                         while (word) {
                             const int l = __ffs(word) - 1;
@@ -675,9 +678,25 @@ sp_status launch_draw_dense(const sp_program *P, uint64_t seed, uint64_t shot0, 
     const int64_t want = 4 * 4 * (int64_t)std::max(P->num_sms, 1);
     const int64_t ngrp = ceil_div(P->n_blk, (int64_t)DRAW_GROUP);
     const int64_t ranges = std::max<int64_t>(1, std::min<int64_t>({ceil_div(want, ctas), ngrp / 64, 65535}));
+    if ((uint64_t)bpitch * 64u >= (1ull << 32)) return set_error(SP_ERR_INVALID_ARG, "shots too wide for the dense draw");
+    // the round keys as launch parameters, and the launch's block constants
+    // when all its shots share a high word (as for the push draw)
+    Keys K;
+    for (int r = 0; r < 10; r++) {
+        K.k0[r] = (uint32_t)seed + (uint32_t)r * PH_W0;
+        K.k1[r] = (uint32_t)(seed >> 32) + (uint32_t)r * PH_W1;
+    }
+    const uint4 *consts = nullptr;
+    if (P->d_blkConst && (shot0 >> 32) == ((shot0 + 32u * (uint64_t)ngroups - 1u) >> 32)) {
+        k_block_consts<<<(unsigned)ceil_div(P->n_blk, 256), 256, 0, s>>>(P->n_blk, (uint32_t)seed,
+                                                                        (uint32_t)(shot0 >> 32), P->d_blkFilt,
+                                                                        P->d_blkConst);
+        SP_CUDA(cudaGetLastError());
+        consts = P->d_blkConst;
+    }
     k_draw_dense<<<dim3((unsigned)ctas, (unsigned)ranges), 256, 0, s>>>(P->d_blkT, P->d_blkMeta, P->d_blkSym0,
-                                                                        P->d_blkFilt, P->n_blk, seed, shot0, ngroups,
-                                                                        Bd, bpitch);
+                                                                        P->d_blkFilt, consts, P->n_blk, seed, K,
+                                                                        shot0, ngroups, Bd, bpitch);
     SP_CUDA(cudaGetLastError());
     return SP_OK;
 }
