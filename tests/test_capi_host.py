@@ -118,3 +118,37 @@ def test_batch_plan_cache_is_empty_and_bounded(lib):
     n, cap = C.c_uint32(7), C.c_uint32(0)
     assert lib.sp_batch_plans(C.byref(n), C.byref(cap)) == 0
     assert n.value == 0 and cap.value == 8
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of sp_op, sp_circuit_desc and sp_info_t have the
+    C header's size and field offsets (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    from paper_2311_03906_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"sp_op": binding.sp_op, "sp_circuit_desc": binding.sp_circuit_desc, "sp_info_t": binding.sp_info_t}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "symphase.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            got[(name, key)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
